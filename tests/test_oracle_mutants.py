@@ -1,0 +1,76 @@
+"""Planted mistakes: each test compiles a copy of the oracle with one
+plausible error (on the CPU, in a temporary directory) and checks that one of
+the pins in test_oracle_pins.py fails for it.  This shows the pins constrain
+the part of the method each mistake touches."""
+import importlib.util
+import os
+import subprocess
+
+import pytest
+
+import test_oracle_pins as P
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "dies_oracle.c")
+
+MUTANTS = {
+    # Eq. 2: background directions mu = sqrt(u)
+    "inject_mu_linear": ("mu = sqrt(u_mu);", "mu = u_mu;", "test_pure_absorber_shells_impact_parameter_quadrature",
+                         {"r_in": 0.0}),
+    # Eq. 4: tau_S consumed with the absorption coefficient
+    "eq4_kappa_typo": ("p.tauS -= ks * l;", "p.tauS -= ka * l;", "test_pure_scatterer_isotropic_field_invariant",
+                       {"g": 0.6}),
+    # HG inversion with the wrong sign of g
+    "hg_sign": ("double mu = (1.0 + g * g - t * t) / (2.0 * g);", "double mu = -(1.0 + g * g - t * t) / (2.0 * g);",
+                "test_hg_sampler_moments", {"g": 0.6}),
+    # scattering azimuth frozen at 0 (direction pulled toward the radius vector)
+    "scatter_no_azimuth": ("dn[i] = mu_s * p->d[i] + st * (cos(phi) * e1[i] + sin(phi) * e2[i]);",
+                           "dn[i] = mu_s * p->d[i] + st * e1[i];", "test_pure_scatterer_isotropic_field_invariant",
+                           {"g": 0.6}),
+    # inward flux of an isotropic field taken as J instead of pi J
+    "external_flux_factor": ("L_out[0] = 4.0 * ORC_PI * ORC_PI * R * R * s;", "L_out[0] = 4.0 * ORC_PI * R * R * s;",
+                             "test_optically_thin_temperature", {}),
+    # re-emission from the new spectrum instead of the difference spectrum
+    "no_difference_spectrum": ("pdiff[k] = bn - Bc[k];", "pdiff[k] = bn;",
+                               "test_difference_spectrum_telescopes_to_final_emission", {}),
+    # Eq. 5 weight with a wrong exponent
+    "kbg_weight_exponent": ("pow(mu, 2.0 - 1.0 / M->k_bg)", "pow(mu, 2.0 - M->k_bg)",
+                            "test_weighted_injection_is_unbiased", {"k_bg": 1.0 / 3.0, "ffi": False}),
+    # Eq. 12 weight not applied
+    "ffi_no_weight": ("    p.w *= q;\n", "\n", "test_weighted_injection_is_unbiased", {"k_bg": 0.5, "ffi": True}),
+    # re-emission direction not isotropic
+    "reemit_not_isotropic": ("double mu = 2.0 * u_mu - 1.0, phi = 2.0 * ORC_PI * u_phi;",
+                             "double mu = u_mu, phi = 2.0 * ORC_PI * u_phi;",
+                             "test_absorb_reemit_grey_isotropic_invariant", {}),
+    # cell emission normalisation without the 4 pi
+    "mass_no_4pi": ("mass[i] = 4.0 * ORC_PI * M->rho[i] * V * Lu2;", "mass[i] = M->rho[i] * V * Lu2;",
+                    "test_optically_thin_temperature", {}),
+    # Philox with one Weyl increment wrong
+    "philox_key_bump": ("k1 += 0xBB67AE85u;", "k1 += 0xBB67AE84u;", "test_philox_known_answer_vectors", {}),
+}
+
+
+def _load_mutant(tmp_path, name, old, new):
+    src = open(SRC).read()
+    assert src.count(old) >= 1, f"mutation anchor for {name} not found"
+    mutated = src.replace(old, new, 1)
+    csrc = tmp_path / f"{name}.c"
+    so = tmp_path / f"lib{name}.so"
+    csrc.write_text(mutated)
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", str(so),
+                           str(csrc), "-lm"])
+    spec = importlib.util.spec_from_file_location(f"oracle_mutant_{name}", os.path.join(ROOT, "oracle", "oracle.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    mod._SRC = str(csrc)
+    mod._LIB = str(so)
+    mod._lib = None
+    return mod
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pin_catches_planted_mistake(tmp_path, name):
+    old, new, pin, kw = MUTANTS[name]
+    mod = _load_mutant(tmp_path, name, old, new)
+    with pytest.raises(AssertionError):
+        getattr(P, pin)(mod, **kw)

@@ -1,0 +1,299 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against a value that does not come from the
+oracle itself: published known-answer vectors, closed-form transfer results
+for special cases of Sect. 2.1, exact invariants (energy conservation, the
+isotropic-field solution of a pure scatterer, the telescoping of the
+difference spectra) and the HG distribution of Eq. 6.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import closed_forms as CF
+from paper_2408_13807_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- RNG
+def test_philox_known_answer_vectors(oracle):
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) if l.strip() and l[0] != "#"]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = oracle.philox(v[0:4], v[4:6])
+        assert [int(x) for x in out] == v[6:10]
+
+
+def test_uniform_open_interval(oracle):
+    assert oracle.u01(0, 0) == 2.0 ** -53
+    assert oracle.u01(0xFFFFFFFF, 0xFFFFFFFF) == 1.0 - 2.0 ** -53
+    # the low 12 bits of the second word do not matter, the top 52 bits do
+    assert oracle.u01(0, 0xFFF) == oracle.u01(0, 0)
+    assert oracle.u01(0, 0x1000) == 1.5 * 2.0 ** -52
+
+
+# ---------------------------------------------------------------- spectra
+def test_planck_integral_is_stefan_boltzmann(oracle):
+    nu = np.geomspace(1e8, 1e17, 20001)
+    for T in (10.0, 300.0, 6000.0):
+        B = np.array([oracle.planck(x, T) for x in nu])
+        tot = np.trapezoid(B * nu, np.log(nu))
+        assert tot == pytest.approx(CF.SIGMA_SB * T ** 4 / np.pi, rel=1e-7)
+
+
+def test_planck_peak_wien(oracle):
+    # peak of B_nu at h nu / kT = 2.821439372122079 (root of x = 3(1 - e^-x))
+    T = 50.0
+    nu = np.linspace(1e12, 6e12, 200001)
+    B = np.array([oracle.planck(x, T) for x in nu[::100]])
+    i = np.argmax(B)
+    x_peak = CF.H * nu[::100][i] / (CF.KB * T)
+    assert x_peak == pytest.approx(2.821439372122079, abs=2e-3)
+
+
+def test_dplanck_matches_finite_difference(oracle):
+    for nu, T in ((1e12, 15.0), (3e13, 150.0), (5e14, 3000.0)):
+        h = T * 1e-6
+        fd = (oracle.planck(nu, T + h) - oracle.planck(nu, T - h)) / (2 * h)
+        assert oracle.dplanck_dT(nu, T) == pytest.approx(fd, rel=1e-6)
+
+
+def test_freq_weights_log_uniform(oracle):
+    f = W.freq_grid(64)
+    d = oracle.freq_weights(f)
+    dln = np.log(30000.0) / 63
+    np.testing.assert_allclose(d, f * dln, rtol=1e-12)
+    # non-uniform grid: the bins tile ln(nu) from half a gap below the first
+    # point to half a gap above the last one
+    g = np.sort(np.random.default_rng(1).uniform(1e11, 1e15, 40))
+    dg = oracle.freq_weights(g)
+    span = np.log(g[-1] / g[0]) + 0.5 * (np.log(g[1] / g[0]) + np.log(g[-1] / g[-2]))
+    assert np.sum(dg / g) == pytest.approx(span, rel=1e-12)
+
+
+def test_emission_grey_closed_form(oracle):
+    nu = np.geomspace(1e9, 1e17, 4001)
+    kap = np.full_like(nu, 2.5)
+    for T in (3.0, 40.0, 900.0):
+        assert oracle.emission(nu, kap, T) == pytest.approx(2.5 * CF.SIGMA_SB * T ** 4 / np.pi, rel=1e-5)
+
+
+def test_temperature_inverts_emission(oracle):
+    f = W.freq_grid(64)
+    ka, _, _ = W.dust_tables(f)
+    rng = np.random.default_rng(7)
+    for T in np.exp(rng.uniform(np.log(2.7), np.log(1500.0), 40)):
+        e = oracle.emission(f, ka, T)
+        assert oracle.temperature(f, ka, e) == pytest.approx(T, rel=1e-12)
+        assert oracle.temperature(f, ka, e, T_guess=T * 1.3) == pytest.approx(T, rel=1e-12)
+    # grey closed form: T = (pi e / (kappa sigma))^(1/4)
+    nu = np.geomspace(1e9, 1e17, 4001)
+    kap = np.full_like(nu, 1.0)
+    e = 1e3
+    assert oracle.temperature(nu, kap, e) == pytest.approx((np.pi * e / CF.SIGMA_SB) ** 0.25, rel=1e-5)
+
+
+# ---------------------------------------------------------------- HG (Eq. 6)
+@pytest.mark.parametrize("g", [-0.5, 0.0, 0.3, 0.6, 0.9])
+def test_hg_sampler_moments(oracle, g):
+    u = (np.arange(200000) + 0.5) / 200000
+    mu = np.array([oracle.hg_mu(g, x) for x in u])
+    assert mu.mean() == pytest.approx(g, abs=2e-5)
+    assert (mu ** 2).mean() == pytest.approx((1 + 2 * g * g) / 3, abs=2e-5)
+
+
+@pytest.mark.parametrize("g", [-0.3, 0.6, 0.9])
+def test_hg_sampler_follows_eq6_cdf(oracle, g):
+    u = (np.arange(20000) + 0.5) / 20000
+    mu = np.sort([oracle.hg_mu(g, x) for x in u])
+    for x in (-0.8, -0.2, 0.3, 0.7, 0.95):
+        frac = np.searchsorted(mu, x) / len(mu)
+        assert frac == pytest.approx(CF.hg_cdf_quad(x, g), abs=1e-4)
+
+
+# ---------------------------------------------------------------- transport
+def _fractions(res, L):
+    return res["E_abs"] / L
+
+
+def test_pure_absorber_single_shell_closed_form(oracle):
+    for tau in (0.3, 1.0, 3.0):
+        m = W.grey_model(1, tau)
+        N = 100_000
+        r = oracle.run(m, N, 3, mode="frozen_terminal", T_frozen=np.full(1, 10.0))
+        L = oracle.source_luminosity(m)[0]
+        f = r["E_abs"].sum() / L
+        expect = CF.uniform_sphere_absorbed_fraction(tau)
+        se = np.sqrt(expect * (1 - expect) / N)
+        assert abs(f - expect) < 4.5 * se
+        assert r["stats"]["E_escaped"] + r["E_abs"].sum() == pytest.approx(L, rel=1e-10)
+
+
+@pytest.mark.parametrize("r_in", [0.0, 0.25])
+def test_pure_absorber_shells_impact_parameter_quadrature(oracle, r_in):
+    m = W.grey_model(6, 2.0, r_in=r_in)
+    rng = np.random.default_rng(5)
+    m = m.replace(rho=rng.uniform(0.3, 2.0, 6))
+    k = m.kabs[0] * m.rho
+    N = 150_000
+    r = oracle.run(m, N, 11, mode="frozen_terminal", T_frozen=np.full(6, 10.0))
+    f = _fractions(r, oracle.source_luminosity(m)[0])
+    expect = CF.external_shell_absorption(m.radii, k)
+    se = np.sqrt(expect * (1 - expect) / N)
+    assert np.all(np.abs(f - expect) < 4.5 * se + 1e-12)
+
+
+def test_point_source_radial_absorber(oracle):
+    m = W.grey_model(5, 1.5, r_in=0.1, external=False, L_point=3.828e33)
+    m = m.replace(rho=np.array([2.0, 0.5, 1.0, 1.5, 0.7]))
+    k = m.kabs[0] * m.rho
+    N = 100_000
+    r = oracle.run(m, N, 2, mode="frozen_terminal", T_frozen=np.full(5, 10.0))
+    f = r["E_abs"] / m.L_point
+    expect = CF.point_shell_absorption(m.radii, k)
+    se = np.sqrt(expect * (1 - expect) / N)
+    assert np.all(np.abs(f - expect) < 4.5 * se)
+
+
+@pytest.mark.parametrize("k_bg,ffi", [(1.0 / 3.0, False), (0.2, False), (0.5, True)])
+def test_weighted_injection_is_unbiased(oracle, k_bg, ffi):
+    """Eq. 5 direction weighting and Eqs. 9-12 forced first interaction leave
+    the expected absorption unchanged (pure absorber closed form)."""
+    m = W.grey_model(4, 0.4).replace(k_bg=k_bg, ffi=ffi)
+    k = m.kabs[0] * m.rho
+    expect = CF.external_shell_absorption(m.radii, k)
+    L = oracle.source_luminosity(m)[0]
+    fr = np.array([_fractions(oracle.run(m, 20_000, s, mode="frozen_terminal", T_frozen=np.full(4, 10.0)), L)
+                   for s in range(12)])
+    mean, se = fr.mean(0), fr.std(0, ddof=1) / np.sqrt(len(fr))
+    assert np.all(np.abs(mean - expect) < 4.5 * se + 1e-9)
+
+
+@pytest.mark.parametrize("g", [0.0, 0.6, 0.9])
+def test_pure_scatterer_isotropic_field_invariant(oracle, g):
+    """In a non-absorbing sphere an isotropic external field stays isotropic,
+    so the mean number of scatterings per package is sum_c k_c V_c / (pi R^2)
+    for any density profile and any HG g."""
+    m = W.grey_model(5, 0.8, albedo=1.0, g=g, r_in=0.1)
+    m = m.replace(rho=np.array([3.0, 0.4, 1.0, 2.0, 0.6]))
+    N = 60_000
+    r = oracle.run(m, N, 4, mode="frozen", T_frozen=np.full(5, 10.0), record=True)
+    n_sca = r["n_events"][:, 0].astype(np.float64)
+    expect = CF.pure_scatterer_mean_events(m.radii, m.ksca[0] * m.rho)
+    assert abs(n_sca.mean() - expect) < 4.5 * n_sca.std() / np.sqrt(N)
+    assert r["stats"]["escaped"] == N
+    assert r["stats"]["E_escaped"] == pytest.approx(r["stats"]["E_injected"], rel=1e-10)
+
+
+def test_energy_conservation_ire(oracle):
+    for m in (W.external_cloud(16, 30.0), W.external_cloud(16, 3.0, ffi=True),
+              W.external_cloud(16, 10.0, k_bg=0.25), W.point_source_cloud(24, 1e-3, 20.0)):
+        r = oracle.run(m, 4000, 9)
+        st = r["stats"]
+        assert st["E_escaped"] + st["E_lost"] == pytest.approx(st["E_injected"], rel=1e-10)
+        assert r["sed"].sum() == pytest.approx(st["E_escaped"], rel=1e-10)
+        if m.k_bg == 0.5:
+            assert st["E_injected"] == pytest.approx(oracle.source_luminosity(m).sum(), rel=1e-10)
+
+
+def test_optically_thin_temperature(oracle):
+    """A_V -> 0 with forced first interaction: every cell sees the unattenuated
+    field, so sum_k kabs B_k(T) dnu_k = sum_k kabs J_k dnu_k (thin limit)."""
+    m = W.external_cloud(6, 1e-3, ffi=True).replace(rho=None)
+    m = W.external_cloud(6, 1e-3, ffi=True)
+    m = m.replace(rho=np.full(6, m.rho.mean()))
+    T_thin = CF.thin_limit_temperature(m.freq, m.kabs, m.J_ext)
+    assert 20.0 < T_thin < 35.0
+    r = oracle.run(m, 200_000, 1)
+    mass = oracle.cell_mass(m)
+    e_tot = r["E_abs"].sum() / mass.sum()
+    T_glob = oracle.temperature(m.freq, m.kabs, e_tot)
+    assert T_glob == pytest.approx(T_thin, rel=4e-3)
+    assert np.all(np.abs(r["T"] / T_thin - 1.0) < 0.03)
+
+
+def test_difference_spectrum_telescopes_to_final_emission(oracle):
+    """Sect. 2.1 re-emission: the difference spectra of all absorptions in a
+    cell sum to kabs B(T_final) dnu, so in a cloud transparent at the emission
+    frequencies the escaping dust SED equals sum_c mass_c kabs_k B_k(T_c) dnu_k."""
+    F = 24
+    freq = np.geomspace(3e11, 3e15, F)
+    kabs = np.where(freq > 3e14, 40.0, 1e-3 * (freq / 3e11))
+    J = np.where(freq > 3e14, 1e-14, 0.0)
+    m = W.CloudModel(name="tele", radii=W.equal_radii(4), rho=np.array([1.0, 0.5, 0.3, 0.2]),
+                     length_unit_cm=W.PC_CM, freq=freq, kabs=kabs, ksca=np.zeros(F), g=np.zeros(F), J_ext=J)
+    r = oracle.run(m, 100_000, 3, T_max=1e5)
+    mass = oracle.cell_mass(m)
+    dnu = oracle.freq_weights(freq)
+    low = freq < 1e14
+    expect = np.array([sum(mass[c] * kabs[k] * oracle.planck(freq[k], r["T"][c]) * dnu[k] for c in range(4))
+                       for k in range(F)])
+    got, exp = r["sed"][low], expect[low]
+    assert got.sum() == pytest.approx(exp.sum(), rel=0.01)
+    big = exp > 0.05 * exp.sum()
+    assert np.all(np.abs(got[big] / exp[big] - 1) < 0.08)
+    assert r["stats"]["E_escaped"] == pytest.approx(r["stats"]["E_injected"], rel=1e-10)
+
+
+def test_frozen_reemission_follows_cell_spectrum(oracle):
+    """Frozen-temperature pass: each absorption re-emits from the full cell
+    spectrum kabs B(T_i) dnu."""
+    F = 16
+    freq = np.geomspace(3e11, 3e15, F)
+    kabs = np.where(freq > 3e14, 40.0, 1e-4)
+    J = np.where(freq > 3e14, 1e-14, 0.0)
+    m = W.CloudModel(name="frz", radii=W.equal_radii(1), rho=np.array([1.0]), length_unit_cm=W.PC_CM,
+                     freq=freq, kabs=kabs, ksca=np.zeros(F), g=np.zeros(F), J_ext=J)
+    T = 60.0
+    r = oracle.run(m, 100_000, 5, mode="frozen", T_frozen=np.array([T]))
+    dnu = oracle.freq_weights(freq)
+    spec = kabs * CF.planck(freq, T) * dnu
+    spec /= spec.sum()
+    low = freq < 1e14
+    got = r["sed"][low] / r["E_abs"].sum()
+    np.testing.assert_allclose(got, spec[low], atol=6e-3)
+
+
+def test_kbg_half_is_the_unweighted_run(oracle):
+    m = W.external_cloud(8, 5.0)
+    a = oracle.run(m, 3000, 4, record=True)
+    b = oracle.run(m.replace(k_bg=0.5), 3000, 4, record=True)
+    assert np.array_equal(a["hash"], b["hash"])
+    assert a["stats"]["E_injected"] == pytest.approx(oracle.source_luminosity(m)[0], rel=1e-13)
+
+
+def test_noise_falls_as_inverse_sqrt_n(oracle):
+    """Brute-force convergence on a two-shell cloud: the seed-to-seed spread of
+    T falls ~N^-1/2 (a factor ~sqrt(16) = 4 from N to 16 N)."""
+    m = W.external_cloud(2, 5.0)
+    s1 = np.std([oracle.run(m, 500, s)["T"] for s in range(24)], axis=0, ddof=1)
+    s2 = np.std([oracle.run(m, 8000, s)["T"] for s in range(24)], axis=0, ddof=1)
+    ratio = s1 / s2
+    assert np.all((ratio > 2.2) & (ratio < 7.0))
+
+
+def test_validation_rejects_bad_models(oracle):
+    m = W.external_cloud(4, 1.0)
+    assert oracle.validate(m) == 0
+    assert oracle.validate(m.replace(radii=m.radii[::-1].copy())) < 0
+    assert oracle.validate(m.replace(rho=-m.rho)) < 0
+    assert oracle.validate(m.replace(g=np.full(m.n_freq, 1.0))) < 0
+    assert oracle.validate(m.replace(J_ext=None)) < 0
+    assert oracle.validate(m.replace(k_bg=0.0)) < 0
+
+
+def test_absorb_reemit_grey_isotropic_invariant(oracle):
+    """With frequency-independent opacity, absorption followed by isotropic
+    re-emission of the same energy acts like isotropic conservative
+    scattering, so the isotropic-field invariant fixes the mean number of
+    absorptions per package: sum_c kabs_c V_c / (pi R^2)."""
+    m = W.grey_model(4, 0.9, albedo=0.0, r_in=0.2)
+    m = m.replace(rho=np.array([2.5, 0.5, 1.2, 0.8]))
+    N = 60_000
+    r = oracle.run(m, N, 8, mode="frozen", T_frozen=np.full(4, 30.0), record=True)
+    n_abs = r["n_events"][:, 1].astype(np.float64)
+    expect = CF.pure_scatterer_mean_events(m.radii, m.kabs[0] * m.rho)
+    assert abs(n_abs.mean() - expect) < 4.5 * n_abs.std() / np.sqrt(N)
