@@ -1,0 +1,238 @@
+/*
+ * dies.h -- C ABI of the GB300 immediate re-emission (IRE) dust radiative
+ * transfer library (Juvela 2024, "DIES: Parallel dust radiative transfer
+ * program with the immediate re-emission method").
+ *
+ * Problem statement (Sect. 2.1): a spherically symmetric cloud of concentric
+ * shells, each with one density; dust absorption and scattering coefficients
+ * and a Henyey-Greenstein asymmetry parameter per frequency; an isotropic
+ * external radiation field and/or a central point source.  The luminosity of
+ * each source is split over N photon packages of equal energy.  Packages are
+ * followed shell by shell with independent free paths for absorption and
+ * scattering (Eqs. 1 and 4); each absorption adds the package energy to its
+ * shell, updates the shell temperature at once and re-emits the same energy
+ * isotropically at a frequency drawn from the difference between the shell's
+ * emission spectra at the new and old temperatures.  Optional weighting:
+ * background directions mu = u^k_bg (Sect. 2.2.1, Eq. 5) and forced first
+ * interaction (Sect. 2.2.2, Eqs. 9-12).
+ *
+ * Conventions shared by every call:
+ *   - All array arguments are HOST pointers unless a name says otherwise.
+ *     Inputs are copied during the call; the caller keeps ownership.
+ *     Outputs are written to caller-allocated host arrays of the stated size.
+ *   - Every call returns a dies_status (0 = success).  On failure the call
+ *     has no effect on the handle, and dies_last_error() returns a
+ *     thread-local, human-readable description.
+ *   - Calls on one handle are not thread-safe; distinct handles are
+ *     independent.  Setters after a run mark the derived tables stale; the
+ *     next run rebuilds them on the device.
+ *   - Units: radii in "length units" (length_unit_cm centimetres each);
+ *     kappa * density is an opacity per length unit; frequencies in Hz;
+ *     intensities in erg s^-1 cm^-2 Hz^-1 sr^-1; luminosities in erg s^-1.
+ *   - Device work is enqueued on the handle's CUDA stream (default: the
+ *     legacy default stream).  dies_run and dies_run_frozen return after the
+ *     stream has completed; dies_run_async only enqueues.
+ */
+#ifndef DIES_H
+#define DIES_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DIES_MAX_FREQ 64      /* frequency bins per package (6-bit index) */
+#define DIES_MAX_SHELLS 65536 /* shells per model */
+#define DIES_MAX_TNODES 4096  /* temperature-table nodes */
+
+typedef enum {
+  DIES_OK = 0,
+  DIES_EINVAL = -1,   /* invalid argument (sizes, ordering, NaN, range) */
+  DIES_ENOMEM = -2,   /* host or device allocation failed, or workspace too small */
+  DIES_ECUDA = -3,    /* a CUDA runtime call failed (no device, launch error, ...) */
+  DIES_ESTATE = -4,   /* call not valid in the handle's state (e.g. run before dust) */
+  DIES_ETIMEOUT = -5, /* the transport kernel hit its wall-clock budget and stopped */
+  DIES_ERANGE = -6    /* a result left its table range with strict range checking on */
+} dies_status;
+
+/* Precision forms of the transport (Sect. 2.3 discusses FP32 only). */
+enum {
+  DIES_PREC_MIXED = 0, /* FP32 stepping and sampling; FP64 crossing distances in the
+                          innermost shells, FP64 absorbed-energy accumulators and
+                          temperature lookup (default) */
+  DIES_PREC_FP32 = 1,  /* everything FP32; absorbed energies in two FP32 counters per
+                          shell (all previous batches + current batch) over n_batches
+                          sequential batches (Sect. 2.3) */
+  DIES_PREC_FP64 = 2   /* FP64 geometry, sampling and accumulation */
+};
+
+/* flags of dies_run_frozen */
+enum {
+  DIES_FROZEN_REEMIT = 0,         /* absorption re-emits from the full cell spectrum */
+  DIES_FROZEN_ABSORB_TERMINAL = 1 /* absorption ends the package (pure-absorber tests) */
+};
+
+typedef struct dies_model dies_model; /* opaque; owned by the library until destroyed */
+typedef struct dies_batch dies_batch; /* opaque; many models in one launch */
+
+/* Counters of the last run (all packages of all sources and models). */
+typedef struct {
+  uint64_t injected;      /* packages started */
+  uint64_t escaped;       /* packages that left through the outer surface */
+  uint64_t absorbed;      /* absorption (+ re-emission) events */
+  uint64_t scattered;     /* scattering events */
+  uint64_t crossed;       /* shell-boundary crossings, including the final exit */
+  uint64_t killed_weight; /* packages ended by the weight floor (Sect. 2.2.1) */
+  uint64_t killed_cap;    /* packages ended by the per-package event cap */
+  uint64_t clamp_hi;      /* absorptions whose energy exceeded the table top */
+  uint64_t forced;        /* packages given a forced first interaction */
+  double E_injected;      /* erg/s carried by injected packages (with weights) */
+  double E_escaped;       /* erg/s leaving the model (SED total) */
+  double E_lost;          /* erg/s of packages ended by the floor or the cap */
+  double E_direct;        /* erg/s of forced packages escaping without interaction */
+  double table_ms;        /* device time of the table build of this run (0 if cached) */
+  double kernel_ms;       /* device time of transport + temperature kernels */
+  uint32_t status_word;   /* device-side error flags (0 = none) */
+  uint32_t launches;      /* kernels launched by this run */
+} dies_stats;
+
+/* ------------------------------------------------------------ one model */
+
+/* Create a model of n_shells shells from n_radii = n_shells + 1 strictly
+ * increasing radii (radii[0] >= 0; r < radii[0] is a transparent void) and
+ * n_shells densities (>= 0, finite) -- Sect. 2.1, one density per shell.
+ * length_unit_cm > 0 converts radii to cm.  Host-only: no CUDA call is made.
+ * Returns DIES_EINVAL on bad sizes or values, DIES_ENOMEM on host OOM. */
+int dies_create_model(const double *radii, int n_radii, const double *densities, int n_shells,
+                      double length_unit_cm, dies_model **out);
+
+/* Dust per frequency (Sect. 2.1, Eq. 4 coefficients; HG phase function of
+ * Sect. 2.2.1): n_freq in [2, DIES_MAX_FREQ] strictly increasing frequencies,
+ * kappa_abs, kappa_sca >= 0 and g in (-1, 1).  Spectral integrals use bin
+ * widths dnu_k = nu_k * (ln-nu width of bin k), the ln-nu width being half
+ * the distance to the two neighbours (the full distance at the two ends). */
+int dies_set_dust(dies_model *m, const double *freq_hz, int n_freq, const double *kappa_abs,
+                  const double *kappa_sca, const double *g);
+
+/* Radiation sources (Sect. 2.1): J_ext[n_freq] isotropic external intensity
+ * (NULL = none) and/or a central point source of luminosity L_point > 0 with
+ * spectral shape point_spectrum[n_freq] (any scale; NULL only if L_point == 0).
+ * At least one source is required.  Call after dies_set_dust. */
+int dies_set_sources(dies_model *m, const double *J_ext, double L_point, const double *point_spectrum);
+
+/* Weighting (Sect. 2.2): background directions mu = u^k_bg with package
+ * weight 2 k_bg mu^(2 - 1/k_bg) (Eq. 5), k_bg in (0, 1], 0.5 = unweighted;
+ * forced_first_interaction != 0 forces one interaction on the first flight
+ * with weight 1 - exp(-tau0) (Eqs. 9-12) and tallies the direct-escape part
+ * exp(-tau0) in the escaping SED. */
+int dies_set_weighting(dies_model *m, double k_bg, int forced_first_interaction);
+
+/* Precision form (DIES_PREC_*) and, for DIES_PREC_FP32, the number of
+ * sequential batches n_batches >= 1 (Sect. 2.3).  fp64_radius: in
+ * DIES_PREC_MIXED, shells whose outer radius is below fp64_radius * R use
+ * FP64 crossing distances (0 = none). */
+int dies_set_precision(dies_model *m, int mode, int n_batches, double fp64_radius);
+
+/* Temperature table: n_nodes in [16, DIES_MAX_TNODES] nodes T_j log-spaced
+ * from T_min to T_max (defaults 2.7 K, 1500 K, 1024).  Temperatures below
+ * T_min are reported as T_min; absorbed energies above the table top are
+ * counted in dies_stats.clamp_hi and reported as T_max. */
+int dies_set_tgrid(dies_model *m, double T_min, double T_max, int n_nodes);
+
+/* CUDA stream for all device work of this handle (cudaStream_t as void*). */
+int dies_set_stream(dies_model *m, void *cuda_stream);
+
+/* Launch shape of the transport kernel: block_size in {64,...,1024}
+ * (multiple of 32), blocks_per_sm >= 0 (0 = occupancy maximum).  Values are
+ * clamped to what the device can keep resident. */
+int dies_set_launch(dies_model *m, int block_size, int blocks_per_sm);
+
+/* Wall-clock budget of one transport launch in seconds (default 120).  A
+ * launch that reaches it stops early and the run returns DIES_ETIMEOUT. */
+int dies_set_time_budget(dies_model *m, double seconds);
+
+/* Device memory.  By default the library allocates its own device memory.
+ * Alternatively the caller provides one device buffer of at least
+ * dies_workspace_bytes() bytes (256-byte aligned, e.g. from a PyTorch
+ * tensor); the caller then owns it and must keep it alive while the handle
+ * uses it.  Call after the setters that fix sizes (create, dust, tgrid). */
+int dies_workspace_bytes(const dies_model *m, size_t *bytes);
+int dies_set_workspace(dies_model *m, void *device_ptr, size_t bytes);
+
+/* Run n_packages packages per active source with Philox seed `seed` (full
+ * IRE transport, Sect. 2.1).  Builds the emission and re-emission tables on
+ * the device when stale, zeroes the accumulators, runs the transport kernel
+ * and the temperature kernel, waits for the stream and reads the counters.
+ * n_packages >= 1.  Errors: DIES_ESTATE (dust/sources missing), DIES_ECUDA,
+ * DIES_ENOMEM, DIES_ETIMEOUT. */
+int dies_run(dies_model *m, uint64_t n_packages, uint64_t seed);
+
+/* As dies_run but only enqueues the work on the handle's stream; results
+ * and counters become readable after the stream completes (the getters
+ * synchronise it). */
+int dies_run_async(dies_model *m, uint64_t n_packages, uint64_t seed);
+
+/* Results of the last run (synchronise the stream first).  n must equal the
+ * number of shells / frequencies.  Temperatures in K from the absorbed energy
+ * per shell by log-log interpolation in the emission table; absorbed energy
+ * per shell in erg/s; escaping SED in erg/s per frequency bin. */
+int dies_get_temperatures(dies_model *m, double *T_out, int n_shells);
+int dies_get_absorbed(dies_model *m, double *E_out, int n_shells);
+int dies_get_escaping_sed(dies_model *m, double *L_out, int n_freq);
+int dies_get_stats(dies_model *m, dies_stats *out);
+
+/* Frozen-temperature transfer pass in FP64 (parity diagnostic): the shell
+ * temperatures are fixed to T_frozen[n_shells] (> 0), an absorption only
+ * tallies its energy and re-emits from the full shell spectrum
+ * kappa_abs B(T_i) dnu (or ends the package with DIES_FROZEN_ABSORB_TERMINAL).
+ * Uses the Philox stream layout of the FP64 form.  Optional per-package
+ * outputs (NULL to skip), package j of active source s at row s*n + j:
+ * n_events_out[rows*3] = (scatterings, absorptions, crossings) and
+ * path_hash_out[rows] = 64-bit FNV-1a hash of the event sequence. */
+int dies_run_frozen(dies_model *m, const double *T_frozen, uint64_t n_packages, uint64_t seed, int flags,
+                    uint32_t *n_events_out, uint64_t *path_hash_out);
+
+void dies_destroy_model(dies_model *m);
+
+/* ------------------------------------------------ batched parameter study */
+
+/* n_models models in one persistent launch.  Model i has shells
+ * [shell_offsets[i], shell_offsets[i+1]) of the concatenated densities array
+ * and radii rows radii[shell_offsets[i] + i ... shell_offsets[i+1] + i]
+ * (n_i + 1 radii per model, concatenated).  source_kind[i] = 1 external
+ * field, 2 point source, 3 both.  All models share one dust table, one
+ * external field and one point-source spectrum/luminosity. */
+int dies_create_batch(int n_models, const int *shell_offsets, const double *radii, const double *densities,
+                      const int *source_kind, double length_unit_cm, dies_batch **out);
+int dies_batch_set_dust(dies_batch *b, const double *freq_hz, int n_freq, const double *kappa_abs,
+                        const double *kappa_sca, const double *g);
+int dies_batch_set_sources(dies_batch *b, const double *J_ext, double L_point, const double *point_spectrum);
+int dies_batch_set_stream(dies_batch *b, void *cuda_stream);
+int dies_batch_set_launch(dies_batch *b, int block_size, int blocks_per_sm);
+int dies_run_batch(dies_batch *b, uint64_t n_packages_per_model, uint64_t seed);
+int dies_run_batch_async(dies_batch *b, uint64_t n_packages_per_model, uint64_t seed);
+/* Results: concatenated per-shell arrays (n_total = shell_offsets[n_models])
+ * and per-model SEDs (n_models * n_freq, model-major). */
+int dies_batch_get_temperatures(dies_batch *b, double *T_out, int n_total_shells);
+int dies_batch_get_escaping_sed(dies_batch *b, double *L_out, int n_values);
+int dies_batch_get_stats(dies_batch *b, dies_stats *out);
+void dies_destroy_batch(dies_batch *b);
+
+/* --------------------------------------------------------------- misc */
+
+/* Thread-local description of the last failure of a call on this thread. */
+const char *dies_last_error(void);
+
+/* Number of kernels this library has launched in this process. */
+uint64_t dies_launch_count(void);
+
+/* Library version string. */
+const char *dies_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DIES_H */

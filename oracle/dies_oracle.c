@@ -652,7 +652,9 @@ static void simulate(orc_ctx *C, int s, uint64_t pkg, uint64_t seed, uint32_t *n
       p.tauA -= ka * l;
       p.tauS -= ks * l;
       if (!do_cross(C, &p, next, l, s)) break;
-    } else if (p.tauS * ka < p.tauA * ks) {
+    } else if (ka <= 0.0 || p.tauS * ka < p.tauA * ks) {
+      /* tau_S ran out first; with no absorption in the cell (ka = 0, only
+       * reachable when tau_A is exactly 0) the interaction is a scattering */
       move(&p, p.tauS / ks);
       do_scatter(C, &p, &rs);
     } else {

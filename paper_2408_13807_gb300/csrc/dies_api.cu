@@ -1,0 +1,866 @@
+// dies_api.cu -- host side of the C ABI declared in include/dies.h.
+//
+// A handle keeps host copies of its inputs, one device workspace holding every
+// table and accumulator, and the results of its last run.  dies_run enqueues,
+// on the handle's stream: (when inputs changed) the table-build kernels, the
+// accumulator resets, the persistent transport kernel (N_B launches plus
+// merges in the FP32 form) and the temperature kernel.
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/dies.h"
+#include "dies_common.cuh"
+
+namespace dies {
+
+static std::atomic<unsigned long long> g_launches{0};
+void launch_counter_add(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+cudaError_t launch_freq_tables(cudaStream_t st, int F, const double *nu, const double *J, const double *spec,
+                               double *dnu, double *src_cdf_d, float *src_cdf_f, double *src_sum);
+cudaError_t launch_node_tables(cudaStream_t st, int F, int n, int n_pow2, double T_min, double T_max,
+                               const double *nu, const double *kabs, const double *dnu, double *Lnode_d,
+                               float *Lnode_f, double *lnT, float *dcdf_f, double *dcdf_d);
+cudaError_t launch_geometry(cudaStream_t st, int n_models, ModelDesc *desc, int n_cells_total, int n_bnd,
+                            const double *radii, const double *rho, double length_unit_cm, const double *src_sum,
+                            double L_point, double *r2d, float *r2f, double *rhod, float *rhof, double *inv_mass,
+                            float *inv_massf);
+cudaError_t launch_frozen_cdf(cudaStream_t st, int n_cells, int F, const double *nu, const double *kabs,
+                              const double *dnu, const double *T, double *cell_cdf);
+size_t transport_smem_bytes(int n_tnodes_pow2);
+cudaError_t launch_transport(int prec, int mode, bool record, const TransportParams &P, int grid, int block,
+                             cudaStream_t st);
+cudaError_t transport_occupancy(int prec, int mode, int block, int n_tnodes_pow2, int *blocks_per_sm);
+cudaError_t launch_finalize(cudaStream_t st, int n_cells, const double *E, const float *Eprev, const float *Ecur,
+                            int fp32, const double *inv_mass, const double *Lnode, const double *lnT, int n,
+                            double *T_out);
+cudaError_t launch_merge(cudaStream_t st, int n_cells, float *Eprev, float *Ecur);
+
+namespace {
+
+thread_local std::string t_error;
+
+int fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  t_error = buf;
+  return code;
+}
+
+#define DIES_CUDA(call)                                                                            \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess) return fail(DIES_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int next_pow2(int n) {
+  int p = 1;
+  while (p < n) p <<= 1;
+  return p;
+}
+
+bool finite_nonneg(const double *a, int n) {
+  for (int i = 0; i < n; ++i)
+    if (!(std::isfinite(a[i]) && a[i] >= 0.0)) return false;
+  return true;
+}
+
+// Offsets (bytes) of every segment of the device workspace.
+struct Layout {
+  size_t desc, radii, rho_in, r2d, r2f, rhod, rhof, inv_mass, inv_massf, E, Eprev, Ecur, T, sed;
+  size_t freq, kabs, ksca, g, J, spec, dnu, src_cdf_d, src_cdf_f, src_sum;
+  size_t Lnode_d, Lnode_f, lnT, dcdf_f, dcdf_d;
+  size_t counters, energies, queue, status;
+  size_t total;
+};
+
+}  // namespace
+
+struct Problem {
+  int n_models = 0;
+  int n_cells = 0;  // total over models
+  std::vector<ModelDesc> desc;
+  std::vector<double> radii, rho;
+  double length_unit_cm = 1.0;
+  int F = 0;
+  std::vector<double> freq, kabs, ksca, g;
+  bool has_dust = false, has_sources = false;
+  bool has_ext = false;
+  std::vector<double> J, spec;
+  double L_point = 0.0;
+  std::vector<int> kind;  // per model: bit 0 external, bit 1 point (batch); 0 = follow the sources
+  double k_bg = 0.5;
+  int ffi = 0;
+  int prec = PREC_MIXED, n_batches = 1;
+  double fp64_radius = 0.0;
+  double T_min = 2.7, T_max = 1500.0;
+  int n_tnodes = 1024;
+  cudaStream_t stream = nullptr;
+  int block = 256, blocks_per_sm = 0;
+  double time_budget_s = 120.0;
+  // device
+  unsigned char *ws = nullptr;
+  size_t ws_bytes = 0;
+  bool ws_owned = false;
+  Layout lay{};
+  bool tables_valid = false;
+  int sm_count = 0;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  bool events_ready = false;
+  bool table_built_this_run = false;
+  bool has_result = false;
+  bool stats_pending = false;
+  unsigned long long launches_at_start = 0;
+  dies_stats stats{};
+
+  ~Problem() {
+    if (ws_owned && ws) cudaFree(ws);
+    for (auto &e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+
+  template <class T>
+  T *at(size_t off) const { return reinterpret_cast<T *>(ws + off); }
+
+  Layout layout() const {
+    Layout L{};
+    size_t o = 0;
+    auto seg = [&](size_t bytes) {
+      size_t r = o;
+      o += align256(bytes);
+      return r;
+    };
+    const size_t nb = (size_t)n_cells + n_models, nc = (size_t)n_cells, nm = (size_t)n_models;
+    const size_t np2 = (size_t)next_pow2(n_tnodes), nt = (size_t)n_tnodes;
+    L.desc = seg(nm * sizeof(ModelDesc));
+    L.radii = seg(nb * 8);
+    L.rho_in = seg(nc * 8);
+    L.r2d = seg(nb * 8);
+    L.r2f = seg(nb * 4);
+    L.rhod = seg(nc * 8);
+    L.rhof = seg(nc * 4);
+    L.inv_mass = seg(nc * 8);
+    L.inv_massf = seg(nc * 4);
+    L.E = seg(nc * 8);
+    L.Eprev = seg(nc * 4);
+    L.Ecur = seg(nc * 4);
+    L.T = seg(nc * 8);
+    L.sed = seg(nm * kMaxFreq * 8);
+    L.freq = seg(kMaxFreq * 8);
+    L.kabs = seg(kMaxFreq * 8);
+    L.ksca = seg(kMaxFreq * 8);
+    L.g = seg(kMaxFreq * 8);
+    L.J = seg(kMaxFreq * 8);
+    L.spec = seg(kMaxFreq * 8);
+    L.dnu = seg(kMaxFreq * 8);
+    L.src_cdf_d = seg(2 * kMaxFreq * 8);
+    L.src_cdf_f = seg(2 * kMaxFreq * 4);
+    L.src_sum = seg(2 * 8);
+    L.Lnode_d = seg(np2 * 8);
+    L.Lnode_f = seg(np2 * 4);
+    L.lnT = seg(np2 * 8);
+    L.dcdf_f = seg(nt * kMaxFreq * 4);
+    L.dcdf_d = seg(nt * kMaxFreq * 8);
+    L.counters = seg(16 * 8);
+    L.energies = seg(8 * 8);
+    L.queue = seg(2 * 8);
+    L.status = seg(4);
+    L.total = o;
+    return L;
+  }
+
+  int source_mask_single() const { return (has_ext ? 1 : 0) | (L_point > 0.0 ? 2 : 0); }
+
+  // Per-model descriptors from the host inputs (work offsets in source slots).
+  void fill_desc() {
+    unsigned long long slot = 0;
+    for (int m = 0; m < n_models; ++m) {
+      ModelDesc &d = desc[m];
+      int mask = kind.empty() || kind[m] == 0 ? source_mask_single() : kind[m];
+      if (!has_ext) mask &= ~1;
+      if (!(L_point > 0.0)) mask &= ~2;
+      d.src_mask = mask;
+      d.n_src = (mask & 1) + ((mask >> 1) & 1);
+      const double *r = radii.data() + d.bnd_off;
+      d.R = r[d.n_cells];
+      d.point_cell = (r[0] > 0.0) ? -1 : 0;
+      int n64 = 0;
+      if (prec == PREC_MIXED && fp64_radius > 0.0)
+        while (n64 < d.n_cells && r[n64 + 1] < fp64_radius * d.R) ++n64;
+      d.n_fp64 = n64;
+      d.pkg_off = slot;
+      slot += (unsigned long long)d.n_src;
+      d.L[0] = d.L[1] = 0.0;
+    }
+  }
+
+  unsigned long long total_slots() const {
+    unsigned long long s = 0;
+    for (const auto &d : desc) s += (unsigned long long)d.n_src;
+    return s;
+  }
+
+  int ensure_device() {
+    if (sm_count == 0) {
+      int dev = 0, count = 0;
+      cudaError_t e = cudaGetDeviceCount(&count);
+      if (e != cudaSuccess || count == 0)
+        return fail(DIES_ECUDA, "no CUDA device available (%s)", cudaGetErrorString(e));
+      DIES_CUDA(cudaGetDevice(&dev));
+      DIES_CUDA(cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev));
+    }
+    if (!events_ready) {
+      for (auto &e : ev) DIES_CUDA(cudaEventCreate(&e));
+      events_ready = true;
+    }
+    const Layout L = layout();
+    if (!ws || L.total > ws_bytes) {
+      if (ws && !ws_owned) return fail(DIES_ENOMEM, "workspace of %zu bytes is smaller than the %zu needed", ws_bytes, L.total);
+      if (ws_owned && ws) {
+        cudaFree(ws);
+        ws = nullptr;
+      }
+      void *p = nullptr;
+      cudaError_t e = cudaMalloc(&p, L.total);
+      if (e != cudaSuccess) return fail(DIES_ENOMEM, "cudaMalloc(%zu) failed: %s", L.total, cudaGetErrorString(e));
+      ws = (unsigned char *)p;
+      ws_bytes = L.total;
+      ws_owned = true;
+      tables_valid = false;
+    }
+    lay = L;
+    return DIES_OK;
+  }
+
+  int upload(size_t off, const void *src, size_t bytes) {
+    if (bytes == 0) return DIES_OK;
+    DIES_CUDA(cudaMemcpyAsync(ws + off, src, bytes, cudaMemcpyHostToDevice, stream));
+    return DIES_OK;
+  }
+
+  int build_tables() {
+    fill_desc();
+    int rc;
+    if ((rc = upload(lay.desc, desc.data(), desc.size() * sizeof(ModelDesc)))) return rc;
+    if ((rc = upload(lay.radii, radii.data(), radii.size() * 8))) return rc;
+    if ((rc = upload(lay.rho_in, rho.data(), rho.size() * 8))) return rc;
+    std::vector<double> pad(6 * kMaxFreq, 0.0);
+    for (int k = 0; k < F; ++k) {
+      pad[0 * kMaxFreq + k] = freq[k];
+      pad[1 * kMaxFreq + k] = kabs[k];
+      pad[2 * kMaxFreq + k] = ksca[k];
+      pad[3 * kMaxFreq + k] = g[k];
+      pad[4 * kMaxFreq + k] = has_ext ? J[k] : 0.0;
+      pad[5 * kMaxFreq + k] = (L_point > 0.0) ? spec[k] : 0.0;
+    }
+    const size_t offs[6] = {lay.freq, lay.kabs, lay.ksca, lay.g, lay.J, lay.spec};
+    for (int i = 0; i < 6; ++i)
+      if ((rc = upload(offs[i], pad.data() + i * kMaxFreq, kMaxFreq * 8))) return rc;
+    DIES_CUDA(launch_freq_tables(stream, F, at<double>(lay.freq), has_ext ? at<double>(lay.J) : nullptr,
+                                 (L_point > 0.0) ? at<double>(lay.spec) : nullptr, at<double>(lay.dnu),
+                                 at<double>(lay.src_cdf_d), at<float>(lay.src_cdf_f), at<double>(lay.src_sum)));
+    DIES_CUDA(launch_node_tables(stream, F, n_tnodes, next_pow2(n_tnodes), T_min, T_max, at<double>(lay.freq),
+                                 at<double>(lay.kabs), at<double>(lay.dnu), at<double>(lay.Lnode_d),
+                                 at<float>(lay.Lnode_f), at<double>(lay.lnT), at<float>(lay.dcdf_f),
+                                 at<double>(lay.dcdf_d)));
+    DIES_CUDA(launch_geometry(stream, n_models, at<ModelDesc>(lay.desc), n_cells, n_cells + n_models,
+                              at<double>(lay.radii), at<double>(lay.rho_in), length_unit_cm, at<double>(lay.src_sum),
+                              L_point, at<double>(lay.r2d), at<float>(lay.r2f), at<double>(lay.rhod),
+                              at<float>(lay.rhof), at<double>(lay.inv_mass), at<float>(lay.inv_massf)));
+    tables_valid = true;
+    return DIES_OK;
+  }
+
+  TransportParams params(int mode, uint64_t n, uint64_t seed) const {
+    TransportParams P{};
+    P.desc = at<ModelDesc>(lay.desc);
+    P.n_models = n_models;
+    P.F = F;
+    P.r2f = at<float>(lay.r2f);
+    P.r2d = at<double>(lay.r2d);
+    P.rhof = at<float>(lay.rhof);
+    P.rhod = at<double>(lay.rhod);
+    P.inv_mass = at<double>(lay.inv_mass);
+    P.inv_massf = at<float>(lay.inv_massf);
+    P.E = at<double>(lay.E);
+    P.Eprev = at<float>(lay.Eprev);
+    P.Ecur = at<float>(lay.Ecur);
+    P.sed = at<double>(lay.sed);
+    P.kabs_d = at<double>(lay.kabs);
+    P.ksca_d = at<double>(lay.ksca);
+    P.g_d = at<double>(lay.g);
+    P.src_cdf_d = at<double>(lay.src_cdf_d);
+    P.Lnode_d = at<double>(lay.Lnode_d);
+    P.Lnode_f = at<float>(lay.Lnode_f);
+    P.dcdf_f = at<float>(lay.dcdf_f);
+    P.dcdf_d = at<double>(lay.dcdf_d);
+    P.n_tnodes = n_tnodes;
+    P.n_tnodes_pow2 = next_pow2(n_tnodes);
+    P.n_per_source = n;
+    P.pkg_begin = 0;
+    P.pkg_len = n;
+    P.total = total_slots() * n;
+    P.seed = seed;
+    P.queue = at<unsigned long long>(lay.queue);
+    P.counters = at<unsigned long long>(lay.counters);
+    P.energies = at<double>(lay.energies);
+    P.status = at<uint32_t>(lay.status);
+    P.k_bg = k_bg;
+    P.ffi = ffi;
+    P.mode = mode;
+    P.max_events = 100000000ULL;
+    P.time_budget_ns = (unsigned long long)(time_budget_s * 1e9);
+    return P;
+  }
+
+  int grid_for(int prec_, int mode, int *grid) {
+    int bps = blocks_per_sm;
+    int occ = 0;
+    DIES_CUDA(transport_occupancy(prec_, mode, block, next_pow2(n_tnodes), &occ));
+    if (occ < 1) return fail(DIES_ECUDA, "transport kernel cannot be resident with block size %d", block);
+    if (bps <= 0 || bps > occ) bps = occ;
+    *grid = sm_count * bps;
+    return DIES_OK;
+  }
+
+  int reset_accumulators() {
+    DIES_CUDA(cudaMemsetAsync(ws + lay.E, 0, (size_t)n_cells * 8, stream));
+    DIES_CUDA(cudaMemsetAsync(ws + lay.Eprev, 0, (size_t)n_cells * 4, stream));
+    DIES_CUDA(cudaMemsetAsync(ws + lay.Ecur, 0, (size_t)n_cells * 4, stream));
+    DIES_CUDA(cudaMemsetAsync(ws + lay.sed, 0, (size_t)n_models * kMaxFreq * 8, stream));
+    DIES_CUDA(cudaMemsetAsync(ws + lay.counters, 0, 16 * 8 + 0, stream));
+    DIES_CUDA(cudaMemsetAsync(ws + lay.energies, 0, 8 * 8, stream));
+    DIES_CUDA(cudaMemsetAsync(ws + lay.queue, 0, 2 * 8, stream));
+    DIES_CUDA(cudaMemsetAsync(ws + lay.status, 0, 4, stream));
+    return DIES_OK;
+  }
+
+  int check_ready() const {
+    if (!has_dust) return fail(DIES_ESTATE, "dust not set (dies_set_dust)");
+    if (!has_sources) return fail(DIES_ESTATE, "sources not set (dies_set_sources)");
+    return DIES_OK;
+  }
+
+  // Enqueue a full IRE run.
+  int enqueue_run(uint64_t n, uint64_t seed) {
+    int rc;
+    if ((rc = check_ready())) return rc;
+    if (n == 0) return fail(DIES_EINVAL, "n_packages must be >= 1");
+    if ((rc = ensure_device())) return rc;
+    launches_at_start = g_launches.load();
+    DIES_CUDA(cudaEventRecord(ev[0], stream));
+    table_built_this_run = false;
+    if (!tables_valid) {
+      if ((rc = build_tables())) return rc;
+      table_built_this_run = true;
+    }
+    DIES_CUDA(cudaEventRecord(ev[1], stream));
+    if ((rc = reset_accumulators())) return rc;
+    int grid;
+    if ((rc = grid_for(prec, MODE_IRE, &grid))) return rc;
+    TransportParams P = params(MODE_IRE, n, seed);
+    const int nb = (prec == PREC_FP32) ? n_batches : 1;
+    const uint64_t per = (n + nb - 1) / nb;
+    for (int b = 0; b < nb; ++b) {
+      const uint64_t begin = (uint64_t)b * per;
+      if (begin >= n) break;
+      const uint64_t len = (begin + per <= n) ? per : n - begin;
+      P.pkg_begin = begin;
+      P.pkg_len = len;
+      P.total = total_slots() * len;
+      P.queue = at<unsigned long long>(lay.queue) + (b & 1);
+      if (b > 0) DIES_CUDA(cudaMemsetAsync(P.queue, 0, 8, stream));
+      DIES_CUDA(launch_transport(prec, MODE_IRE, false, P, grid, block, stream));
+      if (prec == PREC_FP32) DIES_CUDA(launch_merge(stream, n_cells, at<float>(lay.Eprev), at<float>(lay.Ecur)));
+    }
+    DIES_CUDA(launch_finalize(stream, n_cells, at<double>(lay.E), at<float>(lay.Eprev), at<float>(lay.Ecur),
+                              prec == PREC_FP32, at<double>(lay.inv_mass), at<double>(lay.Lnode_d),
+                              at<double>(lay.lnT), n_tnodes, at<double>(lay.T)));
+    DIES_CUDA(cudaEventRecord(ev[2], stream));
+    has_result = true;
+    stats_pending = true;
+    return DIES_OK;
+  }
+
+  // Wait for the stream and collect the counters of the last run.
+  int collect() {
+    if (!has_result) return fail(DIES_ESTATE, "no run has completed on this handle");
+    DIES_CUDA(cudaStreamSynchronize(stream));
+    if (!stats_pending) return (stats.status_word & STATUS_TIMEOUT) ? DIES_ETIMEOUT : DIES_OK;
+    unsigned long long cnt[16];
+    double en[8];
+    uint32_t status = 0;
+    std::vector<double> sed((size_t)n_models * kMaxFreq);
+    DIES_CUDA(cudaMemcpy(cnt, ws + lay.counters, sizeof cnt, cudaMemcpyDeviceToHost));
+    DIES_CUDA(cudaMemcpy(en, ws + lay.energies, sizeof en, cudaMemcpyDeviceToHost));
+    DIES_CUDA(cudaMemcpy(&status, ws + lay.status, 4, cudaMemcpyDeviceToHost));
+    DIES_CUDA(cudaMemcpy(sed.data(), ws + lay.sed, sed.size() * 8, cudaMemcpyDeviceToHost));
+    dies_stats s{};
+    s.injected = cnt[CNT_INJECTED];
+    s.escaped = cnt[CNT_ESCAPED];
+    s.absorbed = cnt[CNT_ABSORB];
+    s.scattered = cnt[CNT_SCATTER];
+    s.crossed = cnt[CNT_CROSS];
+    s.killed_weight = cnt[CNT_KILL_WEIGHT];
+    s.killed_cap = cnt[CNT_KILL_CAP];
+    s.clamp_hi = cnt[CNT_CLAMP_HI];
+    s.forced = cnt[CNT_FORCED];
+    s.E_injected = en[EN_INJECTED];
+    s.E_lost = en[EN_LOST];
+    s.E_direct = en[EN_DIRECT];
+    double esc = 0.0;
+    for (double v : sed) esc += v;
+    s.E_escaped = esc;
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess) s.table_ms = table_built_this_run ? ms : 0.0;
+    if (cudaEventElapsedTime(&ms, ev[1], ev[2]) == cudaSuccess) s.kernel_ms = ms;
+    s.status_word = status;
+    s.launches = (uint32_t)(g_launches.load() - launches_at_start);
+    stats = s;
+    stats_pending = false;
+    if (status & STATUS_TIMEOUT) return fail(DIES_ETIMEOUT, "transport kernel stopped at its time budget");
+    return DIES_OK;
+  }
+
+  int frozen(const double *T_frozen, uint64_t n, uint64_t seed, int flags, uint32_t *ev_out, uint64_t *hash_out) {
+    int rc;
+    if ((rc = check_ready())) return rc;
+    if (n == 0) return fail(DIES_EINVAL, "n_packages must be >= 1");
+    if (!T_frozen) return fail(DIES_EINVAL, "T_frozen is NULL");
+    for (int i = 0; i < n_cells; ++i)
+      if (!(std::isfinite(T_frozen[i]) && T_frozen[i] > 0.0))
+        return fail(DIES_EINVAL, "T_frozen[%d] must be finite and > 0", i);
+    if (flags != DIES_FROZEN_REEMIT && flags != DIES_FROZEN_ABSORB_TERMINAL)
+      return fail(DIES_EINVAL, "unknown frozen flags %d", flags);
+    if ((rc = ensure_device())) return rc;
+    launches_at_start = g_launches.load();
+    DIES_CUDA(cudaEventRecord(ev[0], stream));
+    table_built_this_run = false;
+    if (!tables_valid) {
+      if ((rc = build_tables())) return rc;
+      table_built_this_run = true;
+    }
+    DIES_CUDA(cudaEventRecord(ev[1], stream));
+    const unsigned long long rows = total_slots() * n;
+    double *dT = nullptr, *dcdf = nullptr;
+    uint32_t *dev = nullptr;
+    unsigned long long *dhash = nullptr;
+    auto release = [&]() {
+      if (dT) cudaFree(dT);
+      if (dcdf) cudaFree(dcdf);
+      if (dev) cudaFree(dev);
+      if (dhash) cudaFree(dhash);
+    };
+    cudaError_t e = cudaMalloc(&dT, (size_t)n_cells * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&dcdf, (size_t)n_cells * kMaxFreq * 8);
+    if (e == cudaSuccess && ev_out) e = cudaMalloc(&dev, rows * 3 * 4);
+    if (e == cudaSuccess && hash_out) e = cudaMalloc(&dhash, rows * 8);
+    if (e != cudaSuccess) {
+      release();
+      return fail(DIES_ENOMEM, "frozen-pass buffers: %s", cudaGetErrorString(e));
+    }
+    rc = DIES_OK;
+    do {
+      if ((e = cudaMemcpyAsync(dT, T_frozen, (size_t)n_cells * 8, cudaMemcpyHostToDevice, stream))) break;
+      if ((e = launch_frozen_cdf(stream, n_cells, F, at<double>(lay.freq), at<double>(lay.kabs), at<double>(lay.dnu),
+                                 dT, dcdf)))
+        break;
+      if ((rc = reset_accumulators())) break;
+      int grid;
+      if ((rc = grid_for(PREC_FP64, MODE_FROZEN, &grid))) break;
+      const int mode = (flags == DIES_FROZEN_ABSORB_TERMINAL) ? MODE_FROZEN_TERMINAL : MODE_FROZEN;
+      TransportParams P = params(mode, n, seed);
+      P.cell_cdf = dcdf;
+      P.rec_events = dev;
+      P.rec_hash = dhash;
+      if ((e = launch_transport(PREC_FP64, mode, ev_out || hash_out, P, grid, block, stream))) break;
+      if ((e = cudaMemcpyAsync(ws + lay.T, dT, (size_t)n_cells * 8, cudaMemcpyDeviceToDevice, stream))) break;
+      if ((e = cudaEventRecord(ev[2], stream))) break;
+      has_result = true;
+      stats_pending = true;
+      if ((rc = collect())) break;
+      if (ev_out && (e = cudaMemcpy(ev_out, dev, rows * 3 * 4, cudaMemcpyDeviceToHost))) break;
+      if (hash_out && (e = cudaMemcpy(hash_out, dhash, rows * 8, cudaMemcpyDeviceToHost))) break;
+    } while (0);
+    release();
+    if (e != cudaSuccess) return fail(DIES_ECUDA, "frozen pass: %s", cudaGetErrorString(e));
+    return rc;
+  }
+
+  int get_cells(size_t off, double *out, int n) {
+    if (!out) return fail(DIES_EINVAL, "output pointer is NULL");
+    if (n != n_cells) return fail(DIES_EINVAL, "expected %d shells, got %d", n_cells, n);
+    int rc = collect();
+    if (rc && rc != DIES_ETIMEOUT) return rc;
+    DIES_CUDA(cudaMemcpy(out, ws + off, (size_t)n * 8, cudaMemcpyDeviceToHost));
+    return rc;
+  }
+
+  int get_sed(double *out, int n) {
+    if (!out) return fail(DIES_EINVAL, "output pointer is NULL");
+    if (n != n_models * F) return fail(DIES_EINVAL, "expected %d values, got %d", n_models * F, n);
+    int rc = collect();
+    if (rc && rc != DIES_ETIMEOUT) return rc;
+    std::vector<double> tmp((size_t)n_models * kMaxFreq);
+    DIES_CUDA(cudaMemcpy(tmp.data(), ws + lay.sed, tmp.size() * 8, cudaMemcpyDeviceToHost));
+    for (int m = 0; m < n_models; ++m)
+      for (int k = 0; k < F; ++k) out[(size_t)m * F + k] = tmp[(size_t)m * kMaxFreq + k];
+    return rc;
+  }
+
+  // -------------------------------------------------------------- setters
+  int set_dust(const double *nu, int n, const double *ka, const double *ks, const double *gg) {
+    if (!nu || !ka || !ks || !gg) return fail(DIES_EINVAL, "dust arrays must not be NULL");
+    if (n < 2 || n > DIES_MAX_FREQ) return fail(DIES_EINVAL, "n_freq must be in [2, %d], got %d", DIES_MAX_FREQ, n);
+    for (int k = 0; k < n; ++k) {
+      if (!(std::isfinite(nu[k]) && nu[k] > 0.0)) return fail(DIES_EINVAL, "freq_hz[%d] must be finite and > 0", k);
+      if (k > 0 && !(nu[k] > nu[k - 1])) return fail(DIES_EINVAL, "freq_hz must be strictly increasing");
+      if (!(std::isfinite(ka[k]) && ka[k] >= 0.0)) return fail(DIES_EINVAL, "kappa_abs[%d] must be finite and >= 0", k);
+      if (!(std::isfinite(ks[k]) && ks[k] >= 0.0)) return fail(DIES_EINVAL, "kappa_sca[%d] must be finite and >= 0", k);
+      if (!(std::fabs(gg[k]) < 1.0)) return fail(DIES_EINVAL, "g[%d] must lie in (-1, 1)", k);
+    }
+    if (has_sources && n != F) has_sources = false;  // source spectra no longer match
+    F = n;
+    freq.assign(nu, nu + n);
+    kabs.assign(ka, ka + n);
+    ksca.assign(ks, ks + n);
+    g.assign(gg, gg + n);
+    has_dust = true;
+    tables_valid = false;
+    return DIES_OK;
+  }
+
+  int set_sources(const double *Jx, double Lp, const double *sp) {
+    if (!has_dust) return fail(DIES_ESTATE, "call dies_set_dust before dies_set_sources");
+    if (!std::isfinite(Lp) || Lp < 0.0) return fail(DIES_EINVAL, "L_point must be finite and >= 0");
+    if (!Jx && !(Lp > 0.0)) return fail(DIES_EINVAL, "at least one source (J_ext or L_point > 0) is required");
+    if (Lp > 0.0 && !sp) return fail(DIES_EINVAL, "point_spectrum is required when L_point > 0");
+    double sj = 0.0, ss = 0.0;
+    if (Jx) {
+      if (!finite_nonneg(Jx, F)) return fail(DIES_EINVAL, "J_ext must be finite and >= 0");
+      for (int k = 0; k < F; ++k) sj += Jx[k];
+      if (!(sj > 0.0)) return fail(DIES_EINVAL, "J_ext is zero at every frequency");
+    }
+    if (Lp > 0.0) {
+      if (!finite_nonneg(sp, F)) return fail(DIES_EINVAL, "point_spectrum must be finite and >= 0");
+      for (int k = 0; k < F; ++k) ss += sp[k];
+      if (!(ss > 0.0)) return fail(DIES_EINVAL, "point_spectrum is zero at every frequency");
+    }
+    has_ext = Jx != nullptr;
+    J.assign(Jx ? Jx : sp, (Jx ? Jx : sp) + (Jx ? F : 0));
+    L_point = Lp;
+    spec.assign(sp ? sp : Jx, (sp ? sp : Jx) + ((Lp > 0.0) ? F : 0));
+    has_sources = true;
+    tables_valid = false;
+    return DIES_OK;
+  }
+};
+
+}  // namespace dies
+
+using dies::fail;
+using dies::Problem;
+
+struct dies_model {
+  Problem p;
+};
+struct dies_batch {
+  Problem p;
+};
+
+namespace {
+
+int check_geometry(const double *radii, int n_radii, const double *rho, int n_shells, double lu) {
+  if (!radii || !rho) return fail(DIES_EINVAL, "radii and densities must not be NULL");
+  if (n_shells < 1 || n_shells > DIES_MAX_SHELLS)
+    return fail(DIES_EINVAL, "n_shells must be in [1, %d], got %d", DIES_MAX_SHELLS, n_shells);
+  if (n_radii != n_shells + 1) return fail(DIES_EINVAL, "n_radii must equal n_shells + 1");
+  if (!(std::isfinite(radii[0]) && radii[0] >= 0.0)) return fail(DIES_EINVAL, "radii[0] must be finite and >= 0");
+  for (int i = 0; i < n_shells; ++i) {
+    if (!(std::isfinite(radii[i + 1]) && radii[i + 1] > radii[i]))
+      return fail(DIES_EINVAL, "radii must be finite and strictly increasing (index %d)", i + 1);
+    if (!(std::isfinite(rho[i]) && rho[i] >= 0.0))
+      return fail(DIES_EINVAL, "densities[%d] must be finite and >= 0", i);
+  }
+  if (!(std::isfinite(lu) && lu > 0.0)) return fail(DIES_EINVAL, "length_unit_cm must be finite and > 0");
+  return DIES_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dies_create_model(const double *radii, int n_radii, const double *densities, int n_shells,
+                      double length_unit_cm, dies_model **out) {
+  if (!out) return fail(DIES_EINVAL, "out is NULL");
+  *out = nullptr;
+  int rc = check_geometry(radii, n_radii, densities, n_shells, length_unit_cm);
+  if (rc) return rc;
+  dies_model *m = new (std::nothrow) dies_model();
+  if (!m) return fail(DIES_ENOMEM, "host allocation failed");
+  Problem &p = m->p;
+  p.n_models = 1;
+  p.n_cells = n_shells;
+  p.radii.assign(radii, radii + n_radii);
+  p.rho.assign(densities, densities + n_shells);
+  p.length_unit_cm = length_unit_cm;
+  p.desc.resize(1);
+  p.desc[0] = dies::ModelDesc{};
+  p.desc[0].cell_off = 0;
+  p.desc[0].bnd_off = 0;
+  p.desc[0].n_cells = n_shells;
+  *out = m;
+  return DIES_OK;
+}
+
+int dies_set_dust(dies_model *m, const double *freq_hz, int n_freq, const double *kappa_abs,
+                  const double *kappa_sca, const double *g) {
+  if (!m) return fail(DIES_EINVAL, "model is NULL");
+  return m->p.set_dust(freq_hz, n_freq, kappa_abs, kappa_sca, g);
+}
+
+int dies_set_sources(dies_model *m, const double *J_ext, double L_point, const double *point_spectrum) {
+  if (!m) return fail(DIES_EINVAL, "model is NULL");
+  return m->p.set_sources(J_ext, L_point, point_spectrum);
+}
+
+int dies_set_weighting(dies_model *m, double k_bg, int ffi) {
+  if (!m) return fail(DIES_EINVAL, "model is NULL");
+  if (!(k_bg > 0.0 && k_bg <= 1.0)) return fail(DIES_EINVAL, "k_bg must lie in (0, 1]");
+  m->p.k_bg = k_bg;
+  m->p.ffi = ffi ? 1 : 0;
+  return DIES_OK;
+}
+
+int dies_set_precision(dies_model *m, int mode, int n_batches, double fp64_radius) {
+  if (!m) return fail(DIES_EINVAL, "model is NULL");
+  if (mode != DIES_PREC_MIXED && mode != DIES_PREC_FP32 && mode != DIES_PREC_FP64)
+    return fail(DIES_EINVAL, "unknown precision mode %d", mode);
+  if (n_batches < 1 || n_batches > 1000000) return fail(DIES_EINVAL, "n_batches must be in [1, 1e6]");
+  if (!(fp64_radius >= 0.0 && fp64_radius <= 1.0)) return fail(DIES_EINVAL, "fp64_radius must lie in [0, 1]");
+  m->p.prec = mode;
+  m->p.n_batches = n_batches;
+  if (m->p.fp64_radius != fp64_radius) m->p.tables_valid = false;
+  m->p.fp64_radius = fp64_radius;
+  m->p.tables_valid = false;
+  return DIES_OK;
+}
+
+int dies_set_tgrid(dies_model *m, double T_min, double T_max, int n_nodes) {
+  if (!m) return fail(DIES_EINVAL, "model is NULL");
+  if (!(std::isfinite(T_min) && std::isfinite(T_max) && T_min > 0.0 && T_max > T_min))
+    return fail(DIES_EINVAL, "need 0 < T_min < T_max");
+  if (n_nodes < 16 || n_nodes > DIES_MAX_TNODES) return fail(DIES_EINVAL, "n_nodes must be in [16, %d]", DIES_MAX_TNODES);
+  m->p.T_min = T_min;
+  m->p.T_max = T_max;
+  m->p.n_tnodes = n_nodes;
+  m->p.tables_valid = false;
+  return DIES_OK;
+}
+
+int dies_set_stream(dies_model *m, void *s) {
+  if (!m) return fail(DIES_EINVAL, "model is NULL");
+  m->p.stream = (cudaStream_t)s;
+  return DIES_OK;
+}
+
+static int set_launch(Problem &p, int block, int bps) {
+  if (block < 64 || block > 256 || block % 32) return fail(DIES_EINVAL, "block_size must be a multiple of 32 in [64, 256]");
+  if (bps < 0) return fail(DIES_EINVAL, "blocks_per_sm must be >= 0");
+  p.block = block;
+  p.blocks_per_sm = bps;
+  return DIES_OK;
+}
+
+int dies_set_launch(dies_model *m, int block_size, int blocks_per_sm) {
+  if (!m) return fail(DIES_EINVAL, "model is NULL");
+  return set_launch(m->p, block_size, blocks_per_sm);
+}
+
+int dies_set_time_budget(dies_model *m, double seconds) {
+  if (!m) return fail(DIES_EINVAL, "model is NULL");
+  if (!(seconds > 0.0 && seconds < 1e6)) return fail(DIES_EINVAL, "time budget must lie in (0, 1e6) s");
+  m->p.time_budget_s = seconds;
+  return DIES_OK;
+}
+
+int dies_workspace_bytes(const dies_model *m, size_t *bytes) {
+  if (!m || !bytes) return fail(DIES_EINVAL, "NULL argument");
+  *bytes = m->p.layout().total;
+  return DIES_OK;
+}
+
+int dies_set_workspace(dies_model *m, void *ptr, size_t bytes) {
+  if (!m || !ptr) return fail(DIES_EINVAL, "NULL argument");
+  if (((uintptr_t)ptr & 255u) != 0) return fail(DIES_EINVAL, "workspace must be 256-byte aligned");
+  const size_t need = m->p.layout().total;
+  if (bytes < need) return fail(DIES_ENOMEM, "workspace of %zu bytes is smaller than the %zu needed", bytes, need);
+  Problem &p = m->p;
+  if (p.ws_owned && p.ws) cudaFree(p.ws);
+  p.ws = (unsigned char *)ptr;
+  p.ws_bytes = bytes;
+  p.ws_owned = false;
+  p.tables_valid = false;
+  p.has_result = false;
+  return DIES_OK;
+}
+
+int dies_run_async(dies_model *m, uint64_t n, uint64_t seed) {
+  if (!m) return fail(DIES_EINVAL, "model is NULL");
+  return m->p.enqueue_run(n, seed);
+}
+
+int dies_run(dies_model *m, uint64_t n, uint64_t seed) {
+  int rc = dies_run_async(m, n, seed);
+  if (rc) return rc;
+  return m->p.collect();
+}
+
+int dies_get_temperatures(dies_model *m, double *T, int n) {
+  if (!m) return fail(DIES_EINVAL, "model is NULL");
+  return m->p.get_cells(m->p.lay.T, T, n);
+}
+
+int dies_get_absorbed(dies_model *m, double *E, int n) {
+  if (!m) return fail(DIES_EINVAL, "model is NULL");
+  Problem &p = m->p;
+  if (p.prec == DIES_PREC_FP32 && p.has_result) {
+    // FP32 form: the absorbed energy is the sum of the two FP32 counters
+    if (!E) return fail(DIES_EINVAL, "output pointer is NULL");
+    if (n != p.n_cells) return fail(DIES_EINVAL, "expected %d shells, got %d", p.n_cells, n);
+    int rc = p.collect();
+    if (rc && rc != DIES_ETIMEOUT) return rc;
+    std::vector<float> a(n), b(n);
+    DIES_CUDA(cudaMemcpy(a.data(), p.ws + p.lay.Eprev, (size_t)n * 4, cudaMemcpyDeviceToHost));
+    DIES_CUDA(cudaMemcpy(b.data(), p.ws + p.lay.Ecur, (size_t)n * 4, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < n; ++i) E[i] = (double)a[i] + (double)b[i];
+    return rc;
+  }
+  return p.get_cells(p.lay.E, E, n);
+}
+
+int dies_get_escaping_sed(dies_model *m, double *L, int n) {
+  if (!m) return fail(DIES_EINVAL, "model is NULL");
+  return m->p.get_sed(L, n);
+}
+
+int dies_get_stats(dies_model *m, dies_stats *out) {
+  if (!m || !out) return fail(DIES_EINVAL, "NULL argument");
+  int rc = m->p.collect();
+  if (rc && rc != DIES_ETIMEOUT) return rc;
+  *out = m->p.stats;
+  return rc;
+}
+
+int dies_run_frozen(dies_model *m, const double *T_frozen, uint64_t n, uint64_t seed, int flags,
+                    uint32_t *n_events_out, uint64_t *path_hash_out) {
+  if (!m) return fail(DIES_EINVAL, "model is NULL");
+  return m->p.frozen(T_frozen, n, seed, flags, n_events_out, path_hash_out);
+}
+
+void dies_destroy_model(dies_model *m) { delete m; }
+
+// ------------------------------------------------------------------ batch
+int dies_create_batch(int n_models, const int *off, const double *radii, const double *rho, const int *kind,
+                      double length_unit_cm, dies_batch **out) {
+  if (!out) return fail(DIES_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n_models < 1 || !off || !radii || !rho || !kind) return fail(DIES_EINVAL, "invalid batch arguments");
+  if (off[0] != 0) return fail(DIES_EINVAL, "shell_offsets[0] must be 0");
+  for (int i = 0; i < n_models; ++i) {
+    const int n = off[i + 1] - off[i];
+    int rc = check_geometry(radii + off[i] + i, n + 1, rho + off[i], n, length_unit_cm);
+    if (rc) return fail(rc, "model %d: %s", i, dies_last_error());
+    if (kind[i] < 1 || kind[i] > 3) return fail(DIES_EINVAL, "source_kind[%d] must be 1, 2 or 3", i);
+  }
+  dies_batch *b = new (std::nothrow) dies_batch();
+  if (!b) return fail(DIES_ENOMEM, "host allocation failed");
+  Problem &p = b->p;
+  p.n_models = n_models;
+  p.n_cells = off[n_models];
+  p.radii.assign(radii, radii + off[n_models] + n_models);
+  p.rho.assign(rho, rho + off[n_models]);
+  p.kind.assign(kind, kind + n_models);
+  p.length_unit_cm = length_unit_cm;
+  p.desc.resize(n_models);
+  for (int i = 0; i < n_models; ++i) {
+    p.desc[i] = dies::ModelDesc{};
+    p.desc[i].cell_off = off[i];
+    p.desc[i].bnd_off = off[i] + i;
+    p.desc[i].n_cells = off[i + 1] - off[i];
+  }
+  *out = b;
+  return DIES_OK;
+}
+
+int dies_batch_set_dust(dies_batch *b, const double *freq_hz, int n_freq, const double *ka, const double *ks,
+                        const double *g) {
+  if (!b) return fail(DIES_EINVAL, "batch is NULL");
+  return b->p.set_dust(freq_hz, n_freq, ka, ks, g);
+}
+
+int dies_batch_set_sources(dies_batch *b, const double *J_ext, double L_point, const double *spec) {
+  if (!b) return fail(DIES_EINVAL, "batch is NULL");
+  return b->p.set_sources(J_ext, L_point, spec);
+}
+
+int dies_batch_set_stream(dies_batch *b, void *s) {
+  if (!b) return fail(DIES_EINVAL, "batch is NULL");
+  b->p.stream = (cudaStream_t)s;
+  return DIES_OK;
+}
+
+int dies_batch_set_launch(dies_batch *b, int block_size, int blocks_per_sm) {
+  if (!b) return fail(DIES_EINVAL, "batch is NULL");
+  return set_launch(b->p, block_size, blocks_per_sm);
+}
+
+int dies_run_batch_async(dies_batch *b, uint64_t n, uint64_t seed) {
+  if (!b) return fail(DIES_EINVAL, "batch is NULL");
+  return b->p.enqueue_run(n, seed);
+}
+
+int dies_run_batch(dies_batch *b, uint64_t n, uint64_t seed) {
+  int rc = dies_run_batch_async(b, n, seed);
+  if (rc) return rc;
+  return b->p.collect();
+}
+
+int dies_batch_get_temperatures(dies_batch *b, double *T, int n) {
+  if (!b) return fail(DIES_EINVAL, "batch is NULL");
+  return b->p.get_cells(b->p.lay.T, T, n);
+}
+
+int dies_batch_get_escaping_sed(dies_batch *b, double *L, int n) {
+  if (!b) return fail(DIES_EINVAL, "batch is NULL");
+  return b->p.get_sed(L, n);
+}
+
+int dies_batch_get_stats(dies_batch *b, dies_stats *out) {
+  if (!b || !out) return fail(DIES_EINVAL, "NULL argument");
+  int rc = b->p.collect();
+  if (rc && rc != DIES_ETIMEOUT) return rc;
+  *out = b->p.stats;
+  return rc;
+}
+
+void dies_destroy_batch(dies_batch *b) { delete b; }
+
+const char *dies_last_error(void) { return dies::t_error.c_str(); }
+
+uint64_t dies_launch_count(void) { return dies::g_launches.load(); }
+
+const char *dies_version(void) { return "dies-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,185 @@
+// dies_common.cuh -- device-side data layout and helpers shared by the
+// kernels of the IRE library (tables, transport, temperature).
+//
+// Layout in HBM (one contiguous workspace per handle, 256-byte aligned
+// segments; see workspace_layout() in dies_api.cu):
+//   per model      ModelDesc (geometry offsets, source luminosities)
+//   per boundary   R^2 as float and double (n_cells + 1 per model)
+//   per cell       density (float, double), 1/(4 pi rho V L_u^2) (double),
+//                  absorbed energy (double, or two floats for the FP32 form)
+//   per frequency  dnu, kappa_abs, kappa_sca, g, source CDFs
+//   per T node     Lambda_j = sum_k kappa_k B_k(T_j) dnu_k (float, double),
+//                  ln T_j, and one re-emission CDF row of 64 entries
+//                  (difference spectrum of the interval ending at node j)
+// Everything the transport kernel reads per event is a few KB per model and
+// stays in L1/L2; the per-frequency and per-node tables are staged in shared
+// memory by every CTA.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dies {
+
+constexpr int kMaxFreq = 64;
+constexpr int kFreqShift = 6;  // row stride of the re-emission CDF table
+
+enum Prec { PREC_MIXED = 0, PREC_FP32 = 1, PREC_FP64 = 2 };
+enum Mode { MODE_IRE = 0, MODE_FROZEN = 1, MODE_FROZEN_TERMINAL = 2 };
+
+// event codes folded into the per-package path hash
+enum { EV_INJECT = 0, EV_CROSS = 1, EV_SCATTER = 2, EV_ABSORB = 3 };
+
+// indices of the u64 counter block
+enum {
+  CNT_INJECTED = 0, CNT_ESCAPED, CNT_ABSORB, CNT_SCATTER, CNT_CROSS, CNT_KILL_WEIGHT, CNT_KILL_CAP,
+  CNT_CLAMP_HI, CNT_FORCED, CNT_COUNT
+};
+// indices of the double energy block
+enum { EN_INJECTED = 0, EN_LOST, EN_DIRECT, EN_COUNT };
+
+// device status flags
+enum : uint32_t {
+  STATUS_TIMEOUT = 1u,
+  STATUS_BAD_CELL = 2u,
+  STATUS_BAD_FREQ = 4u,
+};
+
+struct alignas(16) ModelDesc {
+  int cell_off;    // first cell of this model in the per-cell arrays
+  int bnd_off;     // first boundary of this model in the per-boundary arrays
+  int n_cells;
+  int src_mask;    // bit 0: external field, bit 1: point source
+  int n_src;
+  int point_cell;  // start cell of point-source packages (-1 = central void)
+  int n_fp64;      // MIXED form: cells [0, n_fp64) use FP64 crossing distances
+  int pad0;
+  double R;        // outer radius (length units)
+  double L[2];     // source luminosities (erg/s), written by the table build
+  unsigned long long pkg_off;  // first source slot of this model (slots x packages = work items)
+};
+
+struct TransportParams {
+  // geometry
+  const ModelDesc *desc;
+  int n_models;
+  int F;
+  const float *r2f;         // boundary radius^2
+  const double *r2d;
+  const float *rhof;        // cell density
+  const double *rhod;
+  const double *inv_mass;   // 1 / (4 pi rho V L_u^2)
+  const float *inv_massf;
+  // accumulators
+  double *E;                // absorbed energy (MIXED / FP64 forms and frozen tallies)
+  const float *Eprev;       // FP32 form: all previous batches (read only in a batch)
+  float *Ecur;              // FP32 form: current batch
+  double *sed;              // [n_models][F]
+  // per-frequency tables
+  const double *kabs_d, *ksca_d, *g_d;
+  const double *src_cdf_d;  // [2][kMaxFreq]
+  // temperature tables
+  const double *Lnode_d;    // [n_tnodes]
+  const float *Lnode_f;
+  const float *dcdf_f;      // [n_tnodes][kMaxFreq]
+  const double *dcdf_d;
+  int n_tnodes;
+  int n_tnodes_pow2;        // smallest power of two >= n_tnodes
+  // frozen pass
+  const double *cell_cdf;   // [n_cells][kMaxFreq]
+  uint32_t *rec_events;     // [rows][3] or null
+  unsigned long long *rec_hash;  // [rows] or null
+  // work
+  unsigned long long total;       // work items (packages) in this launch
+  unsigned long long pkg_begin;   // first package index of every source in this launch
+  unsigned long long pkg_len;     // packages per source in this launch
+  unsigned long long n_per_source;  // packages per source in the whole run (sets eps)
+  unsigned long long seed;
+  unsigned long long *queue;
+  unsigned long long *counters;   // [CNT_COUNT]
+  double *energies;               // [EN_COUNT]
+  uint32_t *status;
+  // options
+  double k_bg;
+  int ffi;
+  int mode;
+  unsigned long long max_events;
+  unsigned long long time_budget_ns;
+};
+
+// ------------------------------------------------------------------ Philox
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32->64 multiplications by 0xD2511F53 / 0xCD9E8D57 with the high halves
+// xored into the other words and the round key; the key advances by the Weyl
+// increments 0x9E3779B9 / 0xBB67AE85 between rounds.
+struct U4 {
+  uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ U4 philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                       uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c0;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2);
+    const uint32_t n0 = hi1 ^ c1 ^ k0;
+    const uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+  return U4{c0, c1, c2, c3};
+}
+
+// Per-package stream: key = seed, counter = (package lo, package hi, block, model ^ source << 24).
+struct Stream {
+  uint32_t k0, k1, c0, c1, c3;
+  uint32_t blk;
+  __device__ __forceinline__ U4 next() {
+    U4 r = philox10(c0, c1, blk, c3, k0, k1);
+    ++blk;
+    return r;
+  }
+};
+
+// double in (0,1): top 52 bits of a word pair, (m + 1/2) 2^-52 (exact, never 0 or 1)
+__device__ __forceinline__ double u01d(uint32_t a, uint32_t b) {
+  const unsigned long long m = ((unsigned long long)a << 20) | (unsigned long long)(b >> 12);
+  return ((double)m + 0.5) * 0x1p-52;
+}
+
+// float in (0,1): 23 bits, (m + 1/2) 2^-23 (exact, never 0 or 1)
+__device__ __forceinline__ float u01f(uint32_t m23) { return ((float)m23 + 0.5f) * 0x1p-23f; }
+__device__ __forceinline__ float u01f_word(uint32_t w) { return u01f(w >> 9); }
+
+// float in (0,1) with full relative precision near 0 (for 1 - mu^2 of the
+// injection directions): (w + 1/2) 2^-32 rounded to float, capped below 1.
+__device__ __forceinline__ float u01f_fine(uint32_t w) {
+  float v = fmaf(__uint2float_rn(w), 0x1p-32f, 0x1p-33f);
+  return fminf(v, 1.0f - 0x1p-24f);
+}
+
+// ---------------------------------------------------------------- FNV-1a
+__device__ __forceinline__ unsigned long long fnv_word(unsigned long long h, uint32_t w) {
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    h ^= (unsigned long long)((w >> (8 * b)) & 0xffu);
+    h *= 0x100000001b3ULL;
+  }
+  return h;
+}
+__device__ __forceinline__ uint32_t event_word(int ev, int cell, int f) {
+  return (uint32_t)ev | ((uint32_t)(cell + 1) << 3) | ((uint32_t)f << 24);
+}
+
+// ----------------------------------------------------------- host helpers
+void launch_counter_add(unsigned n);
+
+}  // namespace dies

@@ -1,0 +1,141 @@
+"""The C-ABI library loads, exports every symbol include/dies.h declares, and
+validates its inputs on the host (no compute call needs a GPU here)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2408_13807_gb300 import build as B
+from paper_2408_13807_gb300 import dies as D
+from paper_2408_13807_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return D.load()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "dies.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(dies_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_the_binding_names():
+    assert declared_functions() == sorted(D.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    assert D.dies_version().startswith("dies-gb300")
+    assert D.dies_launch_count() >= 0
+
+
+def test_create_and_set_validate_inputs(lib):
+    m = W.config1()
+    h = D.dies_create_model(m.radii, m.rho, m.length_unit_cm)
+    try:
+        D.dies_set_dust(h, m.freq, m.kabs, m.ksca, m.g)
+        D.dies_set_sources(h, m.J_ext, 0.0, None)
+        D.dies_set_weighting(h, 1.0 / 3.0, True)
+        D.dies_set_precision(h, D.DIES_PREC_FP32, 50, 0.0)
+        D.dies_set_tgrid(h, 2.7, 1500.0, 1024)
+        D.dies_set_launch(h, 128, 0)
+        assert D.dies_workspace_bytes(h) > 0
+        bad = [
+            lambda: D.dies_set_dust(h, m.freq[::-1], m.kabs, m.ksca, m.g),
+            lambda: D.dies_set_dust(h, m.freq[:1], m.kabs[:1], m.ksca[:1], m.g[:1]),
+            lambda: D.dies_set_dust(h, np.geomspace(1e11, 1e15, 65), *(np.ones(65),) * 2, np.zeros(65)),
+            lambda: D.dies_set_dust(h, m.freq, m.kabs, m.ksca, np.full(m.n_freq, 1.0)),
+            lambda: D.dies_set_dust(h, m.freq, -m.kabs, m.ksca, m.g),
+            lambda: D.dies_set_sources(h, None, 0.0, None),
+            lambda: D.dies_set_sources(h, None, 1e33, None),
+            lambda: D.dies_set_sources(h, -m.J_ext, 0.0, None),
+            lambda: D.dies_set_weighting(h, 0.0, False),
+            lambda: D.dies_set_weighting(h, 1.5, False),
+            lambda: D.dies_set_precision(h, 7, 1, 0.0),
+            lambda: D.dies_set_precision(h, 1, 0, 0.0),
+            lambda: D.dies_set_tgrid(h, 10.0, 5.0, 1024),
+            lambda: D.dies_set_tgrid(h, 2.7, 1500.0, 8),
+            lambda: D.dies_set_launch(h, 100, 0),
+        ]
+        for call in bad:
+            with pytest.raises(D.DiesError) as e:
+                call()
+            assert e.value.code == D.DIES_EINVAL
+            assert D.dies_last_error()
+    finally:
+        D.dies_destroy_model(h)
+
+
+@pytest.mark.parametrize("case", ["descending", "nan", "negative_rho", "size", "r0_negative", "unit"])
+def test_create_rejects_bad_geometry(lib, case):
+    r = np.linspace(0.0, 1.0, 9)
+    rho = np.ones(8)
+    lu = 1.0
+    if case == "descending":
+        r = r[::-1].copy()
+    elif case == "nan":
+        r[3] = np.nan
+    elif case == "negative_rho":
+        rho[2] = -1.0
+    elif case == "size":
+        rho = np.ones(9)
+    elif case == "r0_negative":
+        r = r - 0.5
+    elif case == "unit":
+        lu = 0.0
+    with pytest.raises(D.DiesError) as e:
+        D.dies_create_model(r, rho, lu)
+    assert e.value.code == D.DIES_EINVAL
+
+
+def test_state_errors(lib):
+    m = W.config1()
+    h = D.dies_create_model(m.radii, m.rho, 1.0)
+    try:
+        with pytest.raises(D.DiesError) as e:
+            D.dies_set_sources(h, m.J_ext, 0.0, None)
+        assert e.value.code == D.DIES_ESTATE
+        with pytest.raises(D.DiesError) as e:
+            D.dies_run(h, 10, 0)
+        assert e.value.code == D.DIES_ESTATE
+    finally:
+        D.dies_destroy_model(h)
+
+
+def test_batch_validation(lib):
+    ms = W.config4_models(3, seed=1)
+    off = np.concatenate([[0], np.cumsum([c.n_cells for c in ms])])
+    radii = np.concatenate([c.radii for c in ms])
+    rho = np.concatenate([c.rho for c in ms])
+    h = D.dies_create_batch(off, radii, rho, [1, 2, 3], 1.0)
+    D.dies_destroy_batch(h)
+    with pytest.raises(D.DiesError):
+        D.dies_create_batch(off, radii, rho, [1, 0, 3], 1.0)
+    bad = radii.copy()
+    bad[off[1] + 1 + 2] = -1.0
+    with pytest.raises(D.DiesError):
+        D.dies_create_batch(off, bad, rho, [1, 1, 1], 1.0)
+
+
+def test_run_without_gpu_fails_loudly(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    m = W.external_cloud(4, 1.0)
+    h = D.dies_create_model(m.radii, m.rho, m.length_unit_cm)
+    try:
+        D.dies_set_dust(h, m.freq, m.kabs, m.ksca, m.g)
+        D.dies_set_sources(h, m.J_ext, 0.0, None)
+        with pytest.raises(D.DiesError) as e:
+            D.dies_run(h, 100, 0)
+        assert e.value.code in (D.DIES_ECUDA, D.DIES_ENOMEM)
+    finally:
+        D.dies_destroy_model(h)

@@ -1,0 +1,156 @@
+"""GPU parity: the CUDA library against the FP64 CPU oracle, through the C ABI.
+
+Frozen-temperature pass: same Philox streams, identical per-package event
+counts and path hashes, absorbed energies within 1e-5 relative.
+Full IRE: per-shell temperatures within 1 % and within the combined standard
+error over 16 seeds.
+"""
+import numpy as np
+import pytest
+
+import closed_forms as CF
+from gpu_util import assert_ensembles_agree
+from paper_2408_13807_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def D():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2408_13807_gb300 import build as B
+    B.build()
+    from paper_2408_13807_gb300 import dies
+    dies.load()
+    return dies
+
+
+FROZEN_CASES = {
+    "C1_external": lambda: W.config1(),
+    "kbg_third": lambda: W.external_cloud(24, 20.0, k_bg=1.0 / 3.0),
+    "ffi_thin": lambda: W.external_cloud(20, 0.3, ffi=True),
+    "point_log_void": lambda: W.point_source_cloud(40, 1e-3, 30.0),
+    "grey_void_scatter": lambda: W.grey_model(7, 3.0, albedo=0.6, g=0.7, r_in=0.2),
+    "both_sources": lambda: W.external_cloud(12, 5.0).replace(L_point=W.L_SUN, point_spec=W.blackbody(W.freq_grid(), 6000.0)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(FROZEN_CASES))
+@pytest.mark.parametrize("terminal", [False, True])
+def test_frozen_pass_bit_exact(D, oracle, name, terminal):
+    cloud = FROZEN_CASES[name]()
+    n = cloud.n_cells
+    T = np.linspace(8.0, 40.0, n)
+    N = 20_000
+    m = D.Model(cloud, precision="fp64")
+    ev, hs = m.run_frozen(T, N, seed=17, terminal=terminal)
+    ref = oracle.run(cloud, N, 17, mode="frozen_terminal" if terminal else "frozen", T_frozen=T, record=True)
+    mism = np.nonzero(np.any(ev != ref["n_events"], axis=1) | (hs != ref["hash"]))[0]
+    assert mism.size == 0, f"{mism.size} packages differ, first rows {mism[:5]}"
+    E_g = m.absorbed()
+    np.testing.assert_allclose(E_g, ref["E_abs"], rtol=1e-5, atol=1e-12 * ref["E_abs"].max())
+    np.testing.assert_allclose(m.sed(), ref["sed"], rtol=1e-5, atol=1e-12 * ref["sed"].max())
+    st = m.stats()
+    assert st["escaped"] == ref["stats"]["escaped"]
+    assert st["absorbed"] == ref["stats"]["absorb"]
+    assert st["scattered"] == ref["stats"]["scatter"]
+    assert st["crossed"] == ref["stats"]["cross"]
+
+
+def test_frozen_pass_ragged_sizes(D, oracle):
+    """Package counts that do not fill the persistent grid or a warp."""
+    cloud = W.external_cloud(9, 4.0)
+    T = np.full(9, 15.0)
+    for N in (1, 31, 33, 1000, 77_777):
+        m = D.Model(cloud, precision="fp64")
+        ev, hs = m.run_frozen(T, N, seed=N)
+        ref = oracle.run(cloud, N, N, mode="frozen", T_frozen=T, record=True)
+        assert np.array_equal(ev, ref["n_events"]) and np.array_equal(hs, ref["hash"]), N
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_ire_config1_matches_oracle_16_seeds(D, oracle, prec):
+    cloud = W.config1()
+    N = 1_000_000
+    Tg = np.array([D.Model(cloud, precision=prec).run(N, seed=s).temperatures() for s in range(16)])
+    To = np.array([r["T"] for r in oracle.run_seeds(cloud, N, range(100, 116))])
+    r = assert_ensembles_agree(Tg, To, 0.01, min_gated=cloud.n_cells // 2)
+    print(f"{prec}: max rel (gated) {r['max_rel_gated']:.4f}, max z {r['max_z']:.2f}, gated {r['gated'].sum()}")
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64", "fp32"])
+def test_energy_conservation_and_counts(D, prec):
+    for cloud in (W.config1(), W.external_cloud(64, 30.0, k_bg=0.2), W.external_cloud(32, 0.5, ffi=True),
+                  W.point_source_cloud(64, 1e-3, 50.0)):
+        m = D.Model(cloud, precision=prec, n_batches=4)
+        m.run(200_000, seed=5)
+        st = m.stats()
+        assert st["injected"] == 200_000
+        assert st["escaped"] + st["killed_weight"] + st["killed_cap"] <= 200_000
+        assert st["E_escaped"] + st["E_lost"] == pytest.approx(st["E_injected"], rel=1e-9)
+        assert m.sed().sum() == pytest.approx(st["E_escaped"], rel=1e-12)
+        if cloud.k_bg == 0.5 and not cloud.ffi:
+            assert st["escaped"] == 200_000
+        assert st["status_word"] == 0
+
+
+def test_optically_thin_limit_gpu(D):
+    m0 = W.external_cloud(6, 1e-3, ffi=True)
+    cloud = m0.replace(rho=np.full(6, m0.rho.mean()))
+    T_thin = CF.thin_limit_temperature(cloud.freq, cloud.kabs, cloud.J_ext)
+    T = D.Model(cloud, precision="mixed").run(2_000_000, seed=2).temperatures()
+    assert np.all(np.abs(T / T_thin - 1.0) < 0.01), (T, T_thin)
+
+
+def test_empty_cloud_sed_is_the_source(D, oracle):
+    """Zero density everywhere: every package leaves at its injected frequency;
+    the FP64 form uses the oracle's streams, so the SEDs agree to rounding."""
+    cloud = W.config1()
+    cloud = cloud.replace(rho=np.zeros(cloud.n_cells))
+    m = D.Model(cloud, precision="fp64").run(100_000, seed=4)
+    ref = oracle.run(cloud, 100_000, 4)
+    np.testing.assert_allclose(m.sed(), ref["sed"], rtol=1e-12, atol=1e-14 * ref["sed"].max())
+    assert np.all(m.temperatures() == pytest.approx(2.7))
+    assert m.stats()["absorbed"] == 0
+
+
+def test_single_shell_and_single_package(D, oracle):
+    cloud = W.grey_model(1, 1.0, albedo=0.3, g=0.5)
+    T = np.array([20.0])
+    for N in (1, 2, 5):
+        m = D.Model(cloud, precision="fp64")
+        ev, hs = m.run_frozen(T, N, seed=9)
+        ref = oracle.run(cloud, N, 9, mode="frozen", T_frozen=T, record=True)
+        assert np.array_equal(ev, ref["n_events"]) and np.array_equal(hs, ref["hash"])
+    m = D.Model(cloud, precision="mixed").run(1, seed=0)
+    st = m.stats()
+    assert st["injected"] == 1 and st["escaped"] == 1
+
+
+def test_fp32_form_matches_oracle_with_batches(D, oracle):
+    cloud = W.config1()
+    N = 1_000_000
+    Tg = np.array([D.Model(cloud, precision="fp32", n_batches=50).run(N, seed=s).temperatures() for s in range(16)])
+    To = np.array([r["T"] for r in oracle.run_seeds(cloud, N, range(200, 216))])
+    assert_ensembles_agree(Tg, To, 0.01, min_gated=cloud.n_cells // 2)
+
+
+def test_batch_matches_single_model_runs(D, oracle):
+    """A parameter-study batch gives each model the same answer as a run of
+    that model alone (ensembles over 8 seeds), and conserves energy."""
+    clouds = W.config4_models(6, seed=11)
+    N = 200_000
+    Tb = []
+    for s in range(8):
+        b = D.Batch(clouds).run(N, seed=s)
+        Tb.append(b.temperatures())
+        st = b.stats()
+        assert st["E_escaped"] + st["E_lost"] == pytest.approx(st["E_injected"], rel=1e-9)
+        assert st["injected"] == N * len(clouds)
+    Tb = np.array(Tb)
+    off = np.concatenate([[0], np.cumsum([c.n_cells for c in clouds])])
+    for i, c in enumerate(clouds):
+        To = np.array([r["T"] for r in oracle.run_seeds(c, N, range(300, 308))])
+        assert_ensembles_agree(Tb[:, off[i]:off[i + 1]], To, 0.02, min_gated=0)
