@@ -1,0 +1,391 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the IRE transport on GB300.
+
+Workload (one "step"): the externally heated sweep of 128 equal shells with
+central A_V in {1, 10, 100}, each run plain, with centre-biased background
+directions (k_bg = 1/3) and with forced first interaction: 9 runs of 1e8
+packages = 9e8 packages per step, mixed precision (FP32 stepping, FP64
+inner-shell crossings, accumulators and temperature lookup).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  ``value`` is packages/s with every input
+already resident on the device; ``e2e`` is the same metric through the public
+API from host arrays (model creation, uploads, table build, run, read-back).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "IRE photon packages/s and batched models/s at <=1% T error vs FP64 oracle"
+UNIT = "packages/s"
+N_PER_RUN = 100_000_000
+L2_FLUSH_BYTES = 256 << 20
+
+# Algorithmic thread-level operations per event (minimum instruction counts of
+# the method's arithmetic, derived in the design doc): boundary crossing, scattering
+# (one Philox4x32-10 block + HG + rotation), absorption (one Philox block, FP64
+# atomic, table searches, isotropic re-emission) and per-package injection/exit.
+OPS = {"crossed": 20, "scattered": 120, "absorbed": 150, "injected": 120}
+SM_COUNT = 152
+LANES_PER_SM = 128  # 4 schedulers x 32 lanes issue per cycle
+
+
+def workload_clouds():
+    from paper_2408_13807_gb300 import workloads as W
+    return W.config2_sweep()
+
+
+def workload_config(n_per_run):
+    return {
+        "workload": "externally heated sweep: 128 equal shells, BE-like density, central A_V in {1,10,100} "
+                    "x {plain, k_bg=1/3 (p'(mu)~mu^2), forced first interaction}, 64 frequencies, "
+                    f"{n_per_run:.0e} packages per run, 9 runs per step",
+        "packages_per_step": 9 * n_per_run,
+        "precision": "mixed (FP32 stepping/sampling, FP64 accumulators, temperature lookup, inner crossings)",
+        "l2": "flushed between steps (256 MB device write)",
+        "inputs": "synthetic (seeded stand-ins for the paper's Bonnor-Ebert clouds, dust and field)",
+    }
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        if not self.rows:
+            return None
+        try:
+            sm = [float(r[1]) for r in self.rows]
+            mx = max(float(r[2]) for r in self.rows)
+        except ValueError:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": reasons, "samples": len(sm)}
+
+
+# ----------------------------------------------------------- distributed
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def init_dist(world, backend):
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend=backend)
+        return dist
+    return None
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, x: float, device=None) -> float:
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- oracle
+def oracle_rate(clouds, seconds_target: float, seed0: int = 1000):
+    """Packages/s of the serial FP64 oracle on a bounded sample of the same
+    runs (one thread), sized to take about ``seconds_target`` seconds."""
+    from oracle import oracle as O
+    O.build()
+    n_cal = 2000
+    t = time.perf_counter()
+    for i, c in enumerate(clouds):
+        O.run(c, n_cal, seed0 + i)
+    per_pkg = (time.perf_counter() - t) / (n_cal * len(clouds))
+    n = max(2000, int(seconds_target / (per_pkg * len(clouds))))
+    t = time.perf_counter()
+    for i, c in enumerate(clouds):
+        O.run(c, n, seed0 + 100 + i)
+    dt = time.perf_counter() - t
+    return n * len(clouds) / dt, n, dt
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    clouds = workload_clouds()
+    for _ in range(args.warmup):
+        oracle_rate(clouds, 0.5)
+    rates, dts, n = [], [], 0
+    for _ in range(args.steps):
+        r, n, dt = oracle_rate(clouds, args.ref_seconds)
+        rates.append(r)
+        dts.append(dt)
+    value = len(clouds) * n * len(rates) / sum(dts)
+    cfg = workload_config(N_PER_RUN)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(dts) / len(dts),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": cfg,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{n} packages per run x 9 runs per step (serial FP64 oracle, one thread)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ ours
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2408_13807_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profile():
+    """DRAM bytes per transport launch from the committed ncu summary, if it
+    was taken on the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "transport_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        rec = json.load(open(p))
+    except ValueError:
+        return None
+    if rec.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return rec.get("dram_bytes_per_launch_full_size")
+
+
+def accuracy_vs_oracle(T_runs):
+    """Largest relative deviation of the step-averaged GPU temperatures from
+    the stored oracle means, on shells where the oracle's 3-sigma is < 1 %."""
+    p = os.path.join(ROOT, "tests", "golden", "c2_sweep_oracle.npz")
+    if not os.path.exists(p) or not T_runs:
+        return None
+    g = np.load(p)
+    worst = 0.0
+    for i, T in enumerate(T_runs):
+        mo, so = g["mean"][i], g["se"][i]
+        gate = 3.0 * so <= 0.01 * mo
+        if gate.any():
+            worst = max(worst, float(np.max(np.abs(np.mean(T, axis=0)[gate] / mo[gate] - 1.0))))
+    return worst
+
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = init_dist(world, "nccl")
+    from paper_2408_13807_gb300 import build as B
+    if rank == 0:
+        B.build()
+    barrier(dist)
+    B.build()
+    from paper_2408_13807_gb300 import dies as D
+
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    clouds = workload_clouds()
+    if args.runs:
+        clouds = [clouds[int(i)] for i in args.runs.split(",")]
+    n = args.n_per_run
+    models = [D.Model(c, precision="mixed", fp64_radius=args.fp64_radius, block_size=args.block,
+                      blocks_per_sm=args.blocks_per_sm) for c in clouds]
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    seed_base = 1_000_000 * rank
+
+    def step(seed):
+        for i, m in enumerate(models):
+            D.dies_run_async(m.h, n, seed * 16 + i)
+
+    for w in range(args.warmup):
+        step(seed_base + w)
+    torch.cuda.synchronize()
+
+    # ---- device-timed region: inputs resident, per-step CUDA events on the library's stream
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(dist)
+    torch.cuda.synchronize()
+    launches0 = D.dies_launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    transport_ms, stats_acc, T_runs = [], {k: 0 for k in OPS}, [[] for _ in models]
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        step(seed_base + 100 + k)
+        ev[k][1].record(stream)
+        for i, m in enumerate(models):
+            st = m.stats()
+            transport_ms.append(st["transport_ms"])
+            for key in OPS:
+                stats_acc[key] += st[key]
+            if st["status_word"] != 0:
+                raise RuntimeError(f"device status {st['status_word']} in run {i}")
+            T_runs[i].append(m.temperatures())
+    torch.cuda.synchronize()
+    barrier(dist)
+    launches = D.dies_launch_count() - launches0
+    clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = max_over_ranks(dist, sum(step_ms), dev)
+    pk_step = len(models) * n
+    value = world * pk_step * args.steps / (total_ms * 1e-3)
+
+    # ---- end-to-end through the public API, host arrays in and out
+    e2e_dts, h2d, d2h = [], 0, 0
+    barrier(dist)
+    for k in range(0 if args.no_e2e else max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        h2d = d2h = 0
+        for i, c in enumerate(clouds):
+            m = D.Model(c, precision="mixed", fp64_radius=args.fp64_radius)
+            m.run(n, seed=seed_base + 500 + 16 * k + i)
+            T, sed = m.temperatures(), m.sed()
+            h2d += (c.radii.nbytes + c.rho.nbytes + 6 * 64 * 8 + 64)
+            d2h += T.nbytes + 2 * sed.nbytes + 16 * 8 + 8 * 8 + 4
+            m.close()
+        torch.cuda.synchronize()
+        e2e_dts.append(time.perf_counter() - t)
+    e2e_value = None
+    if e2e_dts:
+        e2e_dt = max_over_ranks(dist, statistics.median(e2e_dts), dev)
+        e2e_value = world * pk_step / e2e_dt
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    # ---- roofline of the dominant kernel (transport): algorithmic ops / launch time
+    ops = sum(OPS[k] * stats_acc[k] for k in OPS)
+    t_transport = sum(transport_ms) * 1e-3
+    achieved = ops / t_transport / 1e9
+    peaks = {}
+    pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pp):
+        peaks = json.load(open(pp))
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = SM_COUNT * LANES_PER_SM * sm_max * 1e6 / 1e9
+    launches_per_step = launches / args.steps
+    traffic = traffic_from_profile()
+
+    cpu_rate, cpu_n, cpu_dt = oracle_rate(clouds, args.ref_seconds) if not args.no_cpu_baseline else (None, 0, 0)
+    cfg = workload_config(n)
+    if args.runs:
+        cfg["workload"] = "subset of runs " + args.runs + " of: " + cfg["workload"]
+        cfg["packages_per_step"] = pk_step
+    cfg["parallelism"] = f"replicas x{world}" if world > 1 else "single GPU"
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": cfg,
+        "roofline": {
+            "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
+            "traffic": traffic,
+            "kernel": "k_transport<MIXED,IRE> (persistent IRE transport)",
+            "peak_source": f"derived issue peak: {SM_COUNT} SMs x {LANES_PER_SM} lanes x {sm_max:.0f} MHz",
+            "ops_per_event": OPS,
+            "transport_share_of_step": t_transport / (sum(step_ms) * 1e-3),
+        },
+        "cpu_baseline": None if cpu_rate is None else {
+            "value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{cpu_n} packages of each of the 9 runs (serial FP64 oracle, one thread, {cpu_dt:.1f} s)"},
+        "e2e": None if e2e_value is None else {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                                               "d2h_bytes_per_step": d2h},
+        "clocks": clocks.summary(),
+        "gpu_launches": launches,
+        "gpu_launches_per_step": launches_per_step,
+        "events_per_s": (stats_acc["crossed"] + stats_acc["scattered"] + stats_acc["absorbed"]) / t_transport,
+        "atomics_per_s": stats_acc["absorbed"] / t_transport,
+        "events_per_package": {k: stats_acc[k] / max(1, stats_acc["injected"]) for k in ("crossed", "scattered", "absorbed")},
+        "max_rel_T_error_vs_oracle": accuracy_vs_oracle(T_runs),
+    }
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n-per-run", type=int, default=N_PER_RUN)
+    ap.add_argument("--ref-seconds", type=float, default=15.0)
+    ap.add_argument("--block", type=int, default=256)
+    ap.add_argument("--blocks-per-sm", type=int, default=0)
+    ap.add_argument("--fp64-radius", type=float, default=0.05)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--runs", default="", help="comma-separated indices of the 9 sweep runs (profiling cases)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

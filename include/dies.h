@@ -93,7 +93,8 @@ typedef struct {
   double E_lost;          /* erg/s of packages ended by the floor or the cap */
   double E_direct;        /* erg/s of forced packages escaping without interaction */
   double table_ms;        /* device time of the table build of this run (0 if cached) */
-  double kernel_ms;       /* device time of transport + temperature kernels */
+  double kernel_ms;       /* device time from the accumulator reset to the end of the temperature kernel */
+  double transport_ms;    /* device time of the transport launch(es) alone */
   uint32_t status_word;   /* device-side error flags (0 = none) */
   uint32_t launches;      /* kernels launched by this run */
 } dies_stats;

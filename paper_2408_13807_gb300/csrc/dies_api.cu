@@ -116,7 +116,7 @@ struct Problem {
   Layout lay{};
   bool tables_valid = false;
   int sm_count = 0;
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   bool events_ready = false;
   bool table_built_this_run = false;
   bool has_result = false;
@@ -370,6 +370,7 @@ struct Problem {
     int grid;
     if ((rc = grid_for(prec, MODE_IRE, &grid))) return rc;
     TransportParams P = params(MODE_IRE, n, seed);
+    DIES_CUDA(cudaEventRecord(ev[2], stream));
     const int nb = (prec == PREC_FP32) ? n_batches : 1;
     const uint64_t per = (n + nb - 1) / nb;
     for (int b = 0; b < nb; ++b) {
@@ -384,10 +385,11 @@ struct Problem {
       DIES_CUDA(launch_transport(prec, MODE_IRE, false, P, grid, block, stream));
       if (prec == PREC_FP32) DIES_CUDA(launch_merge(stream, n_cells, at<float>(lay.Eprev), at<float>(lay.Ecur)));
     }
+    DIES_CUDA(cudaEventRecord(ev[3], stream));
     DIES_CUDA(launch_finalize(stream, n_cells, at<double>(lay.E), at<float>(lay.Eprev), at<float>(lay.Ecur),
                               prec == PREC_FP32, at<double>(lay.inv_mass), at<double>(lay.Lnode_d),
                               at<double>(lay.lnT), n_tnodes, at<double>(lay.T)));
-    DIES_CUDA(cudaEventRecord(ev[2], stream));
+    DIES_CUDA(cudaEventRecord(ev[4], stream));
     has_result = true;
     stats_pending = true;
     return DIES_OK;
@@ -424,7 +426,8 @@ struct Problem {
     s.E_escaped = esc;
     float ms = 0.0f;
     if (cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess) s.table_ms = table_built_this_run ? ms : 0.0;
-    if (cudaEventElapsedTime(&ms, ev[1], ev[2]) == cudaSuccess) s.kernel_ms = ms;
+    if (cudaEventElapsedTime(&ms, ev[1], ev[4]) == cudaSuccess) s.kernel_ms = ms;
+    if (cudaEventElapsedTime(&ms, ev[2], ev[3]) == cudaSuccess) s.transport_ms = ms;
     s.status_word = status;
     s.launches = (uint32_t)(g_launches.load() - launches_at_start);
     stats = s;
@@ -479,14 +482,16 @@ struct Problem {
       if ((rc = reset_accumulators())) break;
       int grid;
       if ((rc = grid_for(PREC_FP64, MODE_FROZEN, &grid))) break;
+      if ((e = cudaEventRecord(ev[2], stream))) break;
       const int mode = (flags == DIES_FROZEN_ABSORB_TERMINAL) ? MODE_FROZEN_TERMINAL : MODE_FROZEN;
       TransportParams P = params(mode, n, seed);
       P.cell_cdf = dcdf;
       P.rec_events = dev;
       P.rec_hash = dhash;
       if ((e = launch_transport(PREC_FP64, mode, ev_out || hash_out, P, grid, block, stream))) break;
+      if ((e = cudaEventRecord(ev[3], stream))) break;
       if ((e = cudaMemcpyAsync(ws + lay.T, dT, (size_t)n_cells * 8, cudaMemcpyDeviceToDevice, stream))) break;
-      if ((e = cudaEventRecord(ev[2], stream))) break;
+      if ((e = cudaEventRecord(ev[4], stream))) break;
       has_result = true;
       stats_pending = true;
       if ((rc = collect())) break;

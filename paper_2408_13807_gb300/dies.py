@@ -59,6 +59,7 @@ class dies_stats(ctypes.Structure):
         ("killed_cap", ctypes.c_uint64), ("clamp_hi", ctypes.c_uint64), ("forced", ctypes.c_uint64),
         ("E_injected", ctypes.c_double), ("E_escaped", ctypes.c_double), ("E_lost", ctypes.c_double),
         ("E_direct", ctypes.c_double), ("table_ms", ctypes.c_double), ("kernel_ms", ctypes.c_double),
+        ("transport_ms", ctypes.c_double),
         ("status_word", ctypes.c_uint32), ("launches", ctypes.c_uint32),
     ]
 
