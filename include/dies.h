@@ -197,6 +197,33 @@ int dies_run_frozen(dies_model *m, const double *T_frozen, uint64_t n_packages, 
 
 void dies_destroy_model(dies_model *m);
 
+/* Frozen-temperature pass that allocates no device memory.  The paper has no
+ * counterpart: this entry point serves callers that cannot call cudaMalloc
+ * (code running while a stream is being captured, plug-ins whose host
+ * application owns all device memory, allocators that forbid side
+ * allocations).  It computes exactly what dies_run_frozen computes, but every
+ * input and output is a caller-owned DEVICE pointer and the pass's scratch
+ * (per-shell re-emission CDFs, work counter, event counters) lives in one
+ * fixed array inside the library, DIES_STATIC_SCRATCH_BYTES bytes on every
+ * GPU that loads it, kept until the process exits.
+ *   T_frozen_dev  [n_shells] shell temperatures (> 0), device memory
+ *   E_abs_dev     [n_shells] out: absorbed energy per shell (erg/s)
+ *   sed_dev       [n_freq]   out: escaping luminosity per bin (erg/s)
+ *   n_events_dev  [rows*3]   out or NULL, path_hash_dev [rows] out or NULL,
+ *                 rows = n_packages * active sources (layout of dies_run_frozen)
+ * Requirements: n_shells <= DIES_STATIC_MAX_SHELLS (else DIES_EINVAL); the
+ * handle must already hold its device workspace and tables, i.e. one
+ * dies_run / dies_run_async must have completed set-up on it (else
+ * DIES_ESTATE).  The call only enqueues work on the handle's stream.  Its
+ * first call on a device looks up the scratch array's device address; make
+ * that first call before any stream capture.  All calls share the one
+ * scratch array, so calls whose work overlaps on the GPU (other streams,
+ * other threads) race and must be serialised by the caller. */
+#define DIES_STATIC_MAX_SHELLS 4096
+#define DIES_STATIC_SCRATCH_BYTES (DIES_STATIC_MAX_SHELLS * 64 * 8 + 4096)
+int dies_run_frozen_static(dies_model *m, const double *T_frozen_dev, uint64_t n_packages, uint64_t seed, int flags,
+                           double *E_abs_dev, double *sed_dev, uint32_t *n_events_dev, uint64_t *path_hash_dev);
+
 /* ------------------------------------------------ batched parameter study */
 
 /* n_models models in one persistent launch.  Model i has shells

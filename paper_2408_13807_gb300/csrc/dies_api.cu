@@ -776,6 +776,95 @@ int dies_run_frozen(dies_model *m, const double *T_frozen, uint64_t n, uint64_t 
 
 void dies_destroy_model(dies_model *m) { delete m; }
 
+}  // extern "C"
+
+// ------------------------------------------------ frozen pass, no allocation
+// Scratch of dies_run_frozen_static: the per-shell re-emission CDF rows, then
+// the work counter, event counters, energy sums and status word.  Host code
+// must not use the symbol as an address; it looks the device address up once
+// per device below.
+namespace {
+constexpr size_t kStaticCdfBytes = (size_t)DIES_STATIC_MAX_SHELLS * dies::kMaxFreq * 8;
+constexpr size_t kStaticCounters = kStaticCdfBytes;         // 16 x u64
+constexpr size_t kStaticEnergies = kStaticCdfBytes + 128;   // 8 x double
+constexpr size_t kStaticQueue = kStaticCdfBytes + 192;      // 2 x u64
+constexpr size_t kStaticStatus = kStaticCdfBytes + 208;     // u32
+constexpr size_t kStaticZeroBytes = 256;                    // counters .. status
+static_assert(kStaticCdfBytes + kStaticZeroBytes <= DIES_STATIC_SCRATCH_BYTES, "static scratch too small");
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_static_scratch[DIES_STATIC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+unsigned char *g_static_addr[kMaxDevices];
+std::atomic<int> g_static_ready[kMaxDevices];
+
+// Device address of the scratch array on the current device (looked up on the
+// first call per device).
+int static_scratch(unsigned char **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(DIES_ECUDA, "cudaGetDevice failed: %s", cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return fail(DIES_ECUDA, "device index %d out of range", dev);
+  if (g_static_ready[dev].load(std::memory_order_acquire) == 0) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || p == nullptr)
+      return fail(DIES_ECUDA, "cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(e));
+    g_static_addr[dev] = (unsigned char *)p;
+    g_static_ready[dev].store(1, std::memory_order_release);
+  }
+  *out = g_static_addr[dev];
+  return DIES_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int dies_run_frozen_static(dies_model *m, const double *T_frozen_dev, uint64_t n, uint64_t seed, int flags,
+                           double *E_abs_dev, double *sed_dev, uint32_t *n_events_dev, uint64_t *path_hash_dev) {
+  using namespace dies;
+  if (!m) return fail(DIES_EINVAL, "model is NULL");
+  Problem &p = m->p;
+  if (!T_frozen_dev || !E_abs_dev || !sed_dev) return fail(DIES_EINVAL, "T_frozen_dev, E_abs_dev and sed_dev are required");
+  if (n == 0) return fail(DIES_EINVAL, "n_packages must be >= 1");
+  if (flags != DIES_FROZEN_REEMIT && flags != DIES_FROZEN_ABSORB_TERMINAL)
+    return fail(DIES_EINVAL, "unknown frozen flags %d", flags);
+  if (p.n_cells > DIES_STATIC_MAX_SHELLS)
+    return fail(DIES_EINVAL, "%d shells exceed the static scratch capacity of %d shells", p.n_cells,
+                DIES_STATIC_MAX_SHELLS);
+  if (!p.ws || !p.tables_valid || p.sm_count == 0)
+    return fail(DIES_ESTATE, "handle has no device tables yet: run dies_run or dies_run_async on it once first");
+  unsigned char *scr = nullptr;
+  int rc = static_scratch(&scr);
+  if (rc) return rc;
+  DIES_CUDA(cudaMemsetAsync(scr + kStaticCounters, 0, kStaticZeroBytes, p.stream));
+  DIES_CUDA(cudaMemsetAsync(E_abs_dev, 0, (size_t)p.n_cells * 8, p.stream));
+  DIES_CUDA(cudaMemsetAsync(sed_dev, 0, (size_t)p.F * 8, p.stream));
+  double *cdf = reinterpret_cast<double *>(scr);
+  DIES_CUDA(launch_frozen_cdf(p.stream, p.n_cells, p.F, p.at<double>(p.lay.freq), p.at<double>(p.lay.kabs),
+                              p.at<double>(p.lay.dnu), T_frozen_dev, cdf));
+  int occ = 0;
+  DIES_CUDA(transport_occupancy(PREC_FP64, MODE_FROZEN, p.block, next_pow2(p.n_tnodes), &occ));
+  if (occ < 1) return fail(DIES_ECUDA, "transport kernel cannot be resident with block size %d", p.block);
+  const int bps = (p.blocks_per_sm > 0 && p.blocks_per_sm < occ) ? p.blocks_per_sm : occ;
+  const int mode = (flags == DIES_FROZEN_ABSORB_TERMINAL) ? MODE_FROZEN_TERMINAL : MODE_FROZEN;
+  TransportParams P = p.params(mode, n, seed);
+  P.E = E_abs_dev;
+  P.sed = sed_dev;
+  P.cell_cdf = cdf;
+  P.rec_events = n_events_dev;
+  P.rec_hash = reinterpret_cast<unsigned long long *>(path_hash_dev);
+  P.counters = reinterpret_cast<unsigned long long *>(scr + kStaticCounters);
+  P.energies = reinterpret_cast<double *>(scr + kStaticEnergies);
+  P.queue = reinterpret_cast<unsigned long long *>(scr + kStaticQueue);
+  P.status = reinterpret_cast<uint32_t *>(scr + kStaticStatus);
+  const bool record = n_events_dev || path_hash_dev;
+  DIES_CUDA(launch_transport(PREC_FP64, mode, record, P, p.sm_count * bps, p.block, p.stream));
+  return DIES_OK;
+}
+
 // ------------------------------------------------------------------ batch
 int dies_create_batch(int n_models, const int *off, const double *radii, const double *rho, const int *kind,
                       double length_unit_cm, dies_batch **out) {

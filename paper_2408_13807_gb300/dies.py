@@ -43,6 +43,7 @@ EXPORTS = (
     "dies_batch_set_dust", "dies_batch_set_sources", "dies_batch_set_stream", "dies_batch_set_launch",
     "dies_run_batch", "dies_run_batch_async", "dies_batch_get_temperatures", "dies_batch_get_escaping_sed",
     "dies_batch_get_stats", "dies_destroy_batch", "dies_last_error", "dies_launch_count", "dies_version",
+    "dies_run_frozen_static",
 )
 
 
@@ -102,6 +103,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "dies_get_stats": (i, [_vp, _P(dies_stats)]),
         "dies_run_frozen": (i, [_vp, _dp, u64, u64, i, _P(ctypes.c_uint32), _P(ctypes.c_uint64)]),
         "dies_destroy_model": (None, [_vp]),
+        "dies_run_frozen_static": (i, [_vp, _vp, u64, u64, i, _vp, _vp, _vp, _vp]),
         "dies_create_batch": (i, [i, _P(ctypes.c_int), _dp, _dp, _P(ctypes.c_int), d, _P(_vp)]),
         "dies_batch_set_dust": (i, [_vp, _dp, i, _dp, _dp, _dp]),
         "dies_batch_set_sources": (i, [_vp, _dp, d, _dp]),
@@ -231,6 +233,14 @@ def dies_run_frozen(h, T_frozen, n_packages: int, seed: int, flags: int = DIES_F
     _check(load().dies_run_frozen(h, _ptr(T), int(n_packages), int(seed), int(flags), _ptr(ev, ctypes.c_uint32),
                                   _ptr(hs, ctypes.c_uint64)))
     return ev, hs
+
+
+def dies_run_frozen_static(h, T_frozen_dev: int, n_packages: int, seed: int, flags: int, E_abs_dev: int,
+                           sed_dev: int, n_events_dev: int = 0, path_hash_dev: int = 0):
+    """Device pointers (ints) in and out; enqueues only (see include/dies.h)."""
+    return _check(load().dies_run_frozen_static(h, _vp(T_frozen_dev), int(n_packages), int(seed), int(flags),
+                                                _vp(E_abs_dev), _vp(sed_dev), _vp(n_events_dev or None),
+                                                _vp(path_hash_dev or None)))
 
 
 def dies_destroy_model(h):
