@@ -145,10 +145,12 @@ int dies_set_tgrid(dies_model *m, double T_min, double T_max, int n_nodes);
 /* CUDA stream for all device work of this handle (cudaStream_t as void*). */
 int dies_set_stream(dies_model *m, void *cuda_stream);
 
-/* Launch shape of the transport kernel: block_size in {64,...,1024}
- * (multiple of 32), blocks_per_sm >= 0 (0 = occupancy maximum).  Values are
- * clamped to what the device can keep resident. */
-int dies_set_launch(dies_model *m, int block_size, int blocks_per_sm);
+/* Launch shape of the transport kernel: block_size a multiple of 32 in
+ * [64, 256], blocks_per_sm >= 0 (0 = occupancy maximum, larger values are
+ * clamped to it), rare_batch in [1, 32]: a warp runs its scatterings,
+ * absorptions and package starts together once this many of its lanes wait
+ * for one (or when no lane can move on).  Defaults 256, 0, 8. */
+int dies_set_launch(dies_model *m, int block_size, int blocks_per_sm, int rare_batch);
 
 /* Wall-clock budget of one transport launch in seconds (default 120).  A
  * launch that reaches it stops early and the run returns DIES_ETIMEOUT. */
@@ -238,7 +240,7 @@ int dies_batch_set_dust(dies_batch *b, const double *freq_hz, int n_freq, const 
                         const double *kappa_sca, const double *g);
 int dies_batch_set_sources(dies_batch *b, const double *J_ext, double L_point, const double *point_spectrum);
 int dies_batch_set_stream(dies_batch *b, void *cuda_stream);
-int dies_batch_set_launch(dies_batch *b, int block_size, int blocks_per_sm);
+int dies_batch_set_launch(dies_batch *b, int block_size, int blocks_per_sm, int rare_batch);
 int dies_run_batch(dies_batch *b, uint64_t n_packages_per_model, uint64_t seed);
 int dies_run_batch_async(dies_batch *b, uint64_t n_packages_per_model, uint64_t seed);
 /* Results: concatenated per-shell arrays (n_total = shell_offsets[n_models])

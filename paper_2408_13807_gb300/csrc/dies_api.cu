@@ -30,7 +30,7 @@ cudaError_t launch_node_tables(cudaStream_t st, int F, int n, int n_pow2, double
 cudaError_t launch_geometry(cudaStream_t st, int n_models, ModelDesc *desc, int n_cells_total, int n_bnd,
                             const double *radii, const double *rho, double length_unit_cm, const double *src_sum,
                             double L_point, double *r2d, float *r2f, double *rhod, float *rhof, double *inv_mass,
-                            float *inv_massf);
+                            float *inv_massf, float4 *geo, float *rhoe);
 cudaError_t launch_frozen_cdf(cudaStream_t st, int n_cells, int F, const double *nu, const double *kabs,
                               const double *dnu, const double *T, double *cell_cdf);
 size_t transport_smem_bytes(int n_tnodes_pow2);
@@ -41,6 +41,9 @@ cudaError_t launch_finalize(cudaStream_t st, int n_cells, const double *E, const
                             int fp32, const double *inv_mass, const double *Lnode, const double *lnT, int n,
                             double *T_out);
 cudaError_t launch_merge(cudaStream_t st, int n_cells, float *Eprev, float *Ecur);
+cudaError_t launch_tally(cudaStream_t st, int n_models, const ModelDesc *desc, unsigned long long n_per_source,
+                         const unsigned long long *sed_q, const unsigned long long *inj_q,
+                         const unsigned long long *dir_q, double *sed, double *energies);
 
 namespace {
 
@@ -78,7 +81,8 @@ bool finite_nonneg(const double *a, int n) {
 
 // Offsets (bytes) of every segment of the device workspace.
 struct Layout {
-  size_t desc, radii, rho_in, r2d, r2f, rhod, rhof, inv_mass, inv_massf, E, Eprev, Ecur, T, sed;
+  size_t desc, radii, rho_in, r2d, r2f, rhod, rhof, inv_mass, inv_massf, geo, rhoe, E, Eprev, Ecur, T, sed;
+  size_t sed_q, inj_q, dir_q;
   size_t freq, kabs, ksca, g, J, spec, dnu, src_cdf_d, src_cdf_f, src_sum;
   size_t Lnode_d, Lnode_f, lnT, dcdf_f, dcdf_d;
   size_t counters, energies, queue, status;
@@ -107,7 +111,7 @@ struct Problem {
   double T_min = 2.7, T_max = 1500.0;
   int n_tnodes = 1024;
   cudaStream_t stream = nullptr;
-  int block = 256, blocks_per_sm = 0;
+  int block = 256, blocks_per_sm = 0, rare_batch = 8;
   double time_budget_s = 120.0;
   // device
   unsigned char *ws = nullptr;
@@ -152,11 +156,16 @@ struct Problem {
     L.rhof = seg(nc * 4);
     L.inv_mass = seg(nc * 8);
     L.inv_massf = seg(nc * 4);
+    L.geo = seg(nb * 16);
+    L.rhoe = seg(nb * 4);
     L.E = seg(nc * 8);
     L.Eprev = seg(nc * 4);
     L.Ecur = seg(nc * 4);
     L.T = seg(nc * 8);
     L.sed = seg(nm * kMaxFreq * 8);
+    L.sed_q = seg(nm * 2 * kMaxFreq * 8);
+    L.inj_q = seg(nm * 2 * 8);
+    L.dir_q = seg(nm * 2 * 8);
     L.freq = seg(kMaxFreq * 8);
     L.kabs = seg(kMaxFreq * 8);
     L.ksca = seg(kMaxFreq * 8);
@@ -277,7 +286,8 @@ struct Problem {
     DIES_CUDA(launch_geometry(stream, n_models, at<ModelDesc>(lay.desc), n_cells, n_cells + n_models,
                               at<double>(lay.radii), at<double>(lay.rho_in), length_unit_cm, at<double>(lay.src_sum),
                               L_point, at<double>(lay.r2d), at<float>(lay.r2f), at<double>(lay.rhod),
-                              at<float>(lay.rhof), at<double>(lay.inv_mass), at<float>(lay.inv_massf)));
+                              at<float>(lay.rhof), at<double>(lay.inv_mass), at<float>(lay.inv_massf),
+                              at<float4>(lay.geo), at<float>(lay.rhoe)));
     tables_valid = true;
     return DIES_OK;
   }
@@ -293,6 +303,11 @@ struct Problem {
     P.rhod = at<double>(lay.rhod);
     P.inv_mass = at<double>(lay.inv_mass);
     P.inv_massf = at<float>(lay.inv_massf);
+    P.geo = at<float4>(lay.geo);
+    P.rhoe = at<float>(lay.rhoe);
+    P.sed_q = at<unsigned long long>(lay.sed_q);
+    P.inj_q = at<unsigned long long>(lay.inj_q);
+    P.dir_q = at<unsigned long long>(lay.dir_q);
     P.E = at<double>(lay.E);
     P.Eprev = at<float>(lay.Eprev);
     P.Ecur = at<float>(lay.Ecur);
@@ -321,6 +336,8 @@ struct Problem {
     P.mode = mode;
     P.max_events = 100000000ULL;
     P.time_budget_ns = (unsigned long long)(time_budget_s * 1e9);
+    P.inv_n = (float)(1.0 / (double)n);
+    P.batch_min = rare_batch;
     return P;
   }
 
@@ -339,6 +356,9 @@ struct Problem {
     DIES_CUDA(cudaMemsetAsync(ws + lay.Eprev, 0, (size_t)n_cells * 4, stream));
     DIES_CUDA(cudaMemsetAsync(ws + lay.Ecur, 0, (size_t)n_cells * 4, stream));
     DIES_CUDA(cudaMemsetAsync(ws + lay.sed, 0, (size_t)n_models * kMaxFreq * 8, stream));
+    DIES_CUDA(cudaMemsetAsync(ws + lay.sed_q, 0, (size_t)n_models * 2 * kMaxFreq * 8, stream));
+    DIES_CUDA(cudaMemsetAsync(ws + lay.inj_q, 0, (size_t)n_models * 2 * 8, stream));
+    DIES_CUDA(cudaMemsetAsync(ws + lay.dir_q, 0, (size_t)n_models * 2 * 8, stream));
     DIES_CUDA(cudaMemsetAsync(ws + lay.counters, 0, 16 * 8 + 0, stream));
     DIES_CUDA(cudaMemsetAsync(ws + lay.energies, 0, 8 * 8, stream));
     DIES_CUDA(cudaMemsetAsync(ws + lay.queue, 0, 2 * 8, stream));
@@ -386,6 +406,10 @@ struct Problem {
       if (prec == PREC_FP32) DIES_CUDA(launch_merge(stream, n_cells, at<float>(lay.Eprev), at<float>(lay.Ecur)));
     }
     DIES_CUDA(cudaEventRecord(ev[3], stream));
+    if (prec != PREC_FP64)
+      DIES_CUDA(launch_tally(stream, n_models, at<ModelDesc>(lay.desc), n, at<unsigned long long>(lay.sed_q),
+                             at<unsigned long long>(lay.inj_q), at<unsigned long long>(lay.dir_q), at<double>(lay.sed),
+                             at<double>(lay.energies)));
     DIES_CUDA(launch_finalize(stream, n_cells, at<double>(lay.E), at<float>(lay.Eprev), at<float>(lay.Ecur),
                               prec == PREC_FP32, at<double>(lay.inv_mass), at<double>(lay.Lnode_d),
                               at<double>(lay.lnT), n_tnodes, at<double>(lay.T)));
@@ -680,17 +704,19 @@ int dies_set_stream(dies_model *m, void *s) {
   return DIES_OK;
 }
 
-static int set_launch(Problem &p, int block, int bps) {
+static int set_launch(Problem &p, int block, int bps, int rare_batch) {
   if (block < 64 || block > 256 || block % 32) return fail(DIES_EINVAL, "block_size must be a multiple of 32 in [64, 256]");
   if (bps < 0) return fail(DIES_EINVAL, "blocks_per_sm must be >= 0");
+  if (rare_batch < 1 || rare_batch > 32) return fail(DIES_EINVAL, "rare_batch must be in [1, 32]");
   p.block = block;
   p.blocks_per_sm = bps;
+  p.rare_batch = rare_batch;
   return DIES_OK;
 }
 
-int dies_set_launch(dies_model *m, int block_size, int blocks_per_sm) {
+int dies_set_launch(dies_model *m, int block_size, int blocks_per_sm, int rare_batch) {
   if (!m) return fail(DIES_EINVAL, "model is NULL");
-  return set_launch(m->p, block_size, blocks_per_sm);
+  return set_launch(m->p, block_size, blocks_per_sm, rare_batch);
 }
 
 int dies_set_time_budget(dies_model *m, double seconds) {
@@ -915,9 +941,9 @@ int dies_batch_set_stream(dies_batch *b, void *s) {
   return DIES_OK;
 }
 
-int dies_batch_set_launch(dies_batch *b, int block_size, int blocks_per_sm) {
+int dies_batch_set_launch(dies_batch *b, int block_size, int blocks_per_sm, int rare_batch) {
   if (!b) return fail(DIES_EINVAL, "batch is NULL");
-  return set_launch(b->p, block_size, blocks_per_sm);
+  return set_launch(b->p, block_size, blocks_per_sm, rare_batch);
 }
 
 int dies_run_batch_async(dies_batch *b, uint64_t n, uint64_t seed) {

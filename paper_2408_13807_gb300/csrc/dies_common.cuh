@@ -57,6 +57,9 @@ struct alignas(16) ModelDesc {
   double R;        // outer radius (length units)
   double L[2];     // source luminosities (erg/s), written by the table build
   unsigned long long pkg_off;  // first source slot of this model (slots x packages = work items)
+  float Lf[2];     // the luminosities as float (package energies of the FP32 forms)
+  float Rf;        // outer radius as float
+  float pad1;
 };
 
 struct TransportParams {
@@ -70,11 +73,17 @@ struct TransportParams {
   const double *rhod;
   const double *inv_mass;   // 1 / (4 pi rho V L_u^2)
   const float *inv_massf;
+  const float4 *geo;        // FP32 forms: per cell + void {R_in^2 hi, lo, R_out^2 hi, lo}
+  const float *rhoe;        // FP32 forms: density per geo record (0 in the void)
   // accumulators
   double *E;                // absorbed energy (MIXED / FP64 forms and frozen tallies)
   const float *Eprev;       // FP32 form: all previous batches (read only in a batch)
   float *Ecur;              // FP32 form: current batch
-  double *sed;              // [n_models][F]
+  double *sed;              // [n_models][kMaxFreq] (FP64 form writes it directly)
+  // FP32 forms: fixed-point tallies, 2^-24 package energies per unit
+  unsigned long long *sed_q;  // [n_models][2][kMaxFreq]
+  unsigned long long *inj_q;  // [n_models][2]
+  unsigned long long *dir_q;  // [n_models][2]
   // per-frequency tables
   const double *kabs_d, *ksca_d, *g_d;
   const double *src_cdf_d;  // [2][kMaxFreq]
@@ -105,7 +114,11 @@ struct TransportParams {
   int mode;
   unsigned long long max_events;
   unsigned long long time_budget_ns;
+  float inv_n;      // 1 / n_per_source (FP32 package energies)
+  int batch_min;    // lanes that must wait for a rare event before a warp runs them together
 };
+
+constexpr float kQuantum = 16777216.0f;  // 2^24 fixed-point units per package energy
 
 // ------------------------------------------------------------------ Philox
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two

@@ -138,6 +138,9 @@ __global__ void k_cells(int n_models, ModelDesc *desc, int n_cells_total, const 
     const double Rcm = desc[c].R * length_unit_cm;
     desc[c].L[0] = (desc[c].src_mask & 1) ? 4.0 * kPi * kPi * Rcm * Rcm * src_sum[0] : 0.0;
     desc[c].L[1] = (desc[c].src_mask & 2) ? L_point : 0.0;
+    desc[c].Lf[0] = (float)desc[c].L[0];
+    desc[c].Lf[1] = (float)desc[c].L[1];
+    desc[c].Rf = (float)desc[c].R;
   }
   if (c >= n_cells_total) return;
   // model of this cell (binary search over the cell offsets)
@@ -154,6 +157,32 @@ __global__ void k_cells(int n_models, ModelDesc *desc, int n_cells_total, const 
   rhof[c] = (float)rho[c];
   inv_mass[c] = (m > 0.0) ? 1.0 / m : 0.0;
   inv_massf[c] = (m > 0.0) ? (float)(1.0 / m) : 0.0f;
+}
+
+// Per-cell geometry records of the FP32 transport, one per cell plus one for
+// the central void in front of every model's cells (index bnd_off + cell + 1):
+// {R_in^2 hi, R_in^2 lo, R_out^2 hi, R_out^2 lo} as float pairs (hi = float of
+// the FP64 square, lo = float of the remainder) and the density (0 in the void).
+__global__ void k_geo(int n_models, const ModelDesc *desc, int n_bnd, const double *radii, const double *rho,
+                      float4 *geo, float *rhoe) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n_bnd) return;
+  int lo = 0, hi = n_models - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (desc[mid].bnd_off <= b) lo = mid; else hi = mid - 1;
+  }
+  const int i = b - desc[lo].bnd_off;  // 0 = void, i >= 1: cell i - 1
+  const double ro2 = radii[b] * radii[b];
+  const float rh = (float)ro2, rl = (float)(ro2 - (double)rh);
+  float ih = 0.0f, il = 0.0f;
+  if (i >= 1) {
+    const double ri2 = radii[b - 1] * radii[b - 1];
+    ih = (float)ri2;
+    il = (float)(ri2 - (double)ih);
+  }
+  geo[b] = make_float4(ih, il, rh, rl);
+  rhoe[b] = (i >= 1) ? (float)rho[b - lo - 1] : 0.0f;
 }
 
 // Frozen pass: per-cell CDF of kabs_k B_k(T_i) dnu_k (one block of 64 per cell).
@@ -192,9 +221,11 @@ cudaError_t launch_node_tables(cudaStream_t st, int F, int n, int n_pow2, double
 
 cudaError_t launch_geometry(cudaStream_t st, int n_models, ModelDesc *desc, int n_cells_total, int n_bnd, const double *radii, const double *rho,
                             double length_unit_cm, const double *src_sum, double L_point, double *r2d, float *r2f,
-                            double *rhod, float *rhof, double *inv_mass, float *inv_massf) {
+                            double *rhod, float *rhof, double *inv_mass, float *inv_massf, float4 *geo, float *rhoe) {
   const int tb = 256;
   k_boundaries<<<(n_bnd + tb - 1) / tb, tb, 0, st>>>(n_bnd, radii, r2d, r2f);
+  k_geo<<<(n_bnd + tb - 1) / tb, tb, 0, st>>>(n_models, desc, n_bnd, radii, rho, geo, rhoe);
+  launch_counter_add(1);
   const int n = n_cells_total > n_models ? n_cells_total : n_models;
   k_cells<<<(n + tb - 1) / tb, tb, 0, st>>>(n_models, desc, n_cells_total, radii, rho, length_unit_cm, src_sum,
                                             L_point, rhod, rhof, inv_mass, inv_massf);

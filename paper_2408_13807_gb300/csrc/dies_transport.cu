@@ -1,22 +1,32 @@
 // dies_transport.cu -- the IRE transport kernel (Sect. 2.1 with the weighting
-// of Sect. 2.2), the temperature kernel and the FP32 batch merge.
+// of Sect. 2.2), the temperature kernel, the tally conversion and the FP32
+// batch merge.
 //
 // Design (GB300): one persistent grid sized to the SM count; every thread
-// owns one photon package at a time, its state in registers; a warp refills
-// its finished lanes from a device work counter with one atomic per refill
-// (ballot + popc), so that lanes keep stepping while long-lived packages of
-// the same warp finish.  One loop iteration performs exactly one event per
-// live lane (boundary crossing, scattering or absorption + re-emission), so
-// the warp stays converged at the loop head.  Per-frequency tables and the
-// emission table are staged in shared memory; the re-emission CDF rows and
-// the per-cell geometry are read through L1.  Absorbed energies are FP64
-// atomics whose returned old value gives the (E_old, E_new) pair of the
-// absorption, so every GPU run is one serialisation of the IRE updates.
+// owns one photon package at a time, its state in registers.  Each loop
+// iteration moves every live lane by one boundary crossing (the common
+// event).  A lane whose free path runs out inside its cell, or that needs a
+// new package, parks with a pending rare event; the warp runs the rare-event
+// path for all parked lanes together once enough of them wait (or nothing
+// else can move), so one Philox call, one HG inversion or one table search
+// serves many lanes instead of one.  Finished lanes refill from a device work
+// counter with one atomic per refill (ballot + popc).  Per-frequency tables
+// and the emission table are staged in shared memory; the per-cell geometry
+// is one 16-byte record read through L1.
 //
 // Geometry is one-dimensional: the impact parameter p^2 is invariant along a
 // straight flight and s = r mu is the signed path coordinate, r^2 = p^2 + s^2.
 // At each boundary s is set afresh to +-sqrt(R_b^2 - p^2), so no rounding
 // accumulates along a flight and precision is relative to the local radius.
+// In the FP32 forms R_b^2 is a float pair (hi + lo = the FP64 square), so
+// R_b^2 - p^2 is formed as (hi - p^2) + lo without cancellation.
+//
+// Accounting: the FP64 form (parity) adds energies in FP64 exactly as the
+// oracle does.  The FP32 forms keep FP64 only in the absorbed-energy
+// accumulators: escaped, injected and directly escaped weights are summed as
+// 64-bit integers in units of 2^-24 package energies and converted once, so
+// no FP64 instruction runs per event (GB300's FP64 rate is a small fraction of
+// its FP32 rate).
 #include "dies_common.cuh"
 
 namespace dies {
@@ -26,6 +36,7 @@ constexpr double kTwoPi = 6.283185307179586476925286766559;
 constexpr unsigned kFull = 0xffffffffu;
 
 enum Phase { PH_DEAD = 0, PH_PREWALK = 1, PH_FORCED = 2, PH_NORMAL = 3 };
+enum Pend { PEND_NONE = 0, PEND_SCATTER = 1, PEND_ABSORB = 2, PEND_INJECT = 3 };
 
 template <int PREC>
 struct RealOf {
@@ -36,35 +47,46 @@ struct RealOf<PREC_FP64> {
   using T = double;
 };
 
-// Shared-memory tables of one CTA.
+// Shared-memory tables and tallies of one CTA.
 struct Shared {
   float kabs_f[kMaxFreq], ksca_f[kMaxFreq];
   float hg_a[kMaxFreq], hg_b[kMaxFreq], hg_c[kMaxFreq], hg_1pg2[kMaxFreq], hg_inv2g[kMaxFreq];
   float src_cdf_f[2][kMaxFreq];
   double kabs_d[kMaxFreq], ksca_d[kMaxFreq], g_d[kMaxFreq];
   double src_cdf_d[2][kMaxFreq];
-  double sed[kMaxFreq];
+  double sed[kMaxFreq];                    // FP64 form
+  unsigned long long sed_q[2][kMaxFreq];   // FP32 forms, single model
+  unsigned long long inj_q[2], dir_q[2];
+  unsigned int rare[CNT_COUNT];            // per-package counters
 };
 
 template <class Real>
 struct Lane {
   Real p2, s, tauA, tauS, w, acc, tau_int, s0, u_type;
-  double eps;
-  int cell, f, phase, cell0, src, model, cell_off, bnd, n, n64;
-  uint32_t events;
-  Stream rs;
+  Real ka, ks;   // absorption / scattering coefficient per unit density at the current frequency
+  Real eps;      // package energy (erg/s)
+  int cell, f, phase, pend, src, model, cell_off, n, n64;
+  uint32_t events, blk, pkg_lo, pkg_hi;
   // parity records
   unsigned long long row, hash;
   uint32_t nsca, nabs, ncross;
 };
 
 struct Tally {
-  uint32_t c[CNT_COUNT];
-  double e_inj, e_lost, e_direct;
+  uint32_t cross, scat, abs;
+  double e_inj, e_direct;  // FP64 form only
 };
 
+template <int PREC>
+__device__ __forceinline__ U4 draw(const TransportParams &P, Lane<typename RealOf<PREC>::T> &L) {
+  const U4 r = philox10(L.pkg_lo, L.pkg_hi, L.blk, (uint32_t)L.model ^ ((uint32_t)L.src << 24), (uint32_t)P.seed,
+                        (uint32_t)(P.seed >> 32));
+  ++L.blk;
+  return r;
+}
+
 // ------------------------------------------------------------- sampling
-// smallest k with cdf[k] >= u over a 64-entry row (entries >= F hold 1)
+// smallest k with row[k] >= u over a 64-entry row (entries >= F hold 1)
 template <class T>
 __device__ __forceinline__ int cdf_pick(const T *row, T u) {
   int k = 0;
@@ -73,14 +95,8 @@ __device__ __forceinline__ int cdf_pick(const T *row, T u) {
     if (row[k + step - 1] < u) k += step;
   return k;
 }
-__device__ __forceinline__ int cdf_pick_ldg(const float *row, float u) {
-  int k = 0;
-#pragma unroll
-  for (int step = 32; step > 0; step >>= 1)
-    if (__ldg(row + k + step - 1) < u) k += step;
-  return k;
-}
-__device__ __forceinline__ int cdf_pick_ldg(const double *row, double u) {
+template <class T>
+__device__ __forceinline__ int cdf_pick_ldg(const T *row, T u) {
   int k = 0;
 #pragma unroll
   for (int step = 32; step > 0; step >>= 1)
@@ -93,7 +109,7 @@ __device__ __forceinline__ int node_count_f(const float *L, int pow2, float e) {
   int j = 0;
   for (int step = pow2 >> 1; step > 0; step >>= 1)
     if (L[j + step - 1] <= e) j += step;
-  if (L[j] <= e) ++j;  // L[pow2-1] is +inf for a padded table, finite only if n == pow2
+  if (L[j] <= e) ++j;
   return j;
 }
 
@@ -102,58 +118,6 @@ __device__ __forceinline__ int node_count_d(const double *Ld, int n, int j, doub
   while (j < n && __ldg(Ld + j) <= e) ++j;
   while (j > 0 && __ldg(Ld + j - 1) > e) --j;
   return j;
-}
-
-// ------------------------------------------------------------ geometry
-template <class Real>
-__device__ __forceinline__ Real ld_r2(const TransportParams &P, int b);
-template <>
-__device__ __forceinline__ float ld_r2<float>(const TransportParams &P, int b) {
-  return __ldg(P.r2f + b);
-}
-template <>
-__device__ __forceinline__ double ld_r2<double>(const TransportParams &P, int b) {
-  return __ldg(P.r2d + b);
-}
-
-// Distance l to the boundary through which the package leaves its cell, the
-// path coordinate sb of that boundary, and the cell entered there.
-template <int PREC, class Real>
-__device__ __forceinline__ void boundary(const TransportParams &P, const Lane<Real> &L, Real &l, Real &sb,
-                                         int &next) {
-  const int c = L.cell;
-  const int bi = L.bnd + (c >= 0 ? c : 0);
-  const Real lo2 = (c >= 0) ? ld_r2<Real>(P, bi) : Real(0);
-  const Real hi2 = ld_r2<Real>(P, bi + (c >= 0 ? 1 : 0));
-  const bool inward = (L.s < Real(0)) && (L.p2 < lo2);
-  next = inward ? c - 1 : c + 1;
-  if constexpr (PREC == PREC_FP64) {
-    // cancellation-free forms of the two roots of |x + l d|^2 = R^2
-    const Real r2 = L.p2 + L.s * L.s;
-    if (inward) {
-      const Real sq = sqrt(lo2 - L.p2);
-      l = (r2 - lo2) / (-L.s + sq);
-      sb = -sq;
-    } else {
-      const Real sq = sqrt(fmax(hi2 - L.p2, 0.0));
-      l = (L.s <= 0.0) ? (-L.s + sq) : ((hi2 - r2) / (L.s + sq));
-      sb = sq;
-    }
-    l = fmax(l, 0.0);
-  } else {
-    if (PREC == PREC_MIXED && c >= 0 && c < L.n64) {
-      // innermost shells: crossing distance in FP64 (R^2 - p^2 cancels there)
-      const double t2 = __ldg(P.r2d + bi + (inward ? 0 : 1));
-      double sq = sqrt(fmax(t2 - (double)L.p2, 0.0));
-      if (inward) sq = -sq;
-      sb = (float)sq;
-      l = fmaxf((float)(sq - (double)L.s), 0.0f);
-    } else {
-      float sq = sqrtf(fmaxf((inward ? lo2 : hi2) - L.p2, 0.0f));
-      sb = inward ? -sq : sq;
-      l = fmaxf(sb - L.s, 0.0f);
-    }
-  }
 }
 
 // ---------------------------------------------------------- bookkeeping
@@ -165,6 +129,7 @@ __device__ __forceinline__ void record(Lane<Real> &L, int ev, int cell, int f) {
 template <bool RECORD, class Real>
 __device__ __forceinline__ void finish(const TransportParams &P, Lane<Real> &L) {
   L.phase = PH_DEAD;
+  L.pend = PEND_NONE;
   if constexpr (RECORD) {
     if (P.rec_events) {
       P.rec_events[3 * L.row + 0] = L.nsca;
@@ -175,39 +140,200 @@ __device__ __forceinline__ void finish(const TransportParams &P, Lane<Real> &L) 
   }
 }
 
-template <bool RECORD, class Real>
-__device__ __forceinline__ void escape(const TransportParams &P, Shared &S, Lane<Real> &L, Tally &T) {
-  const double e = (double)L.w * L.eps;
-  if (P.n_models == 1) atomicAdd(&S.sed[L.f], e);
-  else atomicAdd(P.sed + (size_t)L.model * kMaxFreq + L.f, e);
-  T.c[CNT_ESCAPED]++;
+// add weight w of the current package to an escaping-SED bin
+template <int PREC>
+__device__ __forceinline__ void tally_sed(const TransportParams &P, Shared &S, Lane<typename RealOf<PREC>::T> &L,
+                                          typename RealOf<PREC>::T w) {
+  if constexpr (PREC == PREC_FP64) {
+    const double e = w * L.eps;
+    if (P.n_models == 1) atomicAdd(&S.sed[L.f], e);
+    else atomicAdd(P.sed + (size_t)L.model * kMaxFreq + L.f, e);
+  } else {
+    const unsigned long long q = __float2ull_rn(w * kQuantum);
+    if (P.n_models == 1) atomicAdd(&S.sed_q[L.src][L.f], q);
+    else atomicAdd(P.sed_q + ((size_t)L.model * 2 + L.src) * kMaxFreq + L.f, q);
+  }
+}
+
+template <int PREC, bool RECORD>
+__device__ __forceinline__ void escape(const TransportParams &P, Shared &S, Lane<typename RealOf<PREC>::T> &L) {
+  tally_sed<PREC>(P, S, L, L.w);
+  atomicAdd(&S.rare[CNT_ESCAPED], 1u);
   finish<RECORD>(P, L);
 }
 
 template <bool RECORD, class Real>
-__device__ __forceinline__ void lose(const TransportParams &P, Lane<Real> &L, Tally &T, int why) {
-  T.c[why]++;
-  T.e_lost += (double)L.w * L.eps;
+__device__ __forceinline__ void lose(const TransportParams &P, Shared &S, Lane<Real> &L, int why) {
+  atomicAdd(&S.rare[why], 1u);
+  atomicAdd(P.energies + EN_LOST, (double)L.w * (double)L.eps);  // rare
   finish<RECORD>(P, L);
 }
 
-template <bool RECORD, class Real>
-__device__ __forceinline__ void cross(const TransportParams &P, Shared &S, Lane<Real> &L, Tally &T, Real sb,
-                                      int next) {
+// ------------------------------------------------------------ geometry
+// Distance l to the boundary through which the package leaves its cell, the
+// path coordinate sb of that boundary, the cell entered there, and the
+// density of the current cell.
+template <int PREC>
+__device__ __forceinline__ void boundary(const TransportParams &P, const Lane<typename RealOf<PREC>::T> &L,
+                                         typename RealOf<PREC>::T &l, typename RealOf<PREC>::T &sb, int &next,
+                                         typename RealOf<PREC>::T &rho) {
+  const int c = L.cell;
+  if constexpr (PREC == PREC_FP64) {
+    // cancellation-free forms of the two roots of |x + l d|^2 = R^2 (as the oracle)
+    const int bi = L.cell_off + L.model + (c >= 0 ? c : 0);
+    const double lo2 = (c >= 0) ? __ldg(P.r2d + bi) : 0.0;
+    const double hi2 = __ldg(P.r2d + bi + (c >= 0 ? 1 : 0));
+    rho = (c >= 0) ? __ldg(P.rhod + L.cell_off + c) : 0.0;
+    const bool inward = (L.s < 0.0) && (L.p2 < lo2);
+    next = inward ? c - 1 : c + 1;
+    const double r2 = L.p2 + L.s * L.s;
+    if (inward) {
+      const double sq = sqrt(lo2 - L.p2);
+      l = (r2 - lo2) / (-L.s + sq);
+      sb = -sq;
+    } else {
+      const double sq = sqrt(fmax(hi2 - L.p2, 0.0));
+      l = (L.s <= 0.0) ? (-L.s + sq) : ((hi2 - r2) / (L.s + sq));
+      sb = sq;
+    }
+    l = fmax(l, 0.0);
+  } else {
+    const int gi = L.cell_off + L.model + c + 1;
+    const float4 G = __ldg(P.geo + gi);
+    rho = __ldg(P.rhoe + gi);
+    const float d_in = (G.x - L.p2) + G.y;
+    const bool inward = (L.s < 0.0f) && (d_in > 0.0f);
+    const float d = inward ? d_in : (G.z - L.p2) + G.w;
+    next = inward ? c - 1 : c + 1;
+    float sq;
+    if (PREC == PREC_MIXED && c >= 0 && c < L.n64) {
+      // optional FP64 crossing distance in the innermost shells
+      const double t2 = __ldg(P.r2d + L.cell_off + L.model + c + (inward ? 0 : 1));
+      sq = (float)sqrt(fmax(t2 - (double)L.p2, 0.0));
+    } else {
+      sq = sqrtf(fmaxf(d, 0.0f));
+    }
+    sb = inward ? -sq : sq;
+    l = fmaxf(sb - L.s, 0.0f);
+  }
+}
+
+template <int PREC, bool RECORD>
+__device__ __forceinline__ void cross(const TransportParams &P, Shared &S, Lane<typename RealOf<PREC>::T> &L,
+                                      Tally &T, typename RealOf<PREC>::T sb, int next) {
   L.s = sb;
   L.cell = next;
-  T.c[CNT_CROSS]++;
+  T.cross++;
   if constexpr (RECORD) L.ncross++;
   record<RECORD>(L, EV_CROSS, next, L.f);
-  if (next >= L.n) escape<RECORD>(P, S, L, T);
+  if (next >= L.n) escape<PREC, RECORD>(P, S, L);
+}
+
+template <int PREC>
+__device__ __forceinline__ void set_freq(const Shared &S, Lane<typename RealOf<PREC>::T> &L, int f) {
+  L.f = f;
+  if constexpr (PREC == PREC_FP64) {
+    L.ka = S.kabs_d[f];
+    L.ks = S.ksca_d[f];
+  } else {
+    L.ka = S.kabs_f[f];
+    L.ks = S.ksca_f[f];
+  }
+}
+
+// -------------------------------------------------- the common event: move
+// One step of a moving package: cross into the next cell, or stop at an
+// interaction point and park with a pending scattering / absorption.
+template <int PREC, int MODE, bool RECORD>
+__device__ __forceinline__ void move(const TransportParams &P, Shared &S, Lane<typename RealOf<PREC>::T> &L,
+                                     Tally &T) {
+  using Real = typename RealOf<PREC>::T;
+  if constexpr (PREC == PREC_FP64) {
+    if (L.phase == PH_NORMAL && L.events >= P.max_events) {
+      lose<RECORD>(P, S, L, CNT_KILL_CAP);
+      return;
+    }
+  }
+  Real l, sb, rho;
+  int next;
+  boundary<PREC>(P, L, l, sb, next, rho);
+  const Real ka = L.ka * rho, ks = L.ks * rho;
+  if (L.phase == PH_PREWALK) {
+    // total extinction optical depth to the surface (Sect. 2.2.2)
+    L.acc += (ka + ks) * l;
+    L.s = sb;
+    L.cell = next;
+    if (next >= L.n) {
+      const Real tau0 = L.acc;
+      Real q;
+      if constexpr (PREC == PREC_FP64) q = -expm1(-tau0);
+      else q = -expm1f(-tau0);
+      // direct escape e^-tau0 of the package is tallied; the rest is forced (Eq. 12)
+      tally_sed<PREC>(P, S, L, L.w * (Real(1) - q));
+      if constexpr (PREC == PREC_FP64) {
+        T.e_direct += (double)L.w * L.eps * (1.0 - (double)q);
+      } else {
+        const unsigned long long dq = __float2ull_rn(L.w * (1.0f - q) * kQuantum);
+        if (P.n_models == 1) atomicAdd(&S.dir_q[L.src], dq);
+        else atomicAdd(P.dir_q + (size_t)L.model * 2 + L.src, dq);
+      }
+      L.w *= q;
+      if (!(q > Real(0))) {
+        atomicAdd(&S.rare[CNT_ESCAPED], 1u);
+        finish<RECORD>(P, L);
+      } else if (L.w < Real(1e-10)) {
+        lose<RECORD>(P, S, L, CNT_KILL_WEIGHT);
+      } else {
+        Real ti;
+        if constexpr (PREC == PREC_FP64) ti = -log1p(-L.tau_int * q);  // Eq. 10
+        else ti = -log1pf(-L.tau_int * q);
+        L.tau_int = (ti > tau0) ? tau0 : ti;
+        atomicAdd(&S.rare[CNT_FORCED], 1u);
+        L.s = L.s0;
+        L.cell = (L.src == 0) ? L.n - 1 : __ldg(&P.desc[L.model].point_cell);
+        L.acc = Real(0);
+        L.phase = PH_FORCED;
+      }
+    }
+    return;
+  }
+  if constexpr (PREC == PREC_FP64) L.events++;
+  if (L.phase == PH_FORCED) {
+    const Real ke = ka + ks;
+    if (ke > Real(0) && L.acc + ke * l >= L.tau_int) {
+      Real li = (L.tau_int - L.acc) / ke;
+      li = li > l ? l : li;
+      li = li < Real(0) ? Real(0) : li;
+      L.s += li;
+      L.phase = PH_NORMAL;
+      L.pend = (L.u_type * ke < ka) ? PEND_ABSORB : PEND_SCATTER;
+    } else {
+      L.acc += ke * l;
+      cross<PREC, RECORD>(P, S, L, T, sb, next);
+    }
+    return;
+  }
+  // normal transport: competing free paths (Eqs. 1 and 4); the boundary wins
+  // ties, and an interaction in a cell without absorption is a scattering
+  const Real ta = ka * l, ts = ks * l;
+  if (L.tauA >= ta && L.tauS >= ts) {
+    L.tauA -= ta;
+    L.tauS -= ts;
+    cross<PREC, RECORD>(P, S, L, T, sb, next);
+  } else if (ka <= Real(0) || L.tauS * ka < L.tauA * ks) {
+    L.s += L.tauS / ks;
+    L.pend = PEND_SCATTER;
+  } else {
+    L.s += L.tauA / ka;
+    L.pend = PEND_ABSORB;
+  }
 }
 
 // ------------------------------------------------------------ injection
+// Decode work index g into (model, source, package) and reset the lane.
 template <int PREC, bool RECORD>
-__device__ void inject(const TransportParams &P, Shared &S, Lane<typename RealOf<PREC>::T> &L,
-                       unsigned long long g, Tally &T) {
-  using Real = typename RealOf<PREC>::T;
-  // work index -> (source slot, package); slots are numbered model by model
+__device__ __forceinline__ void assign(const TransportParams &P, Lane<typename RealOf<PREC>::T> &L,
+                                       unsigned long long g) {
   const unsigned long long slot = g / P.pkg_len;
   const unsigned long long pkg = P.pkg_begin + (g - slot * P.pkg_len);
   int m = 0;
@@ -222,37 +348,44 @@ __device__ void inject(const TransportParams &P, Shared &S, Lane<typename RealOf
   const ModelDesc *D = P.desc + m;
   const unsigned long long sl = slot - __ldg(&D->pkg_off);
   const int mask = __ldg(&D->src_mask);
-  const int src = (mask == 3) ? (int)sl : ((mask & 1) ? 0 : 1);
+  L.src = (mask == 3) ? (int)sl : ((mask & 1) ? 0 : 1);
   L.model = m;
-  L.src = src;
   L.cell_off = __ldg(&D->cell_off);
-  L.bnd = __ldg(&D->bnd_off);
   L.n = __ldg(&D->n_cells);
   L.n64 = __ldg(&D->n_fp64);
-  L.eps = __ldg(&D->L[src]) / (double)P.n_per_source;
-  const double R = __ldg(&D->R);
-  L.rs.k0 = (uint32_t)P.seed;
-  L.rs.k1 = (uint32_t)(P.seed >> 32);
-  L.rs.c0 = (uint32_t)pkg;
-  L.rs.c1 = (uint32_t)(pkg >> 32);
-  L.rs.c3 = (uint32_t)m ^ ((uint32_t)src << 24);
-  L.rs.blk = 0;
+  if constexpr (PREC == PREC_FP64) L.eps = __ldg(&D->L[L.src]) / (double)P.n_per_source;
+  else L.eps = __ldg(&D->Lf[L.src]) * P.inv_n;
+  L.pkg_lo = (uint32_t)pkg;
+  L.pkg_hi = (uint32_t)(pkg >> 32);
+  L.blk = 0;
   L.events = 0;
-  L.w = Real(1);
+  L.pend = PEND_INJECT;
+  L.phase = PH_NORMAL;
   if constexpr (RECORD) {
     L.row = sl * P.n_per_source + pkg;
     L.hash = 0xcbf29ce484222325ULL;
     L.nsca = L.nabs = L.ncross = 0;
   }
+}
+
+// Start the package: frequency from the source CDF, free paths (Eq. 1),
+// direction (Eqs. 2-3, or Eq. 5 with weighting), optional forced first
+// interaction set-up.
+template <int PREC, bool RECORD>
+__device__ __forceinline__ void inject(const TransportParams &P, Shared &S, Lane<typename RealOf<PREC>::T> &L,
+                                       Tally &T, const U4 &a) {
+  using Real = typename RealOf<PREC>::T;
+  const ModelDesc *D = P.desc + L.model;
+  L.w = Real(1);
   Real u_int = Real(0.5);
   if constexpr (PREC == PREC_FP64) {
-    const U4 a = L.rs.next();
     const double u_f = u01d(a.x, a.y), u_mu = u01d(a.z, a.w);
-    L.f = cdf_pick(S.src_cdf_d[src], u_f);
-    const U4 b = L.rs.next();
+    set_freq<PREC>(S, L, cdf_pick(S.src_cdf_d[L.src], u_f));
+    const U4 b = draw<PREC>(P, L);
     L.tauS = -log(u01d(b.x, b.y));
     L.tauA = -log(u01d(b.z, b.w));
-    if (src == 0) {
+    if (L.src == 0) {
+      const double R = __ldg(&D->R);
       double mu;
       if (P.k_bg == 0.5) {
         mu = sqrt(u_mu);
@@ -269,18 +402,17 @@ __device__ void inject(const TransportParams &P, Shared &S, Lane<typename RealOf
       L.cell = __ldg(&D->point_cell);
     }
     if (P.ffi) {
-      const U4 c = L.rs.next();
+      const U4 c = draw<PREC>(P, L);
       u_int = u01d(c.x, c.y);
       L.u_type = u01d(c.z, c.w);
     }
   } else {
-    const U4 a = L.rs.next();
-    L.f = cdf_pick(S.src_cdf_f[src], u01f_word(a.x));
+    set_freq<PREC>(S, L, cdf_pick(S.src_cdf_f[L.src], u01f_word(a.x)));
     const float v = u01f_fine(a.y);  // 1 - u of the direction draw
     L.tauS = -__logf(u01f_word(a.z));
     L.tauA = -__logf(u01f_word(a.w));
-    if (src == 0) {
-      const float Rf = (float)R;
+    if (L.src == 0) {
+      const float Rf = __ldg(&D->Rf);
       float mu, sin2;
       if (P.k_bg == 0.5) {
         mu = sqrtf(1.0f - v);
@@ -302,16 +434,22 @@ __device__ void inject(const TransportParams &P, Shared &S, Lane<typename RealOf
       L.cell = __ldg(&D->point_cell);
     }
     if (P.ffi) {
-      const U4 c = L.rs.next();
+      const U4 c = draw<PREC>(P, L);
       u_int = u01f_word(c.x);
       L.u_type = u01f_word(c.y);
     }
   }
-  T.c[CNT_INJECTED]++;
-  T.e_inj += (double)L.w * L.eps;
+  atomicAdd(&S.rare[CNT_INJECTED], 1u);
+  if constexpr (PREC == PREC_FP64) {
+    T.e_inj += (double)L.w * L.eps;
+  } else {
+    const unsigned long long q = __float2ull_rn(L.w * kQuantum);
+    if (P.n_models == 1) atomicAdd(&S.inj_q[L.src], q);
+    else atomicAdd(P.inj_q + (size_t)L.model * 2 + L.src, q);
+  }
   record<RECORD>(L, EV_INJECT, L.cell, L.f);
   if (L.w < Real(1e-10)) {
-    lose<RECORD>(P, L, T, CNT_KILL_WEIGHT);
+    lose<RECORD>(P, S, L, CNT_KILL_WEIGHT);
     return;
   }
   if (P.ffi) {
@@ -319,7 +457,6 @@ __device__ void inject(const TransportParams &P, Shared &S, Lane<typename RealOf
     L.acc = Real(0);
     L.tau_int = u_int;  // holds u_int until the pre-walk has found tau0
     L.s0 = L.s;
-    L.cell0 = L.cell;
   } else {
     L.phase = PH_NORMAL;
   }
@@ -328,9 +465,8 @@ __device__ void inject(const TransportParams &P, Shared &S, Lane<typename RealOf
 // ----------------------------------------------------------- scattering
 template <int PREC, bool RECORD>
 __device__ __forceinline__ void scatter(const TransportParams &P, Shared &S, Lane<typename RealOf<PREC>::T> &L,
-                                        Tally &T) {
+                                        Tally &T, const U4 &a) {
   if constexpr (PREC == PREC_FP64) {
-    const U4 a = L.rs.next();
     const double u_mu = u01d(a.x, a.y), u_phi = u01d(a.z, a.w);
     const double g = S.g_d[L.f];
     double mu_s;
@@ -352,11 +488,10 @@ __device__ __forceinline__ void scatter(const TransportParams &P, Shared &S, Lan
       L.s = 0.0;
       L.p2 = 0.0;
     }
-    const U4 b = L.rs.next();
+    const U4 b = draw<PREC>(P, L);
     L.tauS = -log(u01d(b.x, b.y));
     L.tauA = -log(u01d(b.z, b.w));
   } else {
-    const U4 a = L.rs.next();
     const float u = u01f_word(a.x), u_phi = u01f_word(a.y);
     const int f = L.f;
     float mu_s, st2;
@@ -383,9 +518,8 @@ __device__ __forceinline__ void scatter(const TransportParams &P, Shared &S, Lan
       const float mup = mu * mu_s + sth * st * cp;
       // sin^2 of the new radial angle from |r_hat x d'|^2 (no 1 - mu'^2 cancellation)
       const float q = mu * st * cp - sth * mu_s;
-      const float sin2 = st2 * sp * sp + q * q;
       L.s = r * mup;
-      L.p2 = r2 * sin2;
+      L.p2 = r2 * (st2 * sp * sp + q * q);
     } else {
       L.s = 0.0f;
       L.p2 = 0.0f;
@@ -393,7 +527,7 @@ __device__ __forceinline__ void scatter(const TransportParams &P, Shared &S, Lan
     L.tauS = -__logf(u01f_word(a.z));
     L.tauA = -__logf(u01f_word(a.w));
   }
-  T.c[CNT_SCATTER]++;
+  T.scat++;
   if constexpr (RECORD) L.nsca++;
   record<RECORD>(L, EV_SCATTER, L.cell, L.f);
 }
@@ -401,24 +535,23 @@ __device__ __forceinline__ void scatter(const TransportParams &P, Shared &S, Lan
 // ---------------------------------------------- absorption + re-emission
 template <int PREC, int MODE, bool RECORD>
 __device__ __forceinline__ void absorb(const TransportParams &P, Shared &S, const float *sLnode,
-                                       Lane<typename RealOf<PREC>::T> &L, Tally &T) {
-  using Real = typename RealOf<PREC>::T;
+                                       Lane<typename RealOf<PREC>::T> &L, Tally &T, const U4 &a) {
   const int gc = L.cell_off + L.cell;
-  T.c[CNT_ABSORB]++;
+  T.abs++;
   if constexpr (RECORD) L.nabs++;
-  const double dE = (double)L.w * L.eps;
   if constexpr (MODE == MODE_FROZEN_TERMINAL) {
-    atomicAdd(P.E + gc, dE);
+    atomicAdd(P.E + gc, (double)L.w * (double)L.eps);
     record<RECORD>(L, EV_ABSORB, L.cell, L.f);
     finish<RECORD>(P, L);
     return;
   }
   if constexpr (PREC == PREC_FP64) {
-    const U4 a = L.rs.next();
+    const double dE = L.w * L.eps;
     const double u_e = u01d(a.x, a.y), u_nu = u01d(a.z, a.w);
+    int f;
     if constexpr (MODE == MODE_FROZEN) {
       atomicAdd(P.E + gc, dE);
-      L.f = cdf_pick_ldg(P.cell_cdf + (size_t)gc * kMaxFreq, u_nu);
+      f = cdf_pick_ldg(P.cell_cdf + (size_t)gc * kMaxFreq, u_nu);
     } else {
       const double old = atomicAdd(P.E + gc, dE);
       const double im = __ldg(P.inv_mass + gc);
@@ -426,49 +559,41 @@ __device__ __forceinline__ void absorb(const TransportParams &P, Shared &S, cons
       const double es = eo + u_e * (en - eo);
       int j = node_count_f(sLnode, P.n_tnodes_pow2, (float)es);
       j = node_count_d(P.Lnode_d, P.n_tnodes, min(j, P.n_tnodes), es);
-      if (en > __ldg(P.Lnode_d + P.n_tnodes - 1)) T.c[CNT_CLAMP_HI]++;
+      if (en > __ldg(P.Lnode_d + P.n_tnodes - 1)) atomicAdd(&S.rare[CNT_CLAMP_HI], 1u);
       const int row = min(j, P.n_tnodes - 1);
-      L.f = cdf_pick_ldg(P.dcdf_d + ((size_t)row << kFreqShift), u_nu);
+      f = cdf_pick_ldg(P.dcdf_d + ((size_t)row << kFreqShift), u_nu);
     }
-    const U4 b = L.rs.next();
+    set_freq<PREC>(S, L, f);
+    const U4 b = draw<PREC>(P, L);
     const double mu = 2.0 * u01d(b.x, b.y) - 1.0;
     const double r2 = L.p2 + L.s * L.s;
     const double r = sqrt(r2);
     L.s = r * mu;
     L.p2 = fmax(r2 - L.s * L.s, 0.0);
-    const U4 c = L.rs.next();
+    const U4 c = draw<PREC>(P, L);
     L.tauS = -log(u01d(c.x, c.y));
     L.tauA = -log(u01d(c.z, c.w));
   } else {
     // one Philox block gives five 23-bit uniforms (4 x top bits + 1 from the low bits)
-    const U4 a = L.rs.next();
     const float u_e = u01f_word(a.x), u_nu = u01f_word(a.y), u_mu = u01f_word(a.z);
     const float u_ts = u01f_word(a.w);
     const float u_ta = u01f((a.x & 0x1ffu) | ((a.y & 0x1ffu) << 9) | ((a.z & 0x1fu) << 18));
-    int row;
+    const float dEf = L.w * L.eps;
+    const float im = __ldg(P.inv_massf + gc);
+    float eo;
     if constexpr (PREC == PREC_MIXED) {
-      const double old = atomicAdd(P.E + gc, dE);
-      const double im = __ldg(P.inv_mass + gc);
-      const double eo = old * im, en = (old + dE) * im;
-      const double es = eo + (double)u_e * (en - eo);
-      int j = node_count_f(sLnode, P.n_tnodes_pow2, (float)es);
-      j = node_count_d(P.Lnode_d, P.n_tnodes, min(j, P.n_tnodes), es);
-      if (en > __ldg(P.Lnode_d + P.n_tnodes - 1)) T.c[CNT_CLAMP_HI]++;
-      row = min(j, P.n_tnodes - 1);
+      // FP64 accumulator; its old value gives e_old, the lookup is FP32
+      eo = (float)atomicAdd(P.E + gc, (double)dEf) * im;
     } else {
       // FP32 form: two FP32 counters, E = E_prev (frozen in this batch) + E_cur
-      const float dEf = (float)dE;
-      const float oc = atomicAdd(P.Ecur + gc, dEf);
-      const float Eo = __ldg(P.Eprev + gc) + oc;
-      const float En = Eo + dEf;
-      const float im = __ldg(P.inv_massf + gc);
-      const float eo = Eo * im, en = En * im;
-      const float es = fmaf(u_e, en - eo, eo);
-      const int j = node_count_f(sLnode, P.n_tnodes_pow2, es);
-      if (en > sLnode[P.n_tnodes - 1]) T.c[CNT_CLAMP_HI]++;
-      row = min(j, P.n_tnodes - 1);
+      eo = (__ldg(P.Eprev + gc) + atomicAdd(P.Ecur + gc, dEf)) * im;
     }
-    L.f = cdf_pick_ldg(P.dcdf_f + ((size_t)row << kFreqShift), u_nu);
+    const float de = dEf * im;
+    const float es = fmaf(u_e, de, eo);
+    const int j = node_count_f(sLnode, P.n_tnodes_pow2, es);
+    if (eo + de > sLnode[P.n_tnodes - 1]) atomicAdd(&S.rare[CNT_CLAMP_HI], 1u);
+    const int row = min(j, P.n_tnodes - 1);
+    set_freq<PREC>(S, L, cdf_pick_ldg(P.dcdf_f + ((size_t)row << kFreqShift), u_nu));
     // isotropic re-emission: mu' = 2u - 1, sin^2 = 4u(1-u)
     const float r2 = L.p2 + L.s * L.s;
     const float r = sqrtf(r2);
@@ -480,96 +605,23 @@ __device__ __forceinline__ void absorb(const TransportParams &P, Shared &S, cons
   record<RECORD>(L, EV_ABSORB, L.cell, L.f);
 }
 
-// ------------------------------------------------------------ one event
+// The rare-event path for one parked lane.
 template <int PREC, int MODE, bool RECORD>
-__device__ __forceinline__ void step(const TransportParams &P, Shared &S, const float *sLnode,
+__device__ __forceinline__ void rare(const TransportParams &P, Shared &S, const float *sLnode,
                                      Lane<typename RealOf<PREC>::T> &L, Tally &T) {
-  using Real = typename RealOf<PREC>::T;
-  if (L.phase == PH_NORMAL && L.events >= P.max_events) {
-    lose<RECORD>(P, L, T, CNT_KILL_CAP);
-    return;
-  }
-  Real l, sb;
-  int next;
-  boundary<PREC>(P, L, l, sb, next);
-  Real ka = Real(0), ks = Real(0);
-  if (L.cell >= 0) {
-    if constexpr (PREC == PREC_FP64) {
-      const double rho = __ldg(P.rhod + L.cell_off + L.cell);
-      ka = S.kabs_d[L.f] * rho;
-      ks = S.ksca_d[L.f] * rho;
-    } else {
-      const float rho = __ldg(P.rhof + L.cell_off + L.cell);
-      ka = S.kabs_f[L.f] * rho;
-      ks = S.ksca_f[L.f] * rho;
+  const int kind = L.pend;
+  if constexpr (PREC != PREC_FP64) {
+    // the FP32 forms interrupt a package only here, so the event cap is checked here
+    if (kind != PEND_INJECT && ++L.events >= P.max_events) {
+      lose<RECORD>(P, S, L, CNT_KILL_CAP);
+      return;
     }
   }
-  if (L.phase == PH_PREWALK) {
-    // total extinction optical depth to the surface (Sect. 2.2.2)
-    L.acc += (ka + ks) * l;
-    L.s = sb;
-    L.cell = next;
-    if (next >= L.n) {
-      const Real tau0 = L.acc;
-      Real q;
-      if constexpr (PREC == PREC_FP64) q = -expm1(-tau0);
-      else q = -expm1f(-tau0);
-      const double e_direct = (double)L.w * L.eps * (1.0 - (double)q);
-      if (P.n_models == 1) atomicAdd(&S.sed[L.f], e_direct);
-      else atomicAdd(P.sed + (size_t)L.model * kMaxFreq + L.f, e_direct);
-      T.e_direct += e_direct;
-      L.w *= q;
-      if (!(q > Real(0))) {
-        T.c[CNT_ESCAPED]++;
-        finish<RECORD>(P, L);
-      } else if (L.w < Real(1e-10)) {
-        lose<RECORD>(P, L, T, CNT_KILL_WEIGHT);
-      } else {
-        Real ti;
-        if constexpr (PREC == PREC_FP64) ti = -log1p(-L.tau_int * q);  // Eq. 10
-        else ti = -log1pf(-L.tau_int * q);
-        L.tau_int = (ti > tau0) ? tau0 : ti;
-        T.c[CNT_FORCED]++;
-        L.s = L.s0;
-        L.cell = L.cell0;
-        L.acc = Real(0);
-        L.phase = PH_FORCED;
-      }
-    }
-    return;
-  }
-  L.events++;
-  if (L.phase == PH_FORCED) {
-    const Real ke = ka + ks;
-    if (ke > Real(0) && L.acc + ke * l >= L.tau_int) {
-      Real li = (L.tau_int - L.acc) / ke;
-      li = li > l ? l : li;
-      li = li < Real(0) ? Real(0) : li;
-      L.s += li;
-      L.phase = PH_NORMAL;
-      if (L.u_type * ke < ka) absorb<PREC, MODE, RECORD>(P, S, sLnode, L, T);
-      else scatter<PREC, RECORD>(P, S, L, T);
-    } else {
-      L.acc += ke * l;
-      cross<RECORD>(P, S, L, T, sb, next);
-    }
-    return;
-  }
-  // normal transport: competing free paths (Eqs. 1 and 4); the boundary wins
-  // ties, and an interaction in a cell without absorption is a scattering
-  const Real ta = ka * l, ts = ks * l;
-  if (L.tauA >= ta && L.tauS >= ts) {
-    L.tauA -= ta;
-    L.tauS -= ts;
-    cross<RECORD>(P, S, L, T, sb, next);
-  } else if (ka <= Real(0) || L.tauS * ka < L.tauA * ks) {
-    L.s += L.tauS / ks;
-    scatter<PREC, RECORD>(P, S, L, T);
-  } else {
-    L.s += L.tauA / ka;
-    absorb<PREC, MODE, RECORD>(P, S, sLnode, L, T);
-  }
-  if (L.phase != PH_DEAD && L.w < Real(1e-10)) lose<RECORD>(P, L, T, CNT_KILL_WEIGHT);
+  const U4 a = draw<PREC>(P, L);  // every rare event starts with one Philox block
+  L.pend = PEND_NONE;
+  if (kind == PEND_INJECT) inject<PREC, RECORD>(P, S, L, T, a);
+  else if (kind == PEND_SCATTER) scatter<PREC, RECORD>(P, S, L, T, a);
+  else absorb<PREC, MODE, RECORD>(P, S, sLnode, L, T, a);
 }
 
 __device__ __forceinline__ unsigned long long globaltimer() {
@@ -602,38 +654,50 @@ __global__ void __launch_bounds__(256) k_transport(const TransportParams P) {
     for (int s = 0; s < 2; ++s) {
       S.src_cdf_d[s][k] = P.src_cdf_d[s * kMaxFreq + k];
       S.src_cdf_f[s][k] = (float)P.src_cdf_d[s * kMaxFreq + k];
+      S.sed_q[s][k] = 0ULL;
     }
     S.sed[k] = 0.0;
   }
+  if (threadIdx.x < 2) {
+    S.inj_q[threadIdx.x] = 0ULL;
+    S.dir_q[threadIdx.x] = 0ULL;
+  }
+  if (threadIdx.x < CNT_COUNT) S.rare[threadIdx.x] = 0u;
   for (int j = threadIdx.x; j < P.n_tnodes_pow2; j += blockDim.x) sLnode[j] = P.Lnode_f[j];
   __syncthreads();
 
   Tally T;
-#pragma unroll
-  for (int i = 0; i < CNT_COUNT; ++i) T.c[i] = 0;
-  T.e_inj = T.e_lost = T.e_direct = 0.0;
+  T.cross = T.scat = T.abs = 0;
+  T.e_inj = T.e_direct = 0.0;
 
   Lane<Real> L;
   L.phase = PH_DEAD;
+  L.pend = PEND_NONE;
   bool exhausted = false;
   const int lane = threadIdx.x & 31;
   const unsigned long long t0 = globaltimer();
   unsigned iter = 0;
   for (;;) {
-    const unsigned need = __ballot_sync(kFull, L.phase == PH_DEAD && !exhausted);
-    if (need) {
-      const int leader = __ffs(need) - 1;
-      unsigned long long base = 0;
-      if (lane == leader) base = atomicAdd(P.queue, (unsigned long long)__popc(need));
-      base = __shfl_sync(kFull, base, leader);
-      if (need & (1u << lane)) {
-        const unsigned long long g = base + __popc(need & ((1u << lane) - 1u));
-        if (g < P.total) inject<PREC, RECORD>(P, S, L, g, T);
-        else exhausted = true;
+    if (L.phase != PH_DEAD && L.pend == PEND_NONE) move<PREC, MODE, RECORD>(P, S, L, T);
+    const unsigned waiting = __ballot_sync(kFull, L.pend != PEND_NONE || (L.phase == PH_DEAD && !exhausted));
+    const unsigned moving = __ballot_sync(kFull, L.phase != PH_DEAD && L.pend == PEND_NONE);
+    if ((waiting | moving) == 0u) break;
+    if (moving == 0u || __popc(waiting) >= P.batch_min) {
+      // refill finished lanes from the work counter (one atomic per warp)
+      const unsigned need = __ballot_sync(kFull, L.phase == PH_DEAD && !exhausted);
+      if (need) {
+        const int leader = __ffs(need) - 1;
+        unsigned long long base = 0;
+        if (lane == leader) base = atomicAdd(P.queue, (unsigned long long)__popc(need));
+        base = __shfl_sync(kFull, base, leader);
+        if (need & (1u << lane)) {
+          const unsigned long long g = base + __popc(need & ((1u << lane) - 1u));
+          if (g < P.total) assign<PREC, RECORD>(P, L, g);
+          else exhausted = true;
+        }
       }
+      if (L.pend != PEND_NONE) rare<PREC, MODE, RECORD>(P, S, sLnode, L, T);
     }
-    if (!__any_sync(kFull, L.phase != PH_DEAD)) break;
-    if (L.phase != PH_DEAD) step<PREC, MODE, RECORD>(P, S, sLnode, L, T);
     if ((++iter & 1023u) == 0) {
       const bool late = (globaltimer() - t0) > P.time_budget_ns;
       if (__shfl_sync(kFull, late, 0)) {
@@ -643,26 +707,61 @@ __global__ void __launch_bounds__(256) k_transport(const TransportParams P) {
     }
   }
 
-  // counters: warp reduction, one atomic per warp
+  // frequent counters: warp reduction, one atomic per warp
+  const uint32_t freq_cnt[3] = {T.cross, T.scat, T.abs};
+  const int freq_idx[3] = {CNT_CROSS, CNT_SCATTER, CNT_ABSORB};
 #pragma unroll
-  for (int i = 0; i < CNT_COUNT; ++i) {
-    unsigned long long v = T.c[i];
+  for (int i = 0; i < 3; ++i) {
+    unsigned long long v = freq_cnt[i];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
-    if (lane == 0 && v) atomicAdd(P.counters + i, v);
+    if (lane == 0 && v) atomicAdd(P.counters + freq_idx[i], v);
   }
-  double ev[EN_COUNT] = {T.e_inj, T.e_lost, T.e_direct};
+  if constexpr (PREC == PREC_FP64) {
+    double ev[2] = {T.e_inj, T.e_direct};
+    const int ei[2] = {EN_INJECTED, EN_DIRECT};
 #pragma unroll
-  for (int i = 0; i < EN_COUNT; ++i) {
-    double v = ev[i];
+    for (int i = 0; i < 2; ++i) {
+      double v = ev[i];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
-    if (lane == 0 && v != 0.0) atomicAdd(P.energies + i, v);
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+      if (lane == 0 && v != 0.0) atomicAdd(P.energies + ei[i], v);
+    }
   }
   __syncthreads();
-  if (P.n_models == 1)
-    for (int k = threadIdx.x; k < P.F; k += blockDim.x)
-      if (S.sed[k] != 0.0) atomicAdd(P.sed + k, S.sed[k]);
+  for (int i = threadIdx.x; i < CNT_COUNT; i += blockDim.x)
+    if (S.rare[i]) atomicAdd(P.counters + i, (unsigned long long)S.rare[i]);
+  if (P.n_models == 1) {
+    if constexpr (PREC == PREC_FP64) {
+      for (int k = threadIdx.x; k < P.F; k += blockDim.x)
+        if (S.sed[k] != 0.0) atomicAdd(P.sed + k, S.sed[k]);
+    } else {
+      for (int i = threadIdx.x; i < 2 * kMaxFreq; i += blockDim.x)
+        if (S.sed_q[i >> 6][i & 63]) atomicAdd(P.sed_q + i, S.sed_q[i >> 6][i & 63]);
+      if (threadIdx.x < 2) {
+        if (S.inj_q[threadIdx.x]) atomicAdd(P.inj_q + threadIdx.x, S.inj_q[threadIdx.x]);
+        if (S.dir_q[threadIdx.x]) atomicAdd(P.dir_q + threadIdx.x, S.dir_q[threadIdx.x]);
+      }
+    }
+  }
+}
+
+// FP32 forms: convert the fixed-point tallies of every model to energies
+// (one block of 64 threads per model).
+__global__ void k_tally(const ModelDesc *desc, unsigned long long n_per_source, const unsigned long long *sed_q,
+                        const unsigned long long *inj_q, const unsigned long long *dir_q, double *sed,
+                        double *energies) {
+  const int m = blockIdx.x, k = threadIdx.x;
+  const double unit = 1.0 / (double)kQuantum;
+  const double e0 = desc[m].L[0] / (double)n_per_source, e1 = desc[m].L[1] / (double)n_per_source;
+  const unsigned long long *q = sed_q + (size_t)m * 2 * kMaxFreq;
+  sed[(size_t)m * kMaxFreq + k] = ((double)q[k] * e0 + (double)q[kMaxFreq + k] * e1) * unit;
+  if (k == 0) {
+    const double inj = ((double)inj_q[2 * m] * e0 + (double)inj_q[2 * m + 1] * e1) * unit;
+    const double dir = ((double)dir_q[2 * m] * e0 + (double)dir_q[2 * m + 1] * e1) * unit;
+    if (inj != 0.0) atomicAdd(energies + EN_INJECTED, inj);
+    if (dir != 0.0) atomicAdd(energies + EN_DIRECT, dir);
+  }
 }
 
 // Temperature of every cell from its absorbed energy: log-log interpolation
@@ -750,6 +849,14 @@ cudaError_t transport_occupancy(int prec, int mode, int block, int n_tnodes_pow2
     case PREC_FP32: return occupancy_one<PREC_FP32, MODE_IRE, false>(block, smem, blocks_per_sm);
     default: return occupancy_one<PREC_FP64, MODE_IRE, false>(block, smem, blocks_per_sm);
   }
+}
+
+cudaError_t launch_tally(cudaStream_t st, int n_models, const ModelDesc *desc, unsigned long long n_per_source,
+                         const unsigned long long *sed_q, const unsigned long long *inj_q,
+                         const unsigned long long *dir_q, double *sed, double *energies) {
+  k_tally<<<n_models, kMaxFreq, 0, st>>>(desc, n_per_source, sed_q, inj_q, dir_q, sed, energies);
+  launch_counter_add(1);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_finalize(cudaStream_t st, int n_cells, const double *E, const float *Eprev, const float *Ecur,
