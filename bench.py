@@ -4,8 +4,8 @@
 Workload (one "step"): the externally heated sweep of 128 equal shells with
 central A_V in {1, 10, 100}, each run plain, with centre-biased background
 directions (k_bg = 1/3) and with forced first interaction: 9 runs of 1e8
-packages = 9e8 packages per step, mixed precision (FP32 stepping, FP64
-inner-shell crossings, accumulators and temperature lookup).
+packages = 9e8 packages per step, mixed precision (FP32 stepping and
+sampling, FP64 absorbed-energy accumulators and temperature inversion).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -55,7 +55,8 @@ def workload_config(n_per_run):
                     "x {plain, k_bg=1/3 (p'(mu)~mu^2), forced first interaction}, 64 frequencies, "
                     f"{n_per_run:.0e} packages per run, 9 runs per step",
         "packages_per_step": 9 * n_per_run,
-        "precision": "mixed (FP32 stepping/sampling, FP64 accumulators, temperature lookup, inner crossings)",
+        "precision": "mixed (FP32 stepping and sampling, compensated FP32 R^2-p^2, FP64 absorbed-energy "
+                     "accumulators and temperature inversion)",
         "l2": "flushed between steps (256 MB device write)",
         "inputs": "synthetic (seeded stand-ins for the paper's Bonnor-Ebert clouds, dust and field)",
     }
@@ -228,6 +229,73 @@ def accuracy_vs_oracle(T_runs):
     return worst
 
 
+def golden_mean(name):
+    p = os.path.join(ROOT, "tests", "golden", f"{name}_oracle.npz")
+    if not os.path.exists(p):
+        return None, None
+    g = np.load(p)
+    return g["mean"], g["se"]
+
+
+def measure_batch(D, autotune, n_per_model: int, reps: int = 2):
+    """Models/s of the 4096-model parameter study in one persistent launch."""
+    from paper_2408_13807_gb300 import workloads as W
+    clouds = W.config4_models()
+    shape = autotune.best_batch_launch(clouds)
+    b = D.Batch(clouds, **shape)
+    b.run(10_000, seed=1)
+    ts = []
+    for r in range(reps):
+        b.run(n_per_model, seed=2 + r)
+        ts.append(b.stats()["transport_ms"])
+    st = b.stats()
+    b.close()
+    t = min(ts) * 1e-3
+    return {"workload": f"{len(clouds)} models (16-256 shells, A_V 0.3-300, 75% external), "
+                        f"{n_per_model:.0e} packages each, one persistent launch",
+            "models_per_s": len(clouds) / t, "packages_per_s": len(clouds) * n_per_model / t,
+            "transport_ms": min(ts), "launch_shape": shape, "events_per_package": (
+                st["crossed"] + st["scattered"] + st["absorbed"]) / max(1, st["injected"])}
+
+
+def measure_precision_forms(D, autotune):
+    """The all-FP32 form (with and without the batches of Sect. 2.3) and the
+    FP64 form, each with its largest temperature error against the stored
+    FP64-oracle means (shells where the oracle's 3-sigma is below 1 %)."""
+    from paper_2408_13807_gb300 import workloads as W
+    out = {}
+    mean, se = golden_mean("c3")
+    c3 = W.config3()
+    for label, prec, nb in (("mixed", "mixed", 1), ("fp32_NB50", "fp32", 50), ("fp32_NB1", "fp32", 1)):
+        m = D.Model(c3, precision=prec, n_batches=nb, **autotune.best_launch(c3, prec))
+        m.run(1_000_000, seed=1)
+        m.run(100_000_000, seed=2)
+        st = m.stats()
+        T = m.temperatures()
+        m.close()
+        rec = {"packages_per_s": 1e8 / (st["transport_ms"] * 1e-3)}
+        if mean is not None:
+            gate = 3 * se[0] <= 0.01 * mean[0]
+            d = T / mean[0] - 1.0
+            rec["max_rel_T_error"] = float(np.max(np.abs(d[gate])))
+            rec["mean_rel_T_error_inner8"] = float(np.mean(d[:8]))
+        out[label] = rec
+    c1 = W.config1()
+    m = D.Model(c1, precision="fp64", **autotune.best_launch(c1, "fp64"))
+    m.run(100_000, seed=1)
+    m.run(10_000_000, seed=2)
+    out["fp64_form_C1"] = {"packages_per_s": 1e7 / (m.stats()["transport_ms"] * 1e-3)}
+    m.close()
+    m = D.Model(c1, precision="mixed", **autotune.best_launch(c1, "mixed"))
+    m.run(100_000, seed=1)
+    m.run(10_000_000, seed=2)
+    out["mixed_form_C1"] = {"packages_per_s": 1e7 / (m.stats()["transport_ms"] * 1e-3)}
+    m.close()
+    out["workload"] = ("C3 point source, 256 log shells, tau_V = 100, 1e8 packages, one seed, error vs the "
+                       "oracle's 16-seed mean; C1 32 shells A_V = 10, 1e7 packages")
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -247,8 +315,13 @@ def run_ours(args):
     if args.runs:
         clouds = [clouds[int(i)] for i in args.runs.split(",")]
     n = args.n_per_run
-    models = [D.Model(c, precision="mixed", fp64_radius=args.fp64_radius, block_size=args.block,
-                      blocks_per_sm=args.blocks_per_sm) for c in clouds]
+    from paper_2408_13807_gb300 import autotune
+    if args.block:
+        shapes = [{"block_size": args.block, "blocks_per_sm": args.blocks_per_sm, "rare_batch": args.rare_batch}
+                  for _ in clouds]
+    else:
+        shapes = [autotune.best_launch(c, "mixed") for c in clouds]  # tuned here if not cached (untimed)
+    models = [D.Model(c, precision="mixed", fp64_radius=args.fp64_radius, **sh) for c, sh in zip(clouds, shapes)]
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     seed_base = 1_000_000 * rank
 
@@ -299,7 +372,7 @@ def run_ours(args):
         t = time.perf_counter()
         h2d = d2h = 0
         for i, c in enumerate(clouds):
-            m = D.Model(c, precision="mixed", fp64_radius=args.fp64_radius)
+            m = D.Model(c, precision="mixed", fp64_radius=args.fp64_radius, **shapes[i])
             m.run(n, seed=seed_base + 500 + 16 * k + i)
             T, sed = m.temperatures(), m.sed()
             h2d += (c.radii.nbytes + c.rho.nbytes + 6 * 64 * 8 + 64)
@@ -330,6 +403,10 @@ def run_ours(args):
     launches_per_step = launches / args.steps
     traffic = traffic_from_profile()
 
+    extra = {}
+    if not args.no_extras:
+        extra["batched"] = measure_batch(D, autotune, args.batch_n)
+        extra["precision_forms"] = measure_precision_forms(D, autotune)
     cpu_rate, cpu_n, cpu_dt = oracle_rate(clouds, args.ref_seconds) if not args.no_cpu_baseline else (None, 0, 0)
     cfg = workload_config(n)
     if args.runs:
@@ -360,6 +437,8 @@ def run_ours(args):
         "atomics_per_s": stats_acc["absorbed"] / t_transport,
         "events_per_package": {k: stats_acc[k] / max(1, stats_acc["injected"]) for k in ("crossed", "scattered", "absorbed")},
         "max_rel_T_error_vs_oracle": accuracy_vs_oracle(T_runs),
+        "launch_shapes": shapes,
+        **extra,
     }
     print(json.dumps(line))
     if dist is not None:
@@ -375,11 +454,14 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n-per-run", type=int, default=N_PER_RUN)
     ap.add_argument("--ref-seconds", type=float, default=15.0)
-    ap.add_argument("--block", type=int, default=256)
+    ap.add_argument("--block", type=int, default=0, help="fixed block size (0 = autotuned launch shapes)")
     ap.add_argument("--blocks-per-sm", type=int, default=0)
-    ap.add_argument("--fp64-radius", type=float, default=0.05)
+    ap.add_argument("--rare-batch", type=int, default=8)
+    ap.add_argument("--fp64-radius", type=float, default=0.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batch and precision-form measurements")
+    ap.add_argument("--batch-n", type=int, default=1_000_000, help="packages per model of the batched study")
     ap.add_argument("--runs", default="", help="comma-separated indices of the 9 sweep runs (profiling cases)")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -1,0 +1,131 @@
+"""Launch-shape autotuner for the IRE transport kernel.
+
+For a cloud model (or a batch of models) it times short runs over a small
+grid of (block size, CTAs per SM, rare_batch) and keeps the fastest.  Results
+are cached per "config class" (precision, weighting, source kind, shell-count
+and optical-depth buckets) in ``tune_cache.json`` next to this file; a class
+missing from the cache is tuned on the spot (on the GPU, through the same C
+ABI as the runs it tunes).
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import threading
+from typing import Dict, Iterable, Optional, Tuple
+
+from . import dies as D
+
+CACHE_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_cache.json")
+GRID_BLOCK = (128, 256)
+GRID_RARE = (4, 8, 12, 16, 24)
+GRID_BPS = (0,)
+DEFAULT = {"block_size": 256, "blocks_per_sm": 0, "rare_batch": 8}
+
+_lock = threading.Lock()
+_cache: Optional[Dict[str, dict]] = None
+
+
+def _load() -> Dict[str, dict]:
+    global _cache
+    if _cache is None:
+        try:
+            with open(CACHE_PATH) as f:
+                _cache = json.load(f)
+        except (OSError, ValueError):
+            _cache = {}
+    return _cache
+
+
+def _save():
+    try:
+        tmp = CACHE_PATH + f".tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(_load(), f, indent=1, sort_keys=True)
+        os.replace(tmp, CACHE_PATH)
+    except OSError:
+        pass
+
+
+def config_class(cloud, precision: str) -> str:
+    """Key of the tuning cache: what the best launch shape depends on."""
+    tau_bucket = int(round(math.log10(max(float((cloud.kabs.max() + cloud.ksca.max()) *
+                                                (cloud.rho * (cloud.radii[1:] - cloud.radii[:-1])).sum()), 1e-3))))
+    n_bucket = int(round(math.log2(max(cloud.n_cells, 1))))
+    kind = ("ext" if cloud.J_ext is not None else "") + ("pt" if cloud.L_point > 0 else "")
+    return f"{precision}|{kind}|n2^{n_bucket}|tau10^{tau_bucket}|kbg{cloud.k_bg:.3f}|ffi{int(bool(cloud.ffi))}"
+
+
+def _time_model(cloud, precision: str, shape: dict, n: int, reps: int = 2) -> float:
+    m = D.Model(cloud, precision=precision, **shape)
+    try:
+        m.run(min(n, 200_000), seed=7)  # tables + warm-up
+        best = float("inf")
+        for r in range(reps):
+            m.run(n, seed=11 + r)
+            best = min(best, m.stats()["transport_ms"])
+        return best
+    finally:
+        m.close()
+
+
+def tune(cloud, precision: str = "mixed", n: int = 4_000_000, blocks: Iterable[int] = GRID_BLOCK,
+         rare: Iterable[int] = GRID_RARE, bps: Iterable[int] = GRID_BPS) -> Tuple[dict, dict]:
+    """Time every shape of the grid on ``cloud``; return (best shape, timings)."""
+    times = {}
+    for b in blocks:
+        for k in bps:
+            for r in rare:
+                shape = {"block_size": b, "blocks_per_sm": k, "rare_batch": r}
+                times[f"{b}/{k}/{r}"] = _time_model(cloud, precision, shape, n)
+    key = min(times, key=times.get)
+    b, k, r = (int(x) for x in key.split("/"))
+    return {"block_size": b, "blocks_per_sm": k, "rare_batch": r, "ms": times[key], "n": n}, times
+
+
+def best_launch(cloud, precision: str = "mixed", allow_tuning: bool = True, n: int = 4_000_000) -> dict:
+    """Cached best launch shape for the config class of ``cloud``; tuned and
+    cached on first use when ``allow_tuning`` (needs a GPU)."""
+    key = config_class(cloud, precision)
+    with _lock:
+        c = _load()
+        if key in c:
+            return {k: c[key][k] for k in ("block_size", "blocks_per_sm", "rare_batch")}
+    if not allow_tuning:
+        return dict(DEFAULT)
+    best, _ = tune(cloud, precision, n)
+    with _lock:
+        _load()[key] = best
+        _save()
+    return {k: best[k] for k in ("block_size", "blocks_per_sm", "rare_batch")}
+
+
+def best_batch_launch(clouds, allow_tuning: bool = True, n_per_model: int = 20_000) -> dict:
+    """Best launch shape for a parameter-study batch (timed on the batch itself)."""
+    key = f"batch|{len(clouds)}|n_avg{int(sum(c.n_cells for c in clouds) / len(clouds))}"
+    with _lock:
+        c = _load()
+        if key in c:
+            return {k: c[key][k] for k in ("block_size", "blocks_per_sm", "rare_batch")}
+    if not allow_tuning:
+        return dict(DEFAULT)
+    times = {}
+    for b in GRID_BLOCK:
+        for r in GRID_RARE:
+            bt = D.Batch(clouds, block_size=b, rare_batch=r)
+            try:
+                bt.run(2_000, seed=3)
+                best = float("inf")
+                for rep in range(2):
+                    bt.run(n_per_model, seed=5 + rep)
+                    best = min(best, bt.stats()["transport_ms"])
+                times[(b, r)] = best
+            finally:
+                bt.close()
+    (b, r) = min(times, key=times.get)
+    rec = {"block_size": b, "blocks_per_sm": 0, "rare_batch": r, "ms": times[(b, r)], "n": n_per_model}
+    with _lock:
+        _load()[key] = rec
+        _save()
+    return {k: rec[k] for k in ("block_size", "blocks_per_sm", "rare_batch")}

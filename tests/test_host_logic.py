@@ -1,0 +1,73 @@
+"""Host-side logic that needs no GPU: workload generators, autotuner keys,
+bench helpers."""
+import json
+import os
+import sys
+
+import numpy as np
+import pytest
+
+from paper_2408_13807_gb300 import autotune
+from paper_2408_13807_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_workloads_match_their_stated_extinction():
+    kv = W.kext_v()
+    for m, av in ((W.config1(), 10.0), (W.config2(100.0), 100.0), (W.config2(1.0, "ffi"), 1.0)):
+        tau = np.sum(kv * m.rho * np.diff(m.radii))
+        assert tau * W.AV_PER_TAU_V == pytest.approx(av, rel=1e-12)
+    c3 = W.config3()
+    assert np.sum(W.kext_v() * c3.rho * np.diff(c3.radii)) == pytest.approx(100.0, rel=1e-12)
+    c5 = W.config5_internal()
+    assert np.sum(W.kext_at(1.0) * c5.rho * np.diff(c5.radii)) == pytest.approx(1000.0, rel=1e-12)
+    assert c3.radii[0] == pytest.approx(1e-3) and c5.radii[0] == pytest.approx(1e-6)
+
+
+def test_workloads_are_deterministic_and_valid():
+    a, b = W.config4_models(50), W.config4_models(50)
+    for x, y in zip(a, b):
+        assert np.array_equal(x.radii, y.radii) and np.array_equal(x.rho, y.rho)
+        assert 16 <= x.n_cells <= 256 and np.all(np.diff(x.radii) > 0) and np.all(x.rho >= 0)
+    kinds = [m.J_ext is not None for m in W.config4_models()]
+    assert 0.70 < np.mean(kinds) < 0.80
+    f = W.freq_grid()
+    assert np.all(np.diff(f) > 0) and len(f) == 64
+    ka, ks, g = W.dust_tables(f)
+    assert np.all(ka > 0) and np.all(ks >= 0) and np.all(np.abs(g) < 1)
+
+
+def test_sweep_is_nine_runs_with_the_three_weightings():
+    runs = W.config2_sweep()
+    assert len(runs) == 9
+    assert {(m.k_bg, m.ffi) for m in runs} == {(0.5, False), (1.0 / 3.0, False), (0.5, True)}
+    assert all(m.n_cells == 128 for m in runs)
+
+
+def test_autotune_config_class_separates_what_matters():
+    k = {autotune.config_class(m, "mixed") for m in W.config2_sweep()}
+    assert len(k) == 9
+    assert autotune.config_class(W.config1(), "mixed") != autotune.config_class(W.config1(), "fp32")
+
+
+def test_autotune_uses_cache_without_gpu(tmp_path, monkeypatch):
+    cache = tmp_path / "tune.json"
+    m = W.config1()
+    key = autotune.config_class(m, "mixed")
+    cache.write_text(json.dumps({key: {"block_size": 128, "blocks_per_sm": 0, "rare_batch": 12, "ms": 1.0}}))
+    monkeypatch.setattr(autotune, "CACHE_PATH", str(cache))
+    monkeypatch.setattr(autotune, "_cache", None)
+    assert autotune.best_launch(m, "mixed", allow_tuning=False) == {"block_size": 128, "blocks_per_sm": 0,
+                                                                    "rare_batch": 12}
+    assert autotune.best_launch(W.config3(), "mixed", allow_tuning=False) == autotune.DEFAULT
+
+
+def test_bench_reference_arm_runs_on_cpu():
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0", "--ref-seconds", "0.5"], capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == "packages/s"
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
