@@ -95,8 +95,12 @@ typedef struct {
   double table_ms;        /* device time of the table build of this run (0 if cached) */
   double kernel_ms;       /* device time from the accumulator reset to the end of the temperature kernel */
   double transport_ms;    /* device time of the transport launch(es) alone */
-  uint32_t status_word;   /* device-side error flags (0 = none) */
+  uint32_t status_word;   /* device-side error flags: 0 = none, 1 = time budget reached, 8 = flight
+                             watchdog tripped, 16 = a package left unfinished */
   uint32_t launches;      /* kernels launched by this run */
+  uint32_t diag[16];      /* diag[0] = 1: state of the first package ended by the flight
+                             watchdog (state, cell, freq, n, s, p^2, tauA, tauS, kA, kS, w
+                             as float bits, package, model) */
 } dies_stats;
 
 /* ------------------------------------------------------------ one model */

@@ -85,7 +85,7 @@ struct Layout {
   size_t sed_q, inj_q, dir_q;
   size_t freq, kabs, ksca, g, J, spec, dnu, src_cdf_d, src_cdf_f, src_sum;
   size_t Lnode_d, Lnode_f, lnT, dcdf_f, dcdf_d;
-  size_t counters, energies, queue, status;
+  size_t counters, energies, queue, status, diag;
   size_t total;
 };
 
@@ -185,6 +185,7 @@ struct Problem {
     L.energies = seg(8 * 8);
     L.queue = seg(2 * 8);
     L.status = seg(4);
+    L.diag = seg(16 * 4);
     L.total = o;
     return L;
   }
@@ -331,6 +332,7 @@ struct Problem {
     P.counters = at<unsigned long long>(lay.counters);
     P.energies = at<double>(lay.energies);
     P.status = at<uint32_t>(lay.status);
+    P.diag = at<uint32_t>(lay.diag);
     P.k_bg = k_bg;
     P.ffi = ffi;
     P.mode = mode;
@@ -363,6 +365,7 @@ struct Problem {
     DIES_CUDA(cudaMemsetAsync(ws + lay.energies, 0, 8 * 8, stream));
     DIES_CUDA(cudaMemsetAsync(ws + lay.queue, 0, 2 * 8, stream));
     DIES_CUDA(cudaMemsetAsync(ws + lay.status, 0, 4, stream));
+    DIES_CUDA(cudaMemsetAsync(ws + lay.diag, 0, 16 * 4, stream));
     return DIES_OK;
   }
 
@@ -431,6 +434,8 @@ struct Problem {
     DIES_CUDA(cudaMemcpy(cnt, ws + lay.counters, sizeof cnt, cudaMemcpyDeviceToHost));
     DIES_CUDA(cudaMemcpy(en, ws + lay.energies, sizeof en, cudaMemcpyDeviceToHost));
     DIES_CUDA(cudaMemcpy(&status, ws + lay.status, 4, cudaMemcpyDeviceToHost));
+    uint32_t diag[16];
+    DIES_CUDA(cudaMemcpy(diag, ws + lay.diag, sizeof diag, cudaMemcpyDeviceToHost));
     DIES_CUDA(cudaMemcpy(sed.data(), ws + lay.sed, sed.size() * 8, cudaMemcpyDeviceToHost));
     dies_stats s{};
     s.injected = cnt[CNT_INJECTED];
@@ -453,6 +458,7 @@ struct Problem {
     if (cudaEventElapsedTime(&ms, ev[1], ev[4]) == cudaSuccess) s.kernel_ms = ms;
     if (cudaEventElapsedTime(&ms, ev[2], ev[3]) == cudaSuccess) s.transport_ms = ms;
     s.status_word = status;
+    for (int i = 0; i < 16; ++i) s.diag[i] = diag[i];
     s.launches = (uint32_t)(g_launches.load() - launches_at_start);
     stats = s;
     stats_pending = false;
@@ -815,7 +821,8 @@ constexpr size_t kStaticCounters = kStaticCdfBytes;         // 16 x u64
 constexpr size_t kStaticEnergies = kStaticCdfBytes + 128;   // 8 x double
 constexpr size_t kStaticQueue = kStaticCdfBytes + 192;      // 2 x u64
 constexpr size_t kStaticStatus = kStaticCdfBytes + 208;     // u32
-constexpr size_t kStaticZeroBytes = 256;                    // counters .. status
+constexpr size_t kStaticDiag = kStaticCdfBytes + 256;       // 16 x u32
+constexpr size_t kStaticZeroBytes = 320;                    // counters .. diag
 static_assert(kStaticCdfBytes + kStaticZeroBytes <= DIES_STATIC_SCRATCH_BYTES, "static scratch too small");
 }  // namespace
 
@@ -886,6 +893,7 @@ int dies_run_frozen_static(dies_model *m, const double *T_frozen_dev, uint64_t n
   P.energies = reinterpret_cast<double *>(scr + kStaticEnergies);
   P.queue = reinterpret_cast<unsigned long long *>(scr + kStaticQueue);
   P.status = reinterpret_cast<uint32_t *>(scr + kStaticStatus);
+  P.diag = reinterpret_cast<uint32_t *>(scr + kStaticDiag);
   const bool record = n_events_dev || path_hash_dev;
   DIES_CUDA(launch_transport(PREC_FP64, mode, record, P, p.sm_count * bps, p.block, p.stream));
   return DIES_OK;

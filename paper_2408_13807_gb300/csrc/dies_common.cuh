@@ -43,7 +43,13 @@ enum : uint32_t {
   STATUS_TIMEOUT = 1u,
   STATUS_BAD_CELL = 2u,
   STATUS_BAD_FREQ = 4u,
+  STATUS_STUCK = 8u,   // a warp ran kFlightLimit moves without a rare event; its moving lanes were ended
+  STATUS_ABANDONED = 16u,  // a package was still in flight when its lane left the work loop
 };
+
+// Consecutive loop iterations a warp may run without any lane finishing a
+// flight segment; a legitimate flight crosses at most ~2 x shells boundaries.
+constexpr unsigned kFlightLimit = 1u << 22;
 
 struct alignas(16) ModelDesc {
   int cell_off;    // first cell of this model in the per-cell arrays
@@ -108,6 +114,7 @@ struct TransportParams {
   unsigned long long *counters;   // [CNT_COUNT]
   double *energies;               // [EN_COUNT]
   uint32_t *status;
+  uint32_t *diag;                 // [16]: diag[0] = 1 once filled; state of the first stuck lane
   // options
   double k_bg;
   int ffi;

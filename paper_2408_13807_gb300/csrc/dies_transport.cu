@@ -35,8 +35,16 @@ namespace {
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 constexpr unsigned kFull = 0xffffffffu;
 
-enum Phase { PH_DEAD = 0, PH_PREWALK = 1, PH_FORCED = 2, PH_NORMAL = 3 };
-enum Pend { PEND_NONE = 0, PEND_SCATTER = 1, PEND_ABSORB = 2, PEND_INJECT = 3 };
+// Lane states.  0-2: the package moves (one crossing per loop iteration);
+// 3-6: parked until the warp runs its rare events (6: the forced-interaction
+// pre-walk reached the surface); 7: finished, waiting for a new package;
+// 8: no work left.  Everything beyond a crossing runs on the rare path, so
+// the per-crossing path stays short and branch-light.
+enum State {
+  ST_NORMAL = 0, ST_PREWALK = 1, ST_FORCED = 2,
+  ST_SCATTER = 3, ST_ABSORB = 4, ST_INJECT = 5, ST_FFIEND = 6,
+  ST_DEAD = 7, ST_DONE = 8
+};
 
 template <int PREC>
 struct RealOf {
@@ -54,9 +62,10 @@ struct Shared {
   float src_cdf_f[2][kMaxFreq];
   double kabs_d[kMaxFreq], ksca_d[kMaxFreq], g_d[kMaxFreq];
   double src_cdf_d[2][kMaxFreq];
-  double sed[kMaxFreq];                    // FP64 form
-  unsigned long long sed_q[2][kMaxFreq];   // FP32 forms, single model
-  unsigned long long inj_q[2], dir_q[2];
+  // FP32 forms, single model: 64-bit fixed-point tallies kept as 32-bit
+  // halves (lo, hi) so that only 32-bit shared-memory atomics are used
+  unsigned int sed_lo[2][kMaxFreq], sed_hi[2][kMaxFreq];
+  unsigned int inj_lo[2], inj_hi[2], dir_lo[2], dir_hi[2];
   unsigned int rare[CNT_COUNT];            // per-package counters
 };
 
@@ -65,7 +74,7 @@ struct Lane {
   Real p2, s, tauA, tauS, w, acc, tau_int, s0, u_type;
   Real ka, ks;   // absorption / scattering coefficient per unit density at the current frequency
   Real eps;      // package energy (erg/s)
-  int cell, f, phase, pend, src, model, cell_off, n, n64;
+  int cell, f, st, src, model, cell_off, gbase, n, n64;
   uint32_t events, blk, pkg_lo, pkg_hi;
   // parity records
   unsigned long long row, hash;
@@ -83,6 +92,13 @@ __device__ __forceinline__ U4 draw(const TransportParams &P, Lane<typename RealO
                         (uint32_t)(P.seed >> 32));
   ++L.blk;
   return r;
+}
+
+// Fixed-point units of a package weight (w * 2^24), via a 32-bit conversion
+// when it fits.
+__device__ __forceinline__ unsigned long long quanta(float w) {
+  const float x = w * kQuantum;
+  return (x < 4.0e9f) ? (unsigned long long)__float2uint_rn(x) : __float2ull_rn(x);
 }
 
 // ------------------------------------------------------------- sampling
@@ -128,8 +144,7 @@ __device__ __forceinline__ void record(Lane<Real> &L, int ev, int cell, int f) {
 
 template <bool RECORD, class Real>
 __device__ __forceinline__ void finish(const TransportParams &P, Lane<Real> &L) {
-  L.phase = PH_DEAD;
-  L.pend = PEND_NONE;
+  L.st = ST_DEAD;
   if constexpr (RECORD) {
     if (P.rec_events) {
       P.rec_events[3 * L.row + 0] = L.nsca;
@@ -140,17 +155,26 @@ __device__ __forceinline__ void finish(const TransportParams &P, Lane<Real> &L) 
   }
 }
 
+// 64-bit add into a (lo, hi) pair of 32-bit shared-memory words: the carry of
+// each add is detected from the value its own atomic returned.  (64-bit
+// shared-memory atomics, emulated in software, broke warp convergence in
+// divergent code here; 32-bit ones are native.)
+__device__ __forceinline__ void smem_add64(unsigned int *lo, unsigned int *hi, unsigned long long q) {
+  const unsigned int ql = (unsigned int)q, qh = (unsigned int)(q >> 32);
+  const unsigned int old = atomicAdd(lo, ql);
+  const unsigned int up = qh + ((old + ql < old) ? 1u : 0u);
+  if (up) atomicAdd(hi, up);
+}
+
 // add weight w of the current package to an escaping-SED bin
 template <int PREC>
 __device__ __forceinline__ void tally_sed(const TransportParams &P, Shared &S, Lane<typename RealOf<PREC>::T> &L,
                                           typename RealOf<PREC>::T w) {
   if constexpr (PREC == PREC_FP64) {
-    const double e = w * L.eps;
-    if (P.n_models == 1) atomicAdd(&S.sed[L.f], e);
-    else atomicAdd(P.sed + (size_t)L.model * kMaxFreq + L.f, e);
+    atomicAdd(P.sed + (size_t)L.model * kMaxFreq + L.f, w * L.eps);  // native FP64 reduction in L2
   } else {
-    const unsigned long long q = __float2ull_rn(w * kQuantum);
-    if (P.n_models == 1) atomicAdd(&S.sed_q[L.src][L.f], q);
+    const unsigned long long q = quanta(w);
+    if (P.n_models == 1) smem_add64(&S.sed_lo[L.src][L.f], &S.sed_hi[L.src][L.f], q);
     else atomicAdd(P.sed_q + ((size_t)L.model * 2 + L.src) * kMaxFreq + L.f, q);
   }
 }
@@ -198,20 +222,19 @@ __device__ __forceinline__ void boundary(const TransportParams &P, const Lane<ty
     }
     l = fmax(l, 0.0);
   } else {
-    const int gi = L.cell_off + L.model + c + 1;
+    const int gi = L.gbase + c;
     const float4 G = __ldg(P.geo + gi);
     rho = __ldg(P.rhoe + gi);
     const float d_in = (G.x - L.p2) + G.y;
-    const bool inward = (L.s < 0.0f) && (d_in > 0.0f);
+    const bool inward = (L.s < 0.0f) & (d_in > 0.0f);
     const float d = inward ? d_in : (G.z - L.p2) + G.w;
     next = inward ? c - 1 : c + 1;
-    float sq;
-    if (PREC == PREC_MIXED && c >= 0 && c < L.n64) {
+    // sqrt from the hardware reciprocal square root (relative error ~1e-7)
+    float sq = (d > 0.0f) ? d * rsqrtf(d) : 0.0f;
+    if (PREC == PREC_MIXED && (unsigned)c < (unsigned)L.n64) {
       // optional FP64 crossing distance in the innermost shells
-      const double t2 = __ldg(P.r2d + L.cell_off + L.model + c + (inward ? 0 : 1));
+      const double t2 = __ldg(P.r2d + L.gbase - 1 + c + (inward ? 0 : 1));
       sq = (float)sqrt(fmax(t2 - (double)L.p2, 0.0));
-    } else {
-      sq = sqrtf(fmaxf(d, 0.0f));
     }
     sb = inward ? -sq : sq;
     l = fmaxf(sb - L.s, 0.0f);
@@ -241,80 +264,64 @@ __device__ __forceinline__ void set_freq(const Shared &S, Lane<typename RealOf<P
   }
 }
 
+// ----------------------------------- forced first interaction (Sect. 2.2.2)
+// PREWALK accumulates the extinction optical depth tau0 to the surface along
+// the first flight; FORCED replays the flight and stops where the cumulative
+// extinction reaches tau_int (Eq. 10), choosing absorption with probability
+// k_A / k_ext.
+template <int PREC, int MODE, bool RECORD>
+__device__ __forceinline__ void move_forced(const TransportParams &P, Shared &S, Lane<typename RealOf<PREC>::T> &L,
+                                         Tally &T) {
+  using Real = typename RealOf<PREC>::T;
+  Real l, sb, rho;
+  int next;
+  boundary<PREC>(P, L, l, sb, next, rho);
+  const Real ka = L.ka * rho, ks = L.ks * rho;
+  if (L.st == ST_PREWALK) {
+    L.acc += (ka + ks) * l;
+    L.s = sb;
+    L.cell = next;
+    if (next >= L.n) L.st = ST_FFIEND;
+    return;
+  }
+  if constexpr (PREC == PREC_FP64) L.events++;
+  const Real ke = ka + ks;
+  if (ke > Real(0) && L.acc + ke * l >= L.tau_int) {
+    Real li = (L.tau_int - L.acc) / ke;
+    li = li > l ? l : li;
+    li = li < Real(0) ? Real(0) : li;
+    L.s += li;
+    L.st = (L.u_type * ke < ka) ? ST_ABSORB : ST_SCATTER;
+  } else {
+    L.acc += ke * l;
+    cross<PREC, RECORD>(P, S, L, T, sb, next);
+  }
+}
+
 // -------------------------------------------------- the common event: move
 // One step of a moving package: cross into the next cell, or stop at an
-// interaction point and park with a pending scattering / absorption.
+// interaction point and park for a scattering / absorption.
 template <int PREC, int MODE, bool RECORD>
 __device__ __forceinline__ void move(const TransportParams &P, Shared &S, Lane<typename RealOf<PREC>::T> &L,
                                      Tally &T) {
   using Real = typename RealOf<PREC>::T;
+  if (L.st != ST_NORMAL) {
+    move_forced<PREC, MODE, RECORD>(P, S, L, T);
+    return;
+  }
   if constexpr (PREC == PREC_FP64) {
-    if (L.phase == PH_NORMAL && L.events >= P.max_events) {
+    if (L.events >= P.max_events) {
       lose<RECORD>(P, S, L, CNT_KILL_CAP);
       return;
     }
+    L.events++;
   }
   Real l, sb, rho;
   int next;
   boundary<PREC>(P, L, l, sb, next, rho);
   const Real ka = L.ka * rho, ks = L.ks * rho;
-  if (L.phase == PH_PREWALK) {
-    // total extinction optical depth to the surface (Sect. 2.2.2)
-    L.acc += (ka + ks) * l;
-    L.s = sb;
-    L.cell = next;
-    if (next >= L.n) {
-      const Real tau0 = L.acc;
-      Real q;
-      if constexpr (PREC == PREC_FP64) q = -expm1(-tau0);
-      else q = -expm1f(-tau0);
-      // direct escape e^-tau0 of the package is tallied; the rest is forced (Eq. 12)
-      tally_sed<PREC>(P, S, L, L.w * (Real(1) - q));
-      if constexpr (PREC == PREC_FP64) {
-        T.e_direct += (double)L.w * L.eps * (1.0 - (double)q);
-      } else {
-        const unsigned long long dq = __float2ull_rn(L.w * (1.0f - q) * kQuantum);
-        if (P.n_models == 1) atomicAdd(&S.dir_q[L.src], dq);
-        else atomicAdd(P.dir_q + (size_t)L.model * 2 + L.src, dq);
-      }
-      L.w *= q;
-      if (!(q > Real(0))) {
-        atomicAdd(&S.rare[CNT_ESCAPED], 1u);
-        finish<RECORD>(P, L);
-      } else if (L.w < Real(1e-10)) {
-        lose<RECORD>(P, S, L, CNT_KILL_WEIGHT);
-      } else {
-        Real ti;
-        if constexpr (PREC == PREC_FP64) ti = -log1p(-L.tau_int * q);  // Eq. 10
-        else ti = -log1pf(-L.tau_int * q);
-        L.tau_int = (ti > tau0) ? tau0 : ti;
-        atomicAdd(&S.rare[CNT_FORCED], 1u);
-        L.s = L.s0;
-        L.cell = (L.src == 0) ? L.n - 1 : __ldg(&P.desc[L.model].point_cell);
-        L.acc = Real(0);
-        L.phase = PH_FORCED;
-      }
-    }
-    return;
-  }
-  if constexpr (PREC == PREC_FP64) L.events++;
-  if (L.phase == PH_FORCED) {
-    const Real ke = ka + ks;
-    if (ke > Real(0) && L.acc + ke * l >= L.tau_int) {
-      Real li = (L.tau_int - L.acc) / ke;
-      li = li > l ? l : li;
-      li = li < Real(0) ? Real(0) : li;
-      L.s += li;
-      L.phase = PH_NORMAL;
-      L.pend = (L.u_type * ke < ka) ? PEND_ABSORB : PEND_SCATTER;
-    } else {
-      L.acc += ke * l;
-      cross<PREC, RECORD>(P, S, L, T, sb, next);
-    }
-    return;
-  }
-  // normal transport: competing free paths (Eqs. 1 and 4); the boundary wins
-  // ties, and an interaction in a cell without absorption is a scattering
+  // competing free paths (Eqs. 1 and 4); the boundary wins ties, and an
+  // interaction in a cell without absorption is a scattering
   const Real ta = ka * l, ts = ks * l;
   if (L.tauA >= ta && L.tauS >= ts) {
     L.tauA -= ta;
@@ -322,10 +329,10 @@ __device__ __forceinline__ void move(const TransportParams &P, Shared &S, Lane<t
     cross<PREC, RECORD>(P, S, L, T, sb, next);
   } else if (ka <= Real(0) || L.tauS * ka < L.tauA * ks) {
     L.s += L.tauS / ks;
-    L.pend = PEND_SCATTER;
+    L.st = ST_SCATTER;
   } else {
     L.s += L.tauA / ka;
-    L.pend = PEND_ABSORB;
+    L.st = ST_ABSORB;
   }
 }
 
@@ -351,6 +358,7 @@ __device__ __forceinline__ void assign(const TransportParams &P, Lane<typename R
   L.src = (mask == 3) ? (int)sl : ((mask & 1) ? 0 : 1);
   L.model = m;
   L.cell_off = __ldg(&D->cell_off);
+  L.gbase = L.cell_off + m + 1;  // geometry record of cell c: gbase + c (void at gbase - 1)
   L.n = __ldg(&D->n_cells);
   L.n64 = __ldg(&D->n_fp64);
   if constexpr (PREC == PREC_FP64) L.eps = __ldg(&D->L[L.src]) / (double)P.n_per_source;
@@ -359,8 +367,7 @@ __device__ __forceinline__ void assign(const TransportParams &P, Lane<typename R
   L.pkg_hi = (uint32_t)(pkg >> 32);
   L.blk = 0;
   L.events = 0;
-  L.pend = PEND_INJECT;
-  L.phase = PH_NORMAL;
+  L.st = ST_INJECT;
   if constexpr (RECORD) {
     L.row = sl * P.n_per_source + pkg;
     L.hash = 0xcbf29ce484222325ULL;
@@ -443,8 +450,8 @@ __device__ __forceinline__ void inject(const TransportParams &P, Shared &S, Lane
   if constexpr (PREC == PREC_FP64) {
     T.e_inj += (double)L.w * L.eps;
   } else {
-    const unsigned long long q = __float2ull_rn(L.w * kQuantum);
-    if (P.n_models == 1) atomicAdd(&S.inj_q[L.src], q);
+    const unsigned long long q = quanta(L.w);
+    if (P.n_models == 1) smem_add64(&S.inj_lo[L.src], &S.inj_hi[L.src], q);
     else atomicAdd(P.inj_q + (size_t)L.model * 2 + L.src, q);
   }
   record<RECORD>(L, EV_INJECT, L.cell, L.f);
@@ -453,12 +460,12 @@ __device__ __forceinline__ void inject(const TransportParams &P, Shared &S, Lane
     return;
   }
   if (P.ffi) {
-    L.phase = PH_PREWALK;
+    L.st = ST_PREWALK;
     L.acc = Real(0);
     L.tau_int = u_int;  // holds u_int until the pre-walk has found tau0
     L.s0 = L.s;
   } else {
-    L.phase = PH_NORMAL;
+    L.st = ST_NORMAL;
   }
 }
 
@@ -605,22 +612,64 @@ __device__ __forceinline__ void absorb(const TransportParams &P, Shared &S, cons
   record<RECORD>(L, EV_ABSORB, L.cell, L.f);
 }
 
+// End of the forced-interaction pre-walk: tally the direct escape e^-tau0,
+// weight the rest by 1 - e^-tau0 (Eq. 12), draw the forced optical depth
+// (Eq. 10) and restart the first flight from the injection point.
+template <int PREC, bool RECORD>
+__device__ __forceinline__ void ffi_end(const TransportParams &P, Shared &S, Lane<typename RealOf<PREC>::T> &L,
+                                        Tally &T) {
+  using Real = typename RealOf<PREC>::T;
+  const Real tau0 = L.acc;
+  Real q;
+  if constexpr (PREC == PREC_FP64) q = -expm1(-tau0);
+  else q = -expm1f(-tau0);
+  tally_sed<PREC>(P, S, L, L.w * (Real(1) - q));
+  if constexpr (PREC == PREC_FP64) {
+    T.e_direct += (double)L.w * L.eps * (1.0 - (double)q);
+  } else {
+    const unsigned long long dq = quanta(L.w * (1.0f - q));
+    if (P.n_models == 1) smem_add64(&S.dir_lo[L.src], &S.dir_hi[L.src], dq);
+    else atomicAdd(P.dir_q + (size_t)L.model * 2 + L.src, dq);
+  }
+  L.w *= q;
+  if (!(q > Real(0))) {
+    atomicAdd(&S.rare[CNT_ESCAPED], 1u);
+    finish<RECORD>(P, L);
+  } else if (L.w < Real(1e-10)) {
+    lose<RECORD>(P, S, L, CNT_KILL_WEIGHT);
+  } else {
+    Real ti;
+    if constexpr (PREC == PREC_FP64) ti = -log1p(-L.tau_int * q);  // Eq. 10
+    else ti = -log1pf(-L.tau_int * q);
+    L.tau_int = (ti > tau0) ? tau0 : ti;
+    atomicAdd(&S.rare[CNT_FORCED], 1u);
+    L.s = L.s0;
+    L.cell = (L.src == 0) ? L.n - 1 : __ldg(&P.desc[L.model].point_cell);
+    L.acc = Real(0);
+    L.st = ST_FORCED;
+  }
+}
+
 // The rare-event path for one parked lane.
 template <int PREC, int MODE, bool RECORD>
 __device__ __forceinline__ void rare(const TransportParams &P, Shared &S, const float *sLnode,
                                      Lane<typename RealOf<PREC>::T> &L, Tally &T) {
-  const int kind = L.pend;
+  const int kind = L.st;
+  if (kind == ST_FFIEND) {
+    ffi_end<PREC, RECORD>(P, S, L, T);
+    return;
+  }
   if constexpr (PREC != PREC_FP64) {
     // the FP32 forms interrupt a package only here, so the event cap is checked here
-    if (kind != PEND_INJECT && ++L.events >= P.max_events) {
+    if (kind != ST_INJECT && ++L.events >= P.max_events) {
       lose<RECORD>(P, S, L, CNT_KILL_CAP);
       return;
     }
   }
   const U4 a = draw<PREC>(P, L);  // every rare event starts with one Philox block
-  L.pend = PEND_NONE;
-  if (kind == PEND_INJECT) inject<PREC, RECORD>(P, S, L, T, a);
-  else if (kind == PEND_SCATTER) scatter<PREC, RECORD>(P, S, L, T, a);
+  L.st = ST_NORMAL;
+  if (kind == ST_INJECT) inject<PREC, RECORD>(P, S, L, T, a);
+  else if (kind == ST_SCATTER) scatter<PREC, RECORD>(P, S, L, T, a);
   else absorb<PREC, MODE, RECORD>(P, S, sLnode, L, T, a);
 }
 
@@ -654,13 +703,13 @@ __global__ void __launch_bounds__(256) k_transport(const TransportParams P) {
     for (int s = 0; s < 2; ++s) {
       S.src_cdf_d[s][k] = P.src_cdf_d[s * kMaxFreq + k];
       S.src_cdf_f[s][k] = (float)P.src_cdf_d[s * kMaxFreq + k];
-      S.sed_q[s][k] = 0ULL;
+      S.sed_lo[s][k] = 0u;
+      S.sed_hi[s][k] = 0u;
     }
-    S.sed[k] = 0.0;
   }
   if (threadIdx.x < 2) {
-    S.inj_q[threadIdx.x] = 0ULL;
-    S.dir_q[threadIdx.x] = 0ULL;
+    S.inj_lo[threadIdx.x] = S.inj_hi[threadIdx.x] = 0u;
+    S.dir_lo[threadIdx.x] = S.dir_hi[threadIdx.x] = 0u;
   }
   if (threadIdx.x < CNT_COUNT) S.rare[threadIdx.x] = 0u;
   for (int j = threadIdx.x; j < P.n_tnodes_pow2; j += blockDim.x) sLnode[j] = P.Lnode_f[j];
@@ -670,78 +719,89 @@ __global__ void __launch_bounds__(256) k_transport(const TransportParams P) {
   T.cross = T.scat = T.abs = 0;
   T.e_inj = T.e_direct = 0.0;
 
+  bool timed_out = false;
   Lane<Real> L;
-  L.phase = PH_DEAD;
-  L.pend = PEND_NONE;
-  bool exhausted = false;
+  L.st = ST_DEAD;
   const int lane = threadIdx.x & 31;
+  const unsigned lanes_below = (1u << lane) - 1u;
   const unsigned long long t0 = globaltimer();
-  unsigned iter = 0;
+  unsigned idle = 0;  // iterations since this warp last ran its rare path
+  // All warp-wide decisions come from the two ballots at the top of each
+  // iteration; nothing about the warp is carried between iterations.
   for (;;) {
-    if (L.phase != PH_DEAD && L.pend == PEND_NONE) move<PREC, MODE, RECORD>(P, S, L, T);
-    const unsigned waiting = __ballot_sync(kFull, L.pend != PEND_NONE || (L.phase == PH_DEAD && !exhausted));
-    const unsigned moving = __ballot_sync(kFull, L.phase != PH_DEAD && L.pend == PEND_NONE);
-    if ((waiting | moving) == 0u) break;
-    if (moving == 0u || __popc(waiting) >= P.batch_min) {
-      // refill finished lanes from the work counter (one atomic per warp)
-      const unsigned need = __ballot_sync(kFull, L.phase == PH_DEAD && !exhausted);
-      if (need) {
-        const int leader = __ffs(need) - 1;
-        unsigned long long base = 0;
-        if (lane == leader) base = atomicAdd(P.queue, (unsigned long long)__popc(need));
-        base = __shfl_sync(kFull, base, leader);
-        if (need & (1u << lane)) {
-          const unsigned long long g = base + __popc(need & ((1u << lane) - 1u));
-          if (g < P.total) assign<PREC, RECORD>(P, L, g);
-          else exhausted = true;
+    if (L.st <= ST_FORCED) move<PREC, MODE, RECORD>(P, S, L, T);
+    const unsigned waiting = __ballot_sync(kFull, (unsigned)(L.st - ST_SCATTER) <= (unsigned)(ST_DEAD - ST_SCATTER));
+    const unsigned done = __ballot_sync(kFull, L.st == ST_DONE);
+    if (done == kFull) break;
+    if ((waiting | done) != kFull && __popc(waiting) < P.batch_min) {
+      if (++idle < kFlightLimit) continue;
+      // watchdog: record the first stuck lane, end the moving packages as lost
+      if (L.st <= ST_FORCED) {
+        if (atomicCAS(P.diag, 0u, 1u) == 0u) {
+          P.diag[1] = (uint32_t)L.st;
+          P.diag[2] = (uint32_t)L.cell;
+          P.diag[3] = (uint32_t)L.f;
+          P.diag[4] = (uint32_t)L.n;
+          P.diag[5] = __float_as_uint((float)L.s);
+          P.diag[6] = __float_as_uint((float)L.p2);
+          P.diag[7] = __float_as_uint((float)L.tauA);
+          P.diag[8] = __float_as_uint((float)L.tauS);
+          P.diag[9] = __float_as_uint((float)L.ka);
+          P.diag[10] = __float_as_uint((float)L.ks);
+          P.diag[11] = __float_as_uint((float)L.w);
+          P.diag[12] = L.pkg_lo;
+          P.diag[13] = (uint32_t)L.model;
+          __threadfence();
         }
+        lose<RECORD>(P, S, L, CNT_KILL_CAP);
+        atomicOr(P.status, STATUS_STUCK);
       }
-      if (L.pend != PEND_NONE) rare<PREC, MODE, RECORD>(P, S, sLnode, L, T);
     }
-    if ((++iter & 1023u) == 0) {
-      const bool late = (globaltimer() - t0) > P.time_budget_ns;
-      if (__shfl_sync(kFull, late, 0)) {
-        if (lane == 0) atomicOr(P.status, STATUS_TIMEOUT);
-        break;
-      }
+    idle = 0;
+    if (L.st == ST_DEAD) {
+      // refill from the work counter: one atomic for the lanes here together
+      const unsigned m = __activemask();
+      const int leader = __ffs(m) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(P.queue, (unsigned long long)__popc(m));
+      base = __shfl_sync(m, base, leader);
+      const unsigned long long g = base + __popc(m & lanes_below);
+      if (g < P.total) assign<PREC, RECORD>(P, L, g);
+      else L.st = ST_DONE;
+    }
+    if ((unsigned)(L.st - ST_SCATTER) <= (unsigned)(ST_FFIEND - ST_SCATTER)) rare<PREC, MODE, RECORD>(P, S, sLnode, L, T);
+    if (L.st != ST_DONE && (globaltimer() - t0) > P.time_budget_ns) {
+      // time budget reached: this lane gives up its package and its share of the work
+      atomicOr(P.status, STATUS_TIMEOUT);
+      L.st = ST_DONE;
+      timed_out = true;
     }
   }
+  if (!timed_out && L.st != ST_DONE) atomicOr(P.status, STATUS_ABANDONED);
 
-  // frequent counters: warp reduction, one atomic per warp
-  const uint32_t freq_cnt[3] = {T.cross, T.scat, T.abs};
-  const int freq_idx[3] = {CNT_CROSS, CNT_SCATTER, CNT_ABSORB};
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    unsigned long long v = freq_cnt[i];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
-    if (lane == 0 && v) atomicAdd(P.counters + freq_idx[i], v);
-  }
+  // per-lane counters through shared / global atomics (no warp collectives
+  // after the work loop)
+  if (T.cross) atomicAdd(&S.rare[CNT_CROSS], T.cross);
+  if (T.scat) atomicAdd(&S.rare[CNT_SCATTER], T.scat);
+  if (T.abs) atomicAdd(&S.rare[CNT_ABSORB], T.abs);
   if constexpr (PREC == PREC_FP64) {
-    double ev[2] = {T.e_inj, T.e_direct};
-    const int ei[2] = {EN_INJECTED, EN_DIRECT};
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      double v = ev[i];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
-      if (lane == 0 && v != 0.0) atomicAdd(P.energies + ei[i], v);
-    }
+    if (T.e_inj != 0.0) atomicAdd(P.energies + EN_INJECTED, T.e_inj);
+    if (T.e_direct != 0.0) atomicAdd(P.energies + EN_DIRECT, T.e_direct);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < CNT_COUNT; i += blockDim.x)
     if (S.rare[i]) atomicAdd(P.counters + i, (unsigned long long)S.rare[i]);
-  if (P.n_models == 1) {
-    if constexpr (PREC == PREC_FP64) {
-      for (int k = threadIdx.x; k < P.F; k += blockDim.x)
-        if (S.sed[k] != 0.0) atomicAdd(P.sed + k, S.sed[k]);
-    } else {
-      for (int i = threadIdx.x; i < 2 * kMaxFreq; i += blockDim.x)
-        if (S.sed_q[i >> 6][i & 63]) atomicAdd(P.sed_q + i, S.sed_q[i >> 6][i & 63]);
-      if (threadIdx.x < 2) {
-        if (S.inj_q[threadIdx.x]) atomicAdd(P.inj_q + threadIdx.x, S.inj_q[threadIdx.x]);
-        if (S.dir_q[threadIdx.x]) atomicAdd(P.dir_q + threadIdx.x, S.dir_q[threadIdx.x]);
-      }
+  if (PREC != PREC_FP64 && P.n_models == 1) {
+    auto pair = [](unsigned int lo, unsigned int hi) { return ((unsigned long long)hi << 32) | lo; };
+    for (int i = threadIdx.x; i < 2 * kMaxFreq; i += blockDim.x) {
+      const unsigned long long v = pair(S.sed_lo[i >> 6][i & 63], S.sed_hi[i >> 6][i & 63]);
+      if (v) atomicAdd(P.sed_q + i, v);
+    }
+    if (threadIdx.x < 2) {
+      const unsigned long long vi = pair(S.inj_lo[threadIdx.x], S.inj_hi[threadIdx.x]);
+      const unsigned long long vd = pair(S.dir_lo[threadIdx.x], S.dir_hi[threadIdx.x]);
+      if (vi) atomicAdd(P.inj_q + threadIdx.x, vi);
+      if (vd) atomicAdd(P.dir_q + threadIdx.x, vd);
     }
   }
 }

@@ -61,11 +61,13 @@ class dies_stats(ctypes.Structure):
         ("E_injected", ctypes.c_double), ("E_escaped", ctypes.c_double), ("E_lost", ctypes.c_double),
         ("E_direct", ctypes.c_double), ("table_ms", ctypes.c_double), ("kernel_ms", ctypes.c_double),
         ("transport_ms", ctypes.c_double),
-        ("status_word", ctypes.c_uint32), ("launches", ctypes.c_uint32),
+        ("status_word", ctypes.c_uint32), ("launches", ctypes.c_uint32), ("diag", ctypes.c_uint32 * 16),
     ]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["diag"] = list(self.diag)
+        return d
 
 
 _P = ctypes.POINTER

@@ -160,3 +160,20 @@ def test_batch_matches_single_model_runs(D, oracle):
     z, rel = np.concatenate(z), np.concatenate(rel)
     assert len(z) >= 50 and len(rel) >= 10, (len(z), len(rel))
     assert rel.max() <= 0.02 and np.mean(z > 3.0) <= 0.05 and z.max() <= 6.0, (rel.max(), np.mean(z > 3), z.max())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_repeated_runs_finish_every_package(D, prec):
+    """Regression: every package of every run finishes (no lane leaves the
+    work loop early), over repeated forced-first-interaction runs whose
+    rare-event paths are the most divergent; the device flags 16 (package
+    left unfinished) and 8 (flight watchdog) must stay clear."""
+    cloud = W.external_cloud(32, 0.5, ffi=True)
+    for rep in range(24):
+        m = D.Model(cloud, precision=prec)
+        m.run(100_000, seed=5)
+        st = m.stats()
+        assert st["status_word"] == 0, (rep, st["status_word"], st["diag"])
+        assert st["escaped"] == 100_000 and st["killed_cap"] == 0
+        assert st["E_escaped"] + st["E_lost"] == pytest.approx(st["E_injected"], rel=1e-9)
+        m.close()
