@@ -153,8 +153,10 @@ int dies_set_stream(dies_model *m, void *cuda_stream);
  * [64, 256], blocks_per_sm >= 0 (0 = occupancy maximum, larger values are
  * clamped to it), rare_batch in [1, 32]: a warp runs its scatterings,
  * absorptions and package starts together once this many of its lanes wait
- * for one (or when no lane can move on).  Defaults 256, 0, 8. */
-int dies_set_launch(dies_model *m, int block_size, int blocks_per_sm, int rare_batch);
+ * for one (or when no lane can move on); inner_moves in [1, 64]: boundary
+ * crossings a lane may make between two of these warp-wide checks.
+ * Defaults 256, 0, 8, 8.  Results do not depend on these values. */
+int dies_set_launch(dies_model *m, int block_size, int blocks_per_sm, int rare_batch, int inner_moves);
 
 /* Wall-clock budget of one transport launch in seconds (default 120).  A
  * launch that reaches it stops early and the run returns DIES_ETIMEOUT. */
@@ -244,7 +246,7 @@ int dies_batch_set_dust(dies_batch *b, const double *freq_hz, int n_freq, const 
                         const double *kappa_sca, const double *g);
 int dies_batch_set_sources(dies_batch *b, const double *J_ext, double L_point, const double *point_spectrum);
 int dies_batch_set_stream(dies_batch *b, void *cuda_stream);
-int dies_batch_set_launch(dies_batch *b, int block_size, int blocks_per_sm, int rare_batch);
+int dies_batch_set_launch(dies_batch *b, int block_size, int blocks_per_sm, int rare_batch, int inner_moves);
 int dies_run_batch(dies_batch *b, uint64_t n_packages_per_model, uint64_t seed);
 int dies_run_batch_async(dies_batch *b, uint64_t n_packages_per_model, uint64_t seed);
 /* Results: concatenated per-shell arrays (n_total = shell_offsets[n_models])

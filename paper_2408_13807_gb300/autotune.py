@@ -1,7 +1,8 @@
 """Launch-shape autotuner for the IRE transport kernel.
 
 For a cloud model (or a batch of models) it times short runs over a small
-grid of (block size, CTAs per SM, rare_batch) and keeps the fastest.  Results
+grid of (block size, CTAs per SM, rare_batch, inner moves) and keeps the
+fastest.  Results
 are cached per "config class" (precision, weighting, source kind, shell-count
 and optical-depth buckets) in ``tune_cache.json`` next to this file; a class
 missing from the cache is tuned on the spot (on the GPU, through the same C
@@ -19,9 +20,11 @@ from . import dies as D
 
 CACHE_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_cache.json")
 GRID_BLOCK = (128, 256)
-GRID_RARE = (4, 8, 12, 16, 24)
+GRID_RARE = (8, 12, 16, 24)
+GRID_INNER = (4, 8, 16)
 GRID_BPS = (0,)
-DEFAULT = {"block_size": 256, "blocks_per_sm": 0, "rare_batch": 8}
+KEYS = ("block_size", "blocks_per_sm", "rare_batch", "inner_moves")
+DEFAULT = {"block_size": 256, "blocks_per_sm": 0, "rare_batch": 8, "inner_moves": 8}
 
 _lock = threading.Lock()
 _cache: Optional[Dict[str, dict]] = None
@@ -70,18 +73,26 @@ def _time_model(cloud, precision: str, shape: dict, n: int, reps: int = 2) -> fl
         m.close()
 
 
+def _cached(c: Dict[str, dict], key: str) -> Optional[dict]:
+    """Cache entry for ``key`` if it holds every knob (older entries are retuned)."""
+    e = c.get(key)
+    return {k: int(e[k]) for k in KEYS} if e is not None and all(k in e for k in KEYS) else None
+
+
 def tune(cloud, precision: str = "mixed", n: int = 4_000_000, blocks: Iterable[int] = GRID_BLOCK,
-         rare: Iterable[int] = GRID_RARE, bps: Iterable[int] = GRID_BPS) -> Tuple[dict, dict]:
+         rare: Iterable[int] = GRID_RARE, bps: Iterable[int] = GRID_BPS,
+         inner: Iterable[int] = GRID_INNER) -> Tuple[dict, dict]:
     """Time every shape of the grid on ``cloud``; return (best shape, timings)."""
     times = {}
     for b in blocks:
         for k in bps:
             for r in rare:
-                shape = {"block_size": b, "blocks_per_sm": k, "rare_batch": r}
-                times[f"{b}/{k}/{r}"] = _time_model(cloud, precision, shape, n)
+                for i in inner:
+                    shape = {"block_size": b, "blocks_per_sm": k, "rare_batch": r, "inner_moves": i}
+                    times[f"{b}/{k}/{r}/{i}"] = _time_model(cloud, precision, shape, n)
     key = min(times, key=times.get)
-    b, k, r = (int(x) for x in key.split("/"))
-    return {"block_size": b, "blocks_per_sm": k, "rare_batch": r, "ms": times[key], "n": n}, times
+    best = dict(zip(KEYS, (int(x) for x in key.split("/"))))
+    return dict(best, ms=times[key], n=n), times
 
 
 def best_launch(cloud, precision: str = "mixed", allow_tuning: bool = True, n: int = 4_000_000) -> dict:
@@ -89,43 +100,45 @@ def best_launch(cloud, precision: str = "mixed", allow_tuning: bool = True, n: i
     cached on first use when ``allow_tuning`` (needs a GPU)."""
     key = config_class(cloud, precision)
     with _lock:
-        c = _load()
-        if key in c:
-            return {k: c[key][k] for k in ("block_size", "blocks_per_sm", "rare_batch")}
+        hit = _cached(_load(), key)
+    if hit is not None:
+        return hit
     if not allow_tuning:
         return dict(DEFAULT)
     best, _ = tune(cloud, precision, n)
     with _lock:
         _load()[key] = best
         _save()
-    return {k: best[k] for k in ("block_size", "blocks_per_sm", "rare_batch")}
+    return {k: best[k] for k in KEYS}
 
 
 def best_batch_launch(clouds, allow_tuning: bool = True, n_per_model: int = 20_000) -> dict:
     """Best launch shape for a parameter-study batch (timed on the batch itself)."""
     key = f"batch|{len(clouds)}|n_avg{int(sum(c.n_cells for c in clouds) / len(clouds))}"
     with _lock:
-        c = _load()
-        if key in c:
-            return {k: c[key][k] for k in ("block_size", "blocks_per_sm", "rare_batch")}
+        hit = _cached(_load(), key)
+    if hit is not None:
+        return hit
     if not allow_tuning:
         return dict(DEFAULT)
     times = {}
     for b in GRID_BLOCK:
         for r in GRID_RARE:
-            bt = D.Batch(clouds, block_size=b, rare_batch=r)
-            try:
-                bt.run(2_000, seed=3)
-                best = float("inf")
-                for rep in range(2):
-                    bt.run(n_per_model, seed=5 + rep)
-                    best = min(best, bt.stats()["transport_ms"])
-                times[(b, r)] = best
-            finally:
-                bt.close()
-    (b, r) = min(times, key=times.get)
-    rec = {"block_size": b, "blocks_per_sm": 0, "rare_batch": r, "ms": times[(b, r)], "n": n_per_model}
+            for i in GRID_INNER:
+                bt = D.Batch(clouds, block_size=b, rare_batch=r, inner_moves=i)
+                try:
+                    bt.run(2_000, seed=3)
+                    best = float("inf")
+                    for rep in range(2):
+                        bt.run(n_per_model, seed=5 + rep)
+                        best = min(best, bt.stats()["transport_ms"])
+                    times[(b, r, i)] = best
+                finally:
+                    bt.close()
+    (b, r, i) = min(times, key=times.get)
+    rec = {"block_size": b, "blocks_per_sm": 0, "rare_batch": r, "inner_moves": i, "ms": times[(b, r, i)],
+           "n": n_per_model}
     with _lock:
         _load()[key] = rec
         _save()
-    return {k: rec[k] for k in ("block_size", "blocks_per_sm", "rare_batch")}
+    return {k: rec[k] for k in KEYS}

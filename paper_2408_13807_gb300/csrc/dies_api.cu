@@ -111,7 +111,7 @@ struct Problem {
   double T_min = 2.7, T_max = 1500.0;
   int n_tnodes = 1024;
   cudaStream_t stream = nullptr;
-  int block = 256, blocks_per_sm = 0, rare_batch = 8;
+  int block = 256, blocks_per_sm = 0, rare_batch = 8, inner = 8;
   double time_budget_s = 120.0;
   // device
   unsigned char *ws = nullptr;
@@ -340,6 +340,7 @@ struct Problem {
     P.time_budget_ns = (unsigned long long)(time_budget_s * 1e9);
     P.inv_n = (float)(1.0 / (double)n);
     P.batch_min = rare_batch;
+    P.inner = inner;
     return P;
   }
 
@@ -710,19 +711,21 @@ int dies_set_stream(dies_model *m, void *s) {
   return DIES_OK;
 }
 
-static int set_launch(Problem &p, int block, int bps, int rare_batch) {
+static int set_launch(Problem &p, int block, int bps, int rare_batch, int inner) {
   if (block < 64 || block > 256 || block % 32) return fail(DIES_EINVAL, "block_size must be a multiple of 32 in [64, 256]");
   if (bps < 0) return fail(DIES_EINVAL, "blocks_per_sm must be >= 0");
   if (rare_batch < 1 || rare_batch > 32) return fail(DIES_EINVAL, "rare_batch must be in [1, 32]");
+  if (inner < 1 || inner > 64) return fail(DIES_EINVAL, "inner_moves must be in [1, 64]");
   p.block = block;
   p.blocks_per_sm = bps;
   p.rare_batch = rare_batch;
+  p.inner = inner;
   return DIES_OK;
 }
 
-int dies_set_launch(dies_model *m, int block_size, int blocks_per_sm, int rare_batch) {
+int dies_set_launch(dies_model *m, int block_size, int blocks_per_sm, int rare_batch, int inner_moves) {
   if (!m) return fail(DIES_EINVAL, "model is NULL");
-  return set_launch(m->p, block_size, blocks_per_sm, rare_batch);
+  return set_launch(m->p, block_size, blocks_per_sm, rare_batch, inner_moves);
 }
 
 int dies_set_time_budget(dies_model *m, double seconds) {
@@ -949,9 +952,9 @@ int dies_batch_set_stream(dies_batch *b, void *s) {
   return DIES_OK;
 }
 
-int dies_batch_set_launch(dies_batch *b, int block_size, int blocks_per_sm, int rare_batch) {
+int dies_batch_set_launch(dies_batch *b, int block_size, int blocks_per_sm, int rare_batch, int inner_moves) {
   if (!b) return fail(DIES_EINVAL, "batch is NULL");
-  return set_launch(b->p, block_size, blocks_per_sm, rare_batch);
+  return set_launch(b->p, block_size, blocks_per_sm, rare_batch, inner_moves);
 }
 
 int dies_run_batch_async(dies_batch *b, uint64_t n, uint64_t seed) {

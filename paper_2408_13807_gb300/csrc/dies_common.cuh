@@ -123,6 +123,7 @@ struct TransportParams {
   unsigned long long time_budget_ns;
   float inv_n;      // 1 / n_per_source (FP32 package energies)
   int batch_min;    // lanes that must wait for a rare event before a warp runs them together
+  int inner;        // moves per lane between two warp-collective sections (>= 1)
 };
 
 constexpr float kQuantum = 16777216.0f;  // 2^24 fixed-point units per package energy

@@ -729,7 +729,8 @@ __global__ void __launch_bounds__(256) k_transport(const TransportParams P) {
   // All warp-wide decisions come from the two ballots at the top of each
   // iteration; nothing about the warp is carried between iterations.
   for (;;) {
-    if (L.st <= ST_FORCED) move<PREC, MODE, RECORD>(P, S, L, T);
+    // up to P.inner moves per lane between two collective sections
+    for (int k = 0; k < P.inner && L.st <= ST_FORCED; ++k) move<PREC, MODE, RECORD>(P, S, L, T);
     const unsigned waiting = __ballot_sync(kFull, (unsigned)(L.st - ST_SCATTER) <= (unsigned)(ST_DEAD - ST_SCATTER));
     const unsigned done = __ballot_sync(kFull, L.st == ST_DONE);
     if (done == kFull) break;

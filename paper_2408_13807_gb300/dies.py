@@ -93,7 +93,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "dies_set_precision": (i, [_vp, i, i, d]),
         "dies_set_tgrid": (i, [_vp, d, d, i]),
         "dies_set_stream": (i, [_vp, _vp]),
-        "dies_set_launch": (i, [_vp, i, i, i]),
+        "dies_set_launch": (i, [_vp, i, i, i, i]),
         "dies_set_time_budget": (i, [_vp, d]),
         "dies_workspace_bytes": (i, [_vp, _P(ctypes.c_size_t)]),
         "dies_set_workspace": (i, [_vp, _vp, ctypes.c_size_t]),
@@ -110,7 +110,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "dies_batch_set_dust": (i, [_vp, _dp, i, _dp, _dp, _dp]),
         "dies_batch_set_sources": (i, [_vp, _dp, d, _dp]),
         "dies_batch_set_stream": (i, [_vp, _vp]),
-        "dies_batch_set_launch": (i, [_vp, i, i, i]),
+        "dies_batch_set_launch": (i, [_vp, i, i, i, i]),
         "dies_run_batch": (i, [_vp, u64, u64]),
         "dies_run_batch_async": (i, [_vp, u64, u64]),
         "dies_batch_get_temperatures": (i, [_vp, _dp, i]),
@@ -177,8 +177,8 @@ def dies_set_stream(h, stream_handle: int):
     return _check(load().dies_set_stream(h, _vp(stream_handle)))
 
 
-def dies_set_launch(h, block_size: int, blocks_per_sm: int = 0, rare_batch: int = 8):
-    return _check(load().dies_set_launch(h, int(block_size), int(blocks_per_sm), int(rare_batch)))
+def dies_set_launch(h, block_size: int, blocks_per_sm: int = 0, rare_batch: int = 8, inner_moves: int = 8):
+    return _check(load().dies_set_launch(h, int(block_size), int(blocks_per_sm), int(rare_batch), int(inner_moves)))
 
 
 def dies_set_time_budget(h, seconds: float):
@@ -274,8 +274,9 @@ def dies_batch_set_stream(h, stream_handle: int):
     return _check(load().dies_batch_set_stream(h, _vp(stream_handle)))
 
 
-def dies_batch_set_launch(h, block_size: int, blocks_per_sm: int = 0, rare_batch: int = 8):
-    return _check(load().dies_batch_set_launch(h, int(block_size), int(blocks_per_sm), int(rare_batch)))
+def dies_batch_set_launch(h, block_size: int, blocks_per_sm: int = 0, rare_batch: int = 8, inner_moves: int = 8):
+    return _check(load().dies_batch_set_launch(h, int(block_size), int(blocks_per_sm), int(rare_batch),
+                                               int(inner_moves)))
 
 
 def dies_run_batch(h, n_packages_per_model: int, seed: int):
@@ -337,7 +338,7 @@ class Model:
 
     def __init__(self, cloud, precision: str = "mixed", n_batches: int = 1, fp64_radius: float = 0.0,
                  tgrid=(2.7, 1500.0, 1024), torch_memory: bool = True, device: int = 0, block_size: int = 256,
-                 blocks_per_sm: int = 0, rare_batch: int = 8):
+                 blocks_per_sm: int = 0, rare_batch: int = 8, inner_moves: int = 8):
         self.cloud = cloud
         self.h = dies_create_model(cloud.radii, cloud.rho, cloud.length_unit_cm)
         self.n_cells = cloud.n_cells
@@ -348,7 +349,7 @@ class Model:
         dies_set_weighting(self.h, cloud.k_bg, cloud.ffi)
         dies_set_precision(self.h, PREC[precision], n_batches, fp64_radius)
         dies_set_tgrid(self.h, *tgrid)
-        dies_set_launch(self.h, block_size, blocks_per_sm, rare_batch)
+        dies_set_launch(self.h, block_size, blocks_per_sm, rare_batch, inner_moves)
         if torch_memory:
             stream, self._ws = _torch_stream_and_workspace(dies_workspace_bytes(self.h), device)
             dies_set_stream(self.h, stream)
@@ -396,7 +397,8 @@ class Batch:
     """Many cloud models (all with the same dust, field and point-source
     spectrum) in one persistent launch."""
 
-    def __init__(self, clouds, block_size: int = 256, blocks_per_sm: int = 0, rare_batch: int = 8):
+    def __init__(self, clouds, block_size: int = 256, blocks_per_sm: int = 0, rare_batch: int = 8,
+                 inner_moves: int = 8):
         c0 = clouds[0]
         n = np.array([c.n_cells for c in clouds], dtype=np.int32)
         self.offsets = np.concatenate([[0], np.cumsum(n)]).astype(np.int32)
@@ -411,7 +413,7 @@ class Batch:
         J = next((c.J_ext for c in clouds if c.J_ext is not None), None)
         pt = next((c for c in clouds if c.L_point > 0), None)
         dies_batch_set_sources(self.h, J, pt.L_point if pt else 0.0, pt.point_spec if pt else None)
-        dies_batch_set_launch(self.h, block_size, blocks_per_sm, rare_batch)
+        dies_batch_set_launch(self.h, block_size, blocks_per_sm, rare_batch, inner_moves)
 
     def set_stream(self, stream_handle: int):
         dies_batch_set_stream(self.h, stream_handle)
