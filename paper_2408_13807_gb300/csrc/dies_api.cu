@@ -36,7 +36,7 @@ cudaError_t launch_frozen_cdf(cudaStream_t st, int n_cells, int F, const double 
 size_t transport_smem_bytes(int n_tnodes_pow2);
 cudaError_t launch_transport(int prec, int mode, bool record, const TransportParams &P, int grid, int block,
                              cudaStream_t st);
-cudaError_t transport_occupancy(int prec, int mode, int block, int n_tnodes_pow2, int *blocks_per_sm);
+cudaError_t transport_occupancy(int prec, int mode, int block, int n_tnodes_pow2, bool r64, int *blocks_per_sm);
 cudaError_t launch_finalize(cudaStream_t st, int n_cells, const double *E, const float *Eprev, const float *Ecur,
                             int fp32, const double *inv_mass, const double *Lnode, const double *lnT, int n,
                             double *T_out);
@@ -339,6 +339,9 @@ struct Problem {
     P.max_events = 100000000ULL;
     P.time_budget_ns = (unsigned long long)(time_budget_s * 1e9);
     P.inv_n = (float)(1.0 / (double)n);
+    P.k_bg_f = (float)k_bg;
+    P.kbg_plain = (k_bg == 0.5);
+    P.r64 = (prec == PREC_MIXED && fp64_radius > 0.0);
     P.batch_min = rare_batch;
     P.inner = inner;
     return P;
@@ -347,7 +350,8 @@ struct Problem {
   int grid_for(int prec_, int mode, int *grid) {
     int bps = blocks_per_sm;
     int occ = 0;
-    DIES_CUDA(transport_occupancy(prec_, mode, block, next_pow2(n_tnodes), &occ));
+    const bool r64 = (prec_ == PREC_MIXED && mode == MODE_IRE && fp64_radius > 0.0);
+    DIES_CUDA(transport_occupancy(prec_, mode, block, next_pow2(n_tnodes), r64, &occ));
     if (occ < 1) return fail(DIES_ECUDA, "transport kernel cannot be resident with block size %d", block);
     if (bps <= 0 || bps > occ) bps = occ;
     *grid = sm_count * bps;
@@ -882,7 +886,7 @@ int dies_run_frozen_static(dies_model *m, const double *T_frozen_dev, uint64_t n
   DIES_CUDA(launch_frozen_cdf(p.stream, p.n_cells, p.F, p.at<double>(p.lay.freq), p.at<double>(p.lay.kabs),
                               p.at<double>(p.lay.dnu), T_frozen_dev, cdf));
   int occ = 0;
-  DIES_CUDA(transport_occupancy(PREC_FP64, MODE_FROZEN, p.block, next_pow2(p.n_tnodes), &occ));
+  DIES_CUDA(transport_occupancy(PREC_FP64, MODE_FROZEN, p.block, next_pow2(p.n_tnodes), false, &occ));
   if (occ < 1) return fail(DIES_ECUDA, "transport kernel cannot be resident with block size %d", p.block);
   const int bps = (p.blocks_per_sm > 0 && p.blocks_per_sm < occ) ? p.blocks_per_sm : occ;
   const int mode = (flags == DIES_FROZEN_ABSORB_TERMINAL) ? MODE_FROZEN_TERMINAL : MODE_FROZEN;

@@ -122,6 +122,9 @@ struct TransportParams {
   unsigned long long max_events;
   unsigned long long time_budget_ns;
   float inv_n;      // 1 / n_per_source (FP32 package energies)
+  float k_bg_f;     // k_bg as float (FP32 forms)
+  int kbg_plain;    // k_bg == 1/2: no weighting
+  int r64;          // MIXED form: some model has FP64 crossing distances in its inner shells
   int batch_min;    // lanes that must wait for a rare event before a warp runs them together
   int inner;        // moves per lane between two warp-collective sections (>= 1)
 };

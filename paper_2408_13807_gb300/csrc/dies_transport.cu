@@ -58,6 +58,7 @@ struct RealOf<PREC_FP64> {
 // Shared-memory tables and tallies of one CTA.
 struct Shared {
   float kabs_f[kMaxFreq], ksca_f[kMaxFreq];
+  float inv_ka_f[kMaxFreq], inv_ks_f[kMaxFreq];  // 1 / coefficient (inf where it is 0)
   float hg_a[kMaxFreq], hg_b[kMaxFreq], hg_c[kMaxFreq], hg_1pg2[kMaxFreq], hg_inv2g[kMaxFreq];
   float src_cdf_f[2][kMaxFreq];
   double kabs_d[kMaxFreq], ksca_d[kMaxFreq], g_d[kMaxFreq];
@@ -72,6 +73,8 @@ struct Shared {
 template <class Real>
 struct Lane {
   Real p2, s, tauA, tauS, w, acc, tau_int, s0, u_type;
+  Real col;      // FP32 forms: column density (density x length) left to the next interaction
+  int next_ev;   // FP32 forms: that interaction (ST_SCATTER or ST_ABSORB)
   Real ka, ks;   // absorption / scattering coefficient per unit density at the current frequency
   Real eps;      // package energy (erg/s)
   int cell, f, st, src, model, cell_off, gbase, n, n64;
@@ -94,11 +97,32 @@ __device__ __forceinline__ U4 draw(const TransportParams &P, Lane<typename RealO
   return r;
 }
 
-// Fixed-point units of a package weight (w * 2^24), via a 32-bit conversion
-// when it fits.
+// Fixed-point units of a package weight (w * 2^24): a 32-bit conversion when
+// it fits, else the exact integer value of the float from its bits (x >= 2^31
+// is an integer; weights stay far below 2^40).
 __device__ __forceinline__ unsigned long long quanta(float w) {
   const float x = w * kQuantum;
-  return (x < 4.0e9f) ? (unsigned long long)__float2uint_rn(x) : __float2ull_rn(x);
+  if (x < 4.0e9f) return (unsigned long long)__float2uint_rn(x);
+  const uint32_t b = __float_as_uint(x);
+  const uint32_t sh = min((b >> 23) - 150u, 40u);
+  return (unsigned long long)((b & 0x7fffffu) | 0x800000u) << sh;
+}
+
+// Exact float -> double and truncating double -> float for non-negative
+// finite values, on the integer pipes: GB300 runs FP64 instructions, the
+// conversions included, at a small fraction of its FP32 rate.  Zero and
+// values below the float normal range map to zero.
+__device__ __forceinline__ double f2d_nonneg(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t hi = (b >> 23) ? (b >> 3) + (896u << 20) : 0u;  // exponent bias 127 -> 1023
+  return __hiloint2double((int)hi, hi ? (int)(b << 29) : 0);
+}
+__device__ __forceinline__ float d2f_nonneg(double d) {
+  const uint32_t hi = (uint32_t)__double2hiint(d), lo = (uint32_t)__double2loint(d);
+  const uint32_t e = hi >> 20;
+  if (e <= 896u) return 0.0f;
+  if (e >= 1151u) return __int_as_float(0x7f800000);
+  return __uint_as_float(((hi - (896u << 20)) << 3) | (lo >> 29));
 }
 
 // ------------------------------------------------------------- sampling
@@ -197,7 +221,7 @@ __device__ __forceinline__ void lose(const TransportParams &P, Shared &S, Lane<R
 // Distance l to the boundary through which the package leaves its cell, the
 // path coordinate sb of that boundary, the cell entered there, and the
 // density of the current cell.
-template <int PREC>
+template <int PREC, bool R64>
 __device__ __forceinline__ void boundary(const TransportParams &P, const Lane<typename RealOf<PREC>::T> &L,
                                          typename RealOf<PREC>::T &l, typename RealOf<PREC>::T &sb, int &next,
                                          typename RealOf<PREC>::T &rho) {
@@ -231,10 +255,12 @@ __device__ __forceinline__ void boundary(const TransportParams &P, const Lane<ty
     next = inward ? c - 1 : c + 1;
     // sqrt from the hardware reciprocal square root (relative error ~1e-7)
     float sq = (d > 0.0f) ? d * rsqrtf(d) : 0.0f;
-    if (PREC == PREC_MIXED && (unsigned)c < (unsigned)L.n64) {
-      // optional FP64 crossing distance in the innermost shells
-      const double t2 = __ldg(P.r2d + L.gbase - 1 + c + (inward ? 0 : 1));
-      sq = (float)sqrt(fmax(t2 - (double)L.p2, 0.0));
+    if constexpr (R64) {
+      if ((unsigned)c < (unsigned)L.n64) {
+        // optional FP64 crossing distance in the innermost shells
+        const double t2 = __ldg(P.r2d + L.gbase - 1 + c + (inward ? 0 : 1));
+        sq = (float)sqrt(fmax(t2 - (double)L.p2, 0.0));
+      }
     }
     sb = inward ? -sq : sq;
     l = fmaxf(sb - L.s, 0.0f);
@@ -264,18 +290,49 @@ __device__ __forceinline__ void set_freq(const Shared &S, Lane<typename RealOf<P
   }
 }
 
+// FP32 forms: the two free paths tau_S, tau_A (Eqs. 1 and 4) become the
+// column densities tau_S / k_S and tau_A / k_A still to travel.  Both shrink
+// by the same column along a flight, so only the smaller and which path it
+// belongs to are carried: one multiply-compare-subtract per crossing.
+// Interactions without absorption and ties resolve as in the FP64 form.
+__device__ __forceinline__ void set_paths(const Shared &S, Lane<float> &L, float tS, float tA) {
+  const float nA = tA * S.inv_ka_f[L.f], nS = tS * S.inv_ks_f[L.f];
+  L.col = fminf(nA, nS);
+  L.next_ev = (nS < nA) ? ST_SCATTER : ST_ABSORB;
+}
+
 // ----------------------------------- forced first interaction (Sect. 2.2.2)
 // PREWALK accumulates the extinction optical depth tau0 to the surface along
 // the first flight; FORCED replays the flight and stops where the cumulative
 // extinction reaches tau_int (Eq. 10), choosing absorption with probability
-// k_A / k_ext.
-template <int PREC, int MODE, bool RECORD>
+// k_A / k_ext.  The FP32 forms accumulate the column density instead (the
+// frequency is fixed along the flight) and scale by k_ext at the end.
+template <int PREC, int MODE, bool RECORD, bool R64>
 __device__ __forceinline__ void move_forced(const TransportParams &P, Shared &S, Lane<typename RealOf<PREC>::T> &L,
                                          Tally &T) {
   using Real = typename RealOf<PREC>::T;
   Real l, sb, rho;
   int next;
-  boundary<PREC>(P, L, l, sb, next, rho);
+  boundary<PREC, R64>(P, L, l, sb, next, rho);
+  if constexpr (PREC != PREC_FP64) {
+    const float x = rho * l;
+    if (L.st == ST_PREWALK) {
+      L.acc += x;
+      L.s = sb;
+      L.cell = next;
+      if (next >= L.n) L.st = ST_FFIEND;
+      return;
+    }
+    if (x > 0.0f && L.acc + x >= L.tau_int) {
+      const float li = fminf(fmaxf(__fdividef(L.tau_int - L.acc, rho), 0.0f), l);
+      L.s += li;
+      L.st = (L.u_type * (L.ka + L.ks) < L.ka) ? ST_ABSORB : ST_SCATTER;
+    } else {
+      L.acc += x;
+      cross<PREC, RECORD>(P, S, L, T, sb, next);
+    }
+    return;
+  }
   const Real ka = L.ka * rho, ks = L.ks * rho;
   if (L.st == ST_PREWALK) {
     L.acc += (ka + ks) * l;
@@ -301,12 +358,26 @@ __device__ __forceinline__ void move_forced(const TransportParams &P, Shared &S,
 // -------------------------------------------------- the common event: move
 // One step of a moving package: cross into the next cell, or stop at an
 // interaction point and park for a scattering / absorption.
-template <int PREC, int MODE, bool RECORD>
+template <int PREC, int MODE, bool RECORD, bool R64>
 __device__ __forceinline__ void move(const TransportParams &P, Shared &S, Lane<typename RealOf<PREC>::T> &L,
                                      Tally &T) {
   using Real = typename RealOf<PREC>::T;
   if (L.st != ST_NORMAL) {
-    move_forced<PREC, MODE, RECORD>(P, S, L, T);
+    move_forced<PREC, MODE, RECORD, R64>(P, S, L, T);
+    return;
+  }
+  if constexpr (PREC != PREC_FP64) {
+    float l, sb, rho;
+    int next;
+    boundary<PREC, R64>(P, L, l, sb, next, rho);
+    const float x = rho * l;
+    if (L.col >= x) {
+      L.col -= x;
+      cross<PREC, RECORD>(P, S, L, T, sb, next);
+    } else {
+      L.s += fminf(__fdividef(L.col, rho), l);  // x > col >= 0, so rho > 0
+      L.st = L.next_ev;
+    }
     return;
   }
   if constexpr (PREC == PREC_FP64) {
@@ -318,7 +389,7 @@ __device__ __forceinline__ void move(const TransportParams &P, Shared &S, Lane<t
   }
   Real l, sb, rho;
   int next;
-  boundary<PREC>(P, L, l, sb, next, rho);
+  boundary<PREC, false>(P, L, l, sb, next, rho);
   const Real ka = L.ka * rho, ks = L.ks * rho;
   // competing free paths (Eqs. 1 and 4); the boundary wins ties, and an
   // interaction in a cell without absorption is a scattering
@@ -416,17 +487,16 @@ __device__ __forceinline__ void inject(const TransportParams &P, Shared &S, Lane
   } else {
     set_freq<PREC>(S, L, cdf_pick(S.src_cdf_f[L.src], u01f_word(a.x)));
     const float v = u01f_fine(a.y);  // 1 - u of the direction draw
-    L.tauS = -__logf(u01f_word(a.z));
-    L.tauA = -__logf(u01f_word(a.w));
+    set_paths(S, L, -__logf(u01f_word(a.z)), -__logf(u01f_word(a.w)));
     if (L.src == 0) {
       const float Rf = __ldg(&D->Rf);
       float mu, sin2;
-      if (P.k_bg == 0.5) {
+      if (P.kbg_plain) {
         mu = sqrtf(1.0f - v);
         sin2 = v;
       } else {
         // mu = u^k, 1 - mu^2 = -expm1(2k ln u), weight 2k u^(2k-1) (Eq. 5)
-        const float k = (float)P.k_bg;
+        const float k = P.k_bg_f;
         const float lnu = log1pf(-v);
         mu = expf(k * lnu);
         sin2 = -expm1f(2.0f * k * lnu);
@@ -531,8 +601,7 @@ __device__ __forceinline__ void scatter(const TransportParams &P, Shared &S, Lan
       L.s = 0.0f;
       L.p2 = 0.0f;
     }
-    L.tauS = -__logf(u01f_word(a.z));
-    L.tauA = -__logf(u01f_word(a.w));
+    set_paths(S, L, -__logf(u01f_word(a.z)), -__logf(u01f_word(a.w)));
   }
   T.scat++;
   if constexpr (RECORD) L.nsca++;
@@ -590,7 +659,7 @@ __device__ __forceinline__ void absorb(const TransportParams &P, Shared &S, cons
     float eo;
     if constexpr (PREC == PREC_MIXED) {
       // FP64 accumulator; its old value gives e_old, the lookup is FP32
-      eo = (float)atomicAdd(P.E + gc, (double)dEf) * im;
+      eo = d2f_nonneg(atomicAdd(P.E + gc, f2d_nonneg(dEf))) * im;
     } else {
       // FP32 form: two FP32 counters, E = E_prev (frozen in this batch) + E_cur
       eo = (__ldg(P.Eprev + gc) + atomicAdd(P.Ecur + gc, dEf)) * im;
@@ -606,8 +675,7 @@ __device__ __forceinline__ void absorb(const TransportParams &P, Shared &S, cons
     const float r = sqrtf(r2);
     L.s = r * (2.0f * u_mu - 1.0f);
     L.p2 = r2 * (4.0f * u_mu * (1.0f - u_mu));
-    L.tauS = -__logf(u_ts);
-    L.tauA = -__logf(u_ta);
+    set_paths(S, L, -__logf(u_ts), -__logf(u_ta));
   }
   record<RECORD>(L, EV_ABSORB, L.cell, L.f);
 }
@@ -619,7 +687,8 @@ template <int PREC, bool RECORD>
 __device__ __forceinline__ void ffi_end(const TransportParams &P, Shared &S, Lane<typename RealOf<PREC>::T> &L,
                                         Tally &T) {
   using Real = typename RealOf<PREC>::T;
-  const Real tau0 = L.acc;
+  const Real ke = L.ka + L.ks;  // per unit density
+  const Real tau0 = (PREC == PREC_FP64) ? L.acc : L.acc * ke;
   Real q;
   if constexpr (PREC == PREC_FP64) q = -expm1(-tau0);
   else q = -expm1f(-tau0);
@@ -639,9 +708,13 @@ __device__ __forceinline__ void ffi_end(const TransportParams &P, Shared &S, Lan
     lose<RECORD>(P, S, L, CNT_KILL_WEIGHT);
   } else {
     Real ti;
-    if constexpr (PREC == PREC_FP64) ti = -log1p(-L.tau_int * q);  // Eq. 10
-    else ti = -log1pf(-L.tau_int * q);
-    L.tau_int = (ti > tau0) ? tau0 : ti;
+    if constexpr (PREC == PREC_FP64) {
+      ti = -log1p(-L.tau_int * q);  // Eq. 10
+      L.tau_int = (ti > tau0) ? tau0 : ti;
+    } else {
+      ti = -log1pf(-L.tau_int * q);
+      L.tau_int = (ti > tau0) ? L.acc : __fdividef(ti, ke);  // as a column (ke > 0 since q > 0)
+    }
     atomicAdd(&S.rare[CNT_FORCED], 1u);
     L.s = L.s0;
     L.cell = (L.src == 0) ? L.n - 1 : __ldg(&P.desc[L.model].point_cell);
@@ -679,7 +752,7 @@ __device__ __forceinline__ unsigned long long globaltimer() {
   return t;
 }
 
-template <int PREC, int MODE, bool RECORD>
+template <int PREC, int MODE, bool RECORD, bool R64>
 __global__ void __launch_bounds__(256) k_transport(const TransportParams P) {
   using Real = typename RealOf<PREC>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -694,6 +767,8 @@ __global__ void __launch_bounds__(256) k_transport(const TransportParams P) {
     S.g_d[k] = g;
     S.kabs_f[k] = (float)ka;
     S.ksca_f[k] = (float)ks;
+    S.inv_ka_f[k] = (float)(1.0 / ka);  // inf where ka = 0
+    S.inv_ks_f[k] = (float)(1.0 / ks);
     const bool iso = fabs(g) < 1e-6;
     S.hg_a[k] = (float)(1.0 - g * g);
     S.hg_b[k] = (float)(1.0 - g);
@@ -730,7 +805,7 @@ __global__ void __launch_bounds__(256) k_transport(const TransportParams P) {
   // iteration; nothing about the warp is carried between iterations.
   for (;;) {
     // up to P.inner moves per lane between two collective sections
-    for (int k = 0; k < P.inner && L.st <= ST_FORCED; ++k) move<PREC, MODE, RECORD>(P, S, L, T);
+    for (int k = 0; k < P.inner && L.st <= ST_FORCED; ++k) move<PREC, MODE, RECORD, R64>(P, S, L, T);
     const unsigned waiting = __ballot_sync(kFull, (unsigned)(L.st - ST_SCATTER) <= (unsigned)(ST_DEAD - ST_SCATTER));
     const unsigned done = __ballot_sync(kFull, L.st == ST_DONE);
     if (done == kFull) break;
@@ -861,9 +936,9 @@ __global__ void k_merge_batches(int n_cells, float *Eprev, float *Ecur) {
   }
 }
 
-template <int PREC, int MODE, bool RECORD>
+template <int PREC, int MODE, bool RECORD, bool R64 = false>
 cudaError_t launch_one(const TransportParams &P, int grid, int block, size_t smem, cudaStream_t st) {
-  auto kern = k_transport<PREC, MODE, RECORD>;
+  auto kern = k_transport<PREC, MODE, RECORD, R64>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, block, smem, st>>>(P);
@@ -871,9 +946,9 @@ cudaError_t launch_one(const TransportParams &P, int grid, int block, size_t sme
   return cudaGetLastError();
 }
 
-template <int PREC, int MODE, bool RECORD>
+template <int PREC, int MODE, bool RECORD, bool R64 = false>
 cudaError_t occupancy_one(int block, size_t smem, int *blocks_per_sm) {
-  auto kern = k_transport<PREC, MODE, RECORD>;
+  auto kern = k_transport<PREC, MODE, RECORD, R64>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kern, block, smem);
@@ -896,17 +971,21 @@ cudaError_t launch_transport(int prec, int mode, bool record, const TransportPar
                   : launch_one<PREC_FP64, MODE_FROZEN_TERMINAL, false>(P, grid, block, smem, st);
   }
   switch (prec) {
-    case PREC_MIXED: return launch_one<PREC_MIXED, MODE_IRE, false>(P, grid, block, smem, st);
+    case PREC_MIXED:
+      return P.r64 ? launch_one<PREC_MIXED, MODE_IRE, false, true>(P, grid, block, smem, st)
+                   : launch_one<PREC_MIXED, MODE_IRE, false, false>(P, grid, block, smem, st);
     case PREC_FP32: return launch_one<PREC_FP32, MODE_IRE, false>(P, grid, block, smem, st);
     default: return launch_one<PREC_FP64, MODE_IRE, false>(P, grid, block, smem, st);
   }
 }
 
-cudaError_t transport_occupancy(int prec, int mode, int block, int n_tnodes_pow2, int *blocks_per_sm) {
+cudaError_t transport_occupancy(int prec, int mode, int block, int n_tnodes_pow2, bool r64, int *blocks_per_sm) {
   const size_t smem = transport_smem_bytes(n_tnodes_pow2);
   if (mode != MODE_IRE) return occupancy_one<PREC_FP64, MODE_FROZEN, true>(block, smem, blocks_per_sm);
   switch (prec) {
-    case PREC_MIXED: return occupancy_one<PREC_MIXED, MODE_IRE, false>(block, smem, blocks_per_sm);
+    case PREC_MIXED:
+      return r64 ? occupancy_one<PREC_MIXED, MODE_IRE, false, true>(block, smem, blocks_per_sm)
+                 : occupancy_one<PREC_MIXED, MODE_IRE, false, false>(block, smem, blocks_per_sm);
     case PREC_FP32: return occupancy_one<PREC_FP32, MODE_IRE, false>(block, smem, blocks_per_sm);
     default: return occupancy_one<PREC_FP64, MODE_IRE, false>(block, smem, blocks_per_sm);
   }
