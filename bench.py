@@ -456,8 +456,8 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     ap.add_argument("--block", type=int, default=0, help="fixed block size (0 = autotuned launch shapes)")
     ap.add_argument("--blocks-per-sm", type=int, default=0)
-    ap.add_argument("--rare-batch", type=int, default=8)
-    ap.add_argument("--inner-moves", type=int, default=8)
+    ap.add_argument("--rare-batch", type=int, default=16)
+    ap.add_argument("--inner-moves", type=int, default=32)
     ap.add_argument("--fp64-radius", type=float, default=0.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

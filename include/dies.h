@@ -99,8 +99,9 @@ typedef struct {
                              watchdog tripped, 16 = a package left unfinished */
   uint32_t launches;      /* kernels launched by this run */
   uint32_t diag[16];      /* diag[0] = 1: state of the first package ended by the flight
-                             watchdog (state, cell, freq, n, s, p^2, tauA, tauS, kA, kS, w
-                             as float bits, package, model) */
+                             watchdog (state, cell, freq, n, s, p^2, tauA, tauS (FP32
+                             forms: column travelled, column limit), kA, kS, w as
+                             float bits, package, model) */
 } dies_stats;
 
 /* ------------------------------------------------------------ one model */
@@ -154,8 +155,9 @@ int dies_set_stream(dies_model *m, void *cuda_stream);
  * clamped to it), rare_batch in [1, 32]: a warp runs its scatterings,
  * absorptions and package starts together once this many of its lanes wait
  * for one (or when no lane can move on); inner_moves in [1, 64]: boundary
- * crossings a lane may make between two of these warp-wide checks.
- * Defaults 256, 0, 8, 8.  Results do not depend on these values. */
+ * crossings a lane may make between two such rare-event passes (taken in
+ * steps of 4, the warp checking its parked lanes after each step).
+ * Defaults 256, 0, 16, 32.  Results do not depend on these values. */
 int dies_set_launch(dies_model *m, int block_size, int blocks_per_sm, int rare_batch, int inner_moves);
 
 /* Wall-clock budget of one transport launch in seconds (default 120).  A

@@ -20,11 +20,11 @@ from . import dies as D
 
 CACHE_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_cache.json")
 GRID_BLOCK = (128, 256)
-GRID_RARE = (8, 12, 16, 24)
-GRID_INNER = (4, 8, 16)
+GRID_RARE = (12, 16, 20, 24)
+GRID_INNER = (16, 32, 64)
 GRID_BPS = (0,)
 KEYS = ("block_size", "blocks_per_sm", "rare_batch", "inner_moves")
-DEFAULT = {"block_size": 256, "blocks_per_sm": 0, "rare_batch": 8, "inner_moves": 8}
+DEFAULT = {"block_size": 256, "blocks_per_sm": 0, "rare_batch": 16, "inner_moves": 32}
 
 _lock = threading.Lock()
 _cache: Optional[Dict[str, dict]] = None
@@ -79,7 +79,7 @@ def _cached(c: Dict[str, dict], key: str) -> Optional[dict]:
     return {k: int(e[k]) for k in KEYS} if e is not None and all(k in e for k in KEYS) else None
 
 
-def tune(cloud, precision: str = "mixed", n: int = 4_000_000, blocks: Iterable[int] = GRID_BLOCK,
+def tune(cloud, precision: str = "mixed", n: int = 20_000_000, blocks: Iterable[int] = GRID_BLOCK,
          rare: Iterable[int] = GRID_RARE, bps: Iterable[int] = GRID_BPS,
          inner: Iterable[int] = GRID_INNER) -> Tuple[dict, dict]:
     """Time every shape of the grid on ``cloud``; return (best shape, timings)."""
@@ -95,7 +95,7 @@ def tune(cloud, precision: str = "mixed", n: int = 4_000_000, blocks: Iterable[i
     return dict(best, ms=times[key], n=n), times
 
 
-def best_launch(cloud, precision: str = "mixed", allow_tuning: bool = True, n: int = 4_000_000) -> dict:
+def best_launch(cloud, precision: str = "mixed", allow_tuning: bool = True, n: int = 20_000_000) -> dict:
     """Cached best launch shape for the config class of ``cloud``; tuned and
     cached on first use when ``allow_tuning`` (needs a GPU)."""
     key = config_class(cloud, precision)

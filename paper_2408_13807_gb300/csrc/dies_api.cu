@@ -111,7 +111,7 @@ struct Problem {
   double T_min = 2.7, T_max = 1500.0;
   int n_tnodes = 1024;
   cudaStream_t stream = nullptr;
-  int block = 256, blocks_per_sm = 0, rare_batch = 8, inner = 8;
+  int block = 256, blocks_per_sm = 0, rare_batch = 16, inner = 32;
   double time_budget_s = 120.0;
   // device
   unsigned char *ws = nullptr;

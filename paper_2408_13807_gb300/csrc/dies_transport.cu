@@ -3,13 +3,14 @@
 // batch merge.
 //
 // Design (GB300): one persistent grid sized to the SM count; every thread
-// owns one photon package at a time, its state in registers.  Each loop
-// iteration moves every live lane by one boundary crossing (the common
-// event).  A lane whose free path runs out inside its cell, or that needs a
-// new package, parks with a pending rare event; the warp runs the rare-event
-// path for all parked lanes together once enough of them wait (or nothing
-// else can move), so one Philox call, one HG inversion or one table search
-// serves many lanes instead of one.  Finished lanes refill from a device work
+// owns one photon package at a time, its state in registers.  The inner loop
+// moves every live lane by boundary crossings (the common event: tens to
+// thousands per package against a handful of interactions).  A lane whose
+// free path runs out inside its cell, or that needs a new package, parks
+// with a pending rare event; the warp leaves the move loop once enough lanes
+// wait (or after inner_moves steps) and runs the rare-event path for all
+// parked lanes together, so one pass through the Philox, HG-inversion or
+// table-search code serves many lanes instead of one.  Finished lanes refill from a device work
 // counter with one atomic per refill (ballot + popc).  Per-frequency tables
 // and the emission table are staged in shared memory; the per-cell geometry
 // is one 16-byte record read through L1.
@@ -34,17 +35,24 @@ namespace {
 
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kCheck = 4;  // moves between two early-exit ballots of the move loop
 
-// Lane states.  0-2: the package moves (one crossing per loop iteration);
-// 3-6: parked until the warp runs its rare events (6: the forced-interaction
-// pre-walk reached the surface); 7: finished, waiting for a new package;
-// 8: no work left.  Everything beyond a crossing runs on the rare path, so
-// the per-crossing path stays short and branch-light.
+// Lane states.  0-2: the package moves; 3: it left the cloud, its escape
+// is tallied with the warp's rare events; 4-7: parked until the warp runs its
+// rare events (7: the forced-interaction pre-walk reached the surface);
+// 8: finished, waiting for a new package; 9: no work left.  Everything beyond
+// a crossing runs on the rare path, so the per-crossing path stays short and
+// free of divergent branches.
 enum State {
   ST_NORMAL = 0, ST_PREWALK = 1, ST_FORCED = 2,
-  ST_SCATTER = 3, ST_ABSORB = 4, ST_INJECT = 5, ST_FFIEND = 6,
-  ST_DEAD = 7, ST_DONE = 8
+  ST_ESCAPE = 3,
+  ST_SCATTER = 4, ST_ABSORB = 5, ST_INJECT = 6, ST_FFIEND = 7,
+  ST_DEAD = 8, ST_DONE = 9
 };
+
+// Compile-time options of the FP32 / MIXED transport kernels.
+constexpr int OPT_R64 = 1;    // MIXED: FP64 crossing distances in the innermost shells of some model
+constexpr int OPT_NOFFI = 2;  // no forced first interaction: every moving package is in ST_NORMAL
 
 template <int PREC>
 struct RealOf {
@@ -73,8 +81,12 @@ struct Shared {
 template <class Real>
 struct Lane {
   Real p2, s, tauA, tauS, w, acc, tau_int, s0, u_type;
-  Real col;      // FP32 forms: column density (density x length) left to the next interaction
-  int next_ev;   // FP32 forms: that interaction (ST_SCATTER or ST_ABSORB)
+  // FP32 forms: every flight (normal, forced pre-walk, forced) accumulates
+  // the column density acc (density x length) and stops at the column lim
+  Real lim;
+  int next_ev;   // state at lim (ST_SCATTER or ST_ABSORB)
+  int exit_st;   // state on leaving the cloud (ST_ESCAPE, or ST_FFIEND for the pre-walk)
+  int cinc;      // 1 if the flight's crossings count as crossings (0 in the pre-walk)
   Real ka, ks;   // absorption / scattering coefficient per unit density at the current frequency
   Real eps;      // package energy (erg/s)
   int cell, f, st, src, model, cell_off, gbase, n, n64;
@@ -221,7 +233,7 @@ __device__ __forceinline__ void lose(const TransportParams &P, Shared &S, Lane<R
 // Distance l to the boundary through which the package leaves its cell, the
 // path coordinate sb of that boundary, the cell entered there, and the
 // density of the current cell.
-template <int PREC, bool R64>
+template <int PREC, int OPT>
 __device__ __forceinline__ void boundary(const TransportParams &P, const Lane<typename RealOf<PREC>::T> &L,
                                          typename RealOf<PREC>::T &l, typename RealOf<PREC>::T &sb, int &next,
                                          typename RealOf<PREC>::T &rho) {
@@ -255,7 +267,7 @@ __device__ __forceinline__ void boundary(const TransportParams &P, const Lane<ty
     next = inward ? c - 1 : c + 1;
     // sqrt from the hardware reciprocal square root (relative error ~1e-7)
     float sq = (d > 0.0f) ? d * rsqrtf(d) : 0.0f;
-    if constexpr (R64) {
+    if constexpr ((OPT & OPT_R64) != 0) {
       if ((unsigned)c < (unsigned)L.n64) {
         // optional FP64 crossing distance in the innermost shells
         const double t2 = __ldg(P.r2d + L.gbase - 1 + c + (inward ? 0 : 1));
@@ -275,7 +287,7 @@ __device__ __forceinline__ void cross(const TransportParams &P, Shared &S, Lane<
   T.cross++;
   if constexpr (RECORD) L.ncross++;
   record<RECORD>(L, EV_CROSS, next, L.f);
-  if (next >= L.n) escape<PREC, RECORD>(P, S, L);
+  if (next >= L.n) L.st = ST_ESCAPE;
 }
 
 template <int PREC>
@@ -291,13 +303,14 @@ __device__ __forceinline__ void set_freq(const Shared &S, Lane<typename RealOf<P
 }
 
 // FP32 forms: the two free paths tau_S, tau_A (Eqs. 1 and 4) become the
-// column densities tau_S / k_S and tau_A / k_A still to travel.  Both shrink
-// by the same column along a flight, so only the smaller and which path it
-// belongs to are carried: one multiply-compare-subtract per crossing.
-// Interactions without absorption and ties resolve as in the FP64 form.
+// column densities tau_S / k_S and tau_A / k_A.  Both are reached by the
+// same column travelled, so only the smaller and which path it belongs to are
+// carried: one multiply-add-compare per crossing.  Interactions without
+// absorption and ties resolve as in the FP64 form.
 __device__ __forceinline__ void set_paths(const Shared &S, Lane<float> &L, float tS, float tA) {
   const float nA = tA * S.inv_ka_f[L.f], nS = tS * S.inv_ks_f[L.f];
-  L.col = fminf(nA, nS);
+  L.acc = 0.0f;
+  L.lim = fminf(nA, nS);
   L.next_ev = (nS < nA) ? ST_SCATTER : ST_ABSORB;
 }
 
@@ -305,34 +318,14 @@ __device__ __forceinline__ void set_paths(const Shared &S, Lane<float> &L, float
 // PREWALK accumulates the extinction optical depth tau0 to the surface along
 // the first flight; FORCED replays the flight and stops where the cumulative
 // extinction reaches tau_int (Eq. 10), choosing absorption with probability
-// k_A / k_ext.  The FP32 forms accumulate the column density instead (the
-// frequency is fixed along the flight) and scale by k_ext at the end.
-template <int PREC, int MODE, bool RECORD, bool R64>
-__device__ __forceinline__ void move_forced(const TransportParams &P, Shared &S, Lane<typename RealOf<PREC>::T> &L,
-                                         Tally &T) {
-  using Real = typename RealOf<PREC>::T;
+// k_A / k_ext.  (FP64 form; the FP32 forms run both as ordinary flights of
+// the common move, see move.)
+template <int PREC, int MODE, bool RECORD>
+__device__ __forceinline__ void move_forced(const TransportParams &P, Shared &S, Lane<double> &L, Tally &T) {
+  using Real = double;
   Real l, sb, rho;
   int next;
-  boundary<PREC, R64>(P, L, l, sb, next, rho);
-  if constexpr (PREC != PREC_FP64) {
-    const float x = rho * l;
-    if (L.st == ST_PREWALK) {
-      L.acc += x;
-      L.s = sb;
-      L.cell = next;
-      if (next >= L.n) L.st = ST_FFIEND;
-      return;
-    }
-    if (x > 0.0f && L.acc + x >= L.tau_int) {
-      const float li = fminf(fmaxf(__fdividef(L.tau_int - L.acc, rho), 0.0f), l);
-      L.s += li;
-      L.st = (L.u_type * (L.ka + L.ks) < L.ka) ? ST_ABSORB : ST_SCATTER;
-    } else {
-      L.acc += x;
-      cross<PREC, RECORD>(P, S, L, T, sb, next);
-    }
-    return;
-  }
+  boundary<PREC, 0>(P, L, l, sb, next, rho);
   const Real ka = L.ka * rho, ks = L.ks * rho;
   if (L.st == ST_PREWALK) {
     L.acc += (ka + ks) * l;
@@ -358,27 +351,42 @@ __device__ __forceinline__ void move_forced(const TransportParams &P, Shared &S,
 // -------------------------------------------------- the common event: move
 // One step of a moving package: cross into the next cell, or stop at an
 // interaction point and park for a scattering / absorption.
-template <int PREC, int MODE, bool RECORD, bool R64>
+//
+// FP32 forms: the normal flight, the forced-interaction pre-walk and the
+// forced flight are one instruction stream (no divergence between lanes in
+// different kinds of flight): accumulate the column x = rho l; stop inside
+// the cell where acc + x passes lim (x > 0 there, so rho > 0), else cross.
+// The pre-walk has lim = inf and leaves the cloud into ST_FFIEND.
+template <int PREC, int MODE, bool RECORD, int OPT>
 __device__ __forceinline__ void move(const TransportParams &P, Shared &S, Lane<typename RealOf<PREC>::T> &L,
                                      Tally &T) {
   using Real = typename RealOf<PREC>::T;
-  if (L.st != ST_NORMAL) {
-    move_forced<PREC, MODE, RECORD, R64>(P, S, L, T);
-    return;
-  }
   if constexpr (PREC != PREC_FP64) {
     float l, sb, rho;
     int next;
-    boundary<PREC, R64>(P, L, l, sb, next, rho);
-    const float x = rho * l;
-    if (L.col >= x) {
-      L.col -= x;
-      cross<PREC, RECORD>(P, S, L, T, sb, next);
-    } else {
-      L.s += fminf(__fdividef(L.col, rho), l);  // x > col >= 0, so rho > 0
+    boundary<PREC, OPT>(P, L, l, sb, next, rho);
+    const float a2 = fmaf(rho, l, L.acc);
+    if (a2 > L.lim) {
+      L.s += fminf(__fdividef(L.lim - L.acc, rho), l);
       L.st = L.next_ev;
+    } else {
+      L.acc = a2;
+      L.s = sb;
+      L.cell = next;
+      if constexpr ((OPT & OPT_NOFFI) != 0) {
+        T.cross++;
+        if (next >= L.n) L.st = ST_ESCAPE;
+      } else {
+        T.cross += L.cinc;
+        if (next >= L.n) L.st = L.exit_st;
+      }
     }
     return;
+  } else {
+    if (L.st != ST_NORMAL) {
+      move_forced<PREC, MODE, RECORD>(P, S, L, T);
+      return;
+    }
   }
   if constexpr (PREC == PREC_FP64) {
     if (L.events >= P.max_events) {
@@ -529,11 +537,20 @@ __device__ __forceinline__ void inject(const TransportParams &P, Shared &S, Lane
     lose<RECORD>(P, S, L, CNT_KILL_WEIGHT);
     return;
   }
+  if constexpr (PREC != PREC_FP64) {
+    L.exit_st = ST_ESCAPE;
+    L.cinc = 1;
+  }
   if (P.ffi) {
     L.st = ST_PREWALK;
     L.acc = Real(0);
     L.tau_int = u_int;  // holds u_int until the pre-walk has found tau0
     L.s0 = L.s;
+    if constexpr (PREC != PREC_FP64) {
+      L.lim = __int_as_float(0x7f800000);  // the pre-walk runs to the surface
+      L.exit_st = ST_FFIEND;
+      L.cinc = 0;
+    }
   } else {
     L.st = ST_NORMAL;
   }
@@ -712,8 +729,13 @@ __device__ __forceinline__ void ffi_end(const TransportParams &P, Shared &S, Lan
       ti = -log1p(-L.tau_int * q);  // Eq. 10
       L.tau_int = (ti > tau0) ? tau0 : ti;
     } else {
+      // the forced depth as a column (ke > 0 since q > 0); kept strictly
+      // below the pre-walk's column, which the replay reproduces exactly
       ti = -log1pf(-L.tau_int * q);
-      L.tau_int = (ti > tau0) ? L.acc : __fdividef(ti, ke);  // as a column (ke > 0 since q > 0)
+      L.lim = fminf(__fdividef(ti, ke), L.acc * 0.99999905f);
+      L.next_ev = (L.u_type * ke < L.ka) ? ST_ABSORB : ST_SCATTER;
+      L.exit_st = ST_ESCAPE;
+      L.cinc = 1;
     }
     atomicAdd(&S.rare[CNT_FORCED], 1u);
     L.s = L.s0;
@@ -752,7 +774,7 @@ __device__ __forceinline__ unsigned long long globaltimer() {
   return t;
 }
 
-template <int PREC, int MODE, bool RECORD, bool R64>
+template <int PREC, int MODE, bool RECORD, int OPT>
 __global__ void __launch_bounds__(256) k_transport(const TransportParams P) {
   using Real = typename RealOf<PREC>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -801,12 +823,19 @@ __global__ void __launch_bounds__(256) k_transport(const TransportParams P) {
   const unsigned lanes_below = (1u << lane) - 1u;
   const unsigned long long t0 = globaltimer();
   unsigned idle = 0;  // iterations since this warp last ran its rare path
-  // All warp-wide decisions come from the two ballots at the top of each
-  // iteration; nothing about the warp is carried between iterations.
+  unsigned sections = 0;
+  // All warp-wide decisions come from ballots taken by all 32 lanes; nothing
+  // about the warp is carried between iterations.
   for (;;) {
-    // up to P.inner moves per lane between two collective sections
-    for (int k = 0; k < P.inner && L.st <= ST_FORCED; ++k) move<PREC, MODE, RECORD, R64>(P, S, L, T);
-    const unsigned waiting = __ballot_sync(kFull, (unsigned)(L.st - ST_SCATTER) <= (unsigned)(ST_DEAD - ST_SCATTER));
+    // up to P.inner moves per lane (in steps of kCheck); after each step the
+    // warp stops early once batch_min lanes no longer move (warp-uniform loop)
+    for (int k = 0; k < P.inner; k += kCheck) {
+#pragma unroll
+      for (int j = 0; j < kCheck; ++j)
+        if (L.st <= ST_FORCED) move<PREC, MODE, RECORD, OPT>(P, S, L, T);
+      if (__popc(__ballot_sync(kFull, L.st > ST_FORCED)) >= P.batch_min) break;
+    }
+    const unsigned waiting = __ballot_sync(kFull, (unsigned)(L.st - ST_ESCAPE) <= (unsigned)(ST_DEAD - ST_ESCAPE));
     const unsigned done = __ballot_sync(kFull, L.st == ST_DONE);
     if (done == kFull) break;
     if ((waiting | done) != kFull && __popc(waiting) < P.batch_min) {
@@ -820,8 +849,13 @@ __global__ void __launch_bounds__(256) k_transport(const TransportParams P) {
           P.diag[4] = (uint32_t)L.n;
           P.diag[5] = __float_as_uint((float)L.s);
           P.diag[6] = __float_as_uint((float)L.p2);
-          P.diag[7] = __float_as_uint((float)L.tauA);
-          P.diag[8] = __float_as_uint((float)L.tauS);
+          if constexpr (PREC == PREC_FP64) {
+            P.diag[7] = __float_as_uint((float)L.tauA);
+            P.diag[8] = __float_as_uint((float)L.tauS);
+          } else {
+            P.diag[7] = __float_as_uint(L.acc);
+            P.diag[8] = __float_as_uint(L.lim);
+          }
           P.diag[9] = __float_as_uint((float)L.ka);
           P.diag[10] = __float_as_uint((float)L.ks);
           P.diag[11] = __float_as_uint((float)L.w);
@@ -834,6 +868,7 @@ __global__ void __launch_bounds__(256) k_transport(const TransportParams P) {
       }
     }
     idle = 0;
+    if (L.st == ST_ESCAPE) escape<PREC, RECORD>(P, S, L);
     if (L.st == ST_DEAD) {
       // refill from the work counter: one atomic for the lanes here together
       const unsigned m = __activemask();
@@ -846,7 +881,7 @@ __global__ void __launch_bounds__(256) k_transport(const TransportParams P) {
       else L.st = ST_DONE;
     }
     if ((unsigned)(L.st - ST_SCATTER) <= (unsigned)(ST_FFIEND - ST_SCATTER)) rare<PREC, MODE, RECORD>(P, S, sLnode, L, T);
-    if (L.st != ST_DONE && (globaltimer() - t0) > P.time_budget_ns) {
+    if ((++sections & 31u) == 0 && L.st != ST_DONE && (globaltimer() - t0) > P.time_budget_ns) {
       // time budget reached: this lane gives up its package and its share of the work
       atomicOr(P.status, STATUS_TIMEOUT);
       L.st = ST_DONE;
@@ -936,9 +971,9 @@ __global__ void k_merge_batches(int n_cells, float *Eprev, float *Ecur) {
   }
 }
 
-template <int PREC, int MODE, bool RECORD, bool R64 = false>
+template <int PREC, int MODE, bool RECORD, int OPT = 0>
 cudaError_t launch_one(const TransportParams &P, int grid, int block, size_t smem, cudaStream_t st) {
-  auto kern = k_transport<PREC, MODE, RECORD, R64>;
+  auto kern = k_transport<PREC, MODE, RECORD, OPT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, block, smem, st>>>(P);
@@ -946,9 +981,9 @@ cudaError_t launch_one(const TransportParams &P, int grid, int block, size_t sme
   return cudaGetLastError();
 }
 
-template <int PREC, int MODE, bool RECORD, bool R64 = false>
+template <int PREC, int MODE, bool RECORD, int OPT = 0>
 cudaError_t occupancy_one(int block, size_t smem, int *blocks_per_sm) {
-  auto kern = k_transport<PREC, MODE, RECORD, R64>;
+  auto kern = k_transport<PREC, MODE, RECORD, OPT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kern, block, smem);
@@ -972,9 +1007,14 @@ cudaError_t launch_transport(int prec, int mode, bool record, const TransportPar
   }
   switch (prec) {
     case PREC_MIXED:
-      return P.r64 ? launch_one<PREC_MIXED, MODE_IRE, false, true>(P, grid, block, smem, st)
-                   : launch_one<PREC_MIXED, MODE_IRE, false, false>(P, grid, block, smem, st);
-    case PREC_FP32: return launch_one<PREC_FP32, MODE_IRE, false>(P, grid, block, smem, st);
+      if (P.ffi)
+        return P.r64 ? launch_one<PREC_MIXED, MODE_IRE, false, OPT_R64>(P, grid, block, smem, st)
+                     : launch_one<PREC_MIXED, MODE_IRE, false, 0>(P, grid, block, smem, st);
+      return P.r64 ? launch_one<PREC_MIXED, MODE_IRE, false, OPT_R64 | OPT_NOFFI>(P, grid, block, smem, st)
+                   : launch_one<PREC_MIXED, MODE_IRE, false, OPT_NOFFI>(P, grid, block, smem, st);
+    case PREC_FP32:
+      return P.ffi ? launch_one<PREC_FP32, MODE_IRE, false, 0>(P, grid, block, smem, st)
+                   : launch_one<PREC_FP32, MODE_IRE, false, OPT_NOFFI>(P, grid, block, smem, st);
     default: return launch_one<PREC_FP64, MODE_IRE, false>(P, grid, block, smem, st);
   }
 }
@@ -984,8 +1024,9 @@ cudaError_t transport_occupancy(int prec, int mode, int block, int n_tnodes_pow2
   if (mode != MODE_IRE) return occupancy_one<PREC_FP64, MODE_FROZEN, true>(block, smem, blocks_per_sm);
   switch (prec) {
     case PREC_MIXED:
-      return r64 ? occupancy_one<PREC_MIXED, MODE_IRE, false, true>(block, smem, blocks_per_sm)
-                 : occupancy_one<PREC_MIXED, MODE_IRE, false, false>(block, smem, blocks_per_sm);
+      // the variants differ by a few registers at most; the FFI ones are the larger
+      return r64 ? occupancy_one<PREC_MIXED, MODE_IRE, false, OPT_R64>(block, smem, blocks_per_sm)
+                 : occupancy_one<PREC_MIXED, MODE_IRE, false, 0>(block, smem, blocks_per_sm);
     case PREC_FP32: return occupancy_one<PREC_FP32, MODE_IRE, false>(block, smem, blocks_per_sm);
     default: return occupancy_one<PREC_FP64, MODE_IRE, false>(block, smem, blocks_per_sm);
   }

@@ -177,7 +177,7 @@ def dies_set_stream(h, stream_handle: int):
     return _check(load().dies_set_stream(h, _vp(stream_handle)))
 
 
-def dies_set_launch(h, block_size: int, blocks_per_sm: int = 0, rare_batch: int = 8, inner_moves: int = 8):
+def dies_set_launch(h, block_size: int, blocks_per_sm: int = 0, rare_batch: int = 16, inner_moves: int = 32):
     return _check(load().dies_set_launch(h, int(block_size), int(blocks_per_sm), int(rare_batch), int(inner_moves)))
 
 
@@ -274,7 +274,7 @@ def dies_batch_set_stream(h, stream_handle: int):
     return _check(load().dies_batch_set_stream(h, _vp(stream_handle)))
 
 
-def dies_batch_set_launch(h, block_size: int, blocks_per_sm: int = 0, rare_batch: int = 8, inner_moves: int = 8):
+def dies_batch_set_launch(h, block_size: int, blocks_per_sm: int = 0, rare_batch: int = 16, inner_moves: int = 32):
     return _check(load().dies_batch_set_launch(h, int(block_size), int(blocks_per_sm), int(rare_batch),
                                                int(inner_moves)))
 
@@ -338,7 +338,7 @@ class Model:
 
     def __init__(self, cloud, precision: str = "mixed", n_batches: int = 1, fp64_radius: float = 0.0,
                  tgrid=(2.7, 1500.0, 1024), torch_memory: bool = True, device: int = 0, block_size: int = 256,
-                 blocks_per_sm: int = 0, rare_batch: int = 8, inner_moves: int = 8):
+                 blocks_per_sm: int = 0, rare_batch: int = 16, inner_moves: int = 32):
         self.cloud = cloud
         self.h = dies_create_model(cloud.radii, cloud.rho, cloud.length_unit_cm)
         self.n_cells = cloud.n_cells
@@ -397,8 +397,8 @@ class Batch:
     """Many cloud models (all with the same dust, field and point-source
     spectrum) in one persistent launch."""
 
-    def __init__(self, clouds, block_size: int = 256, blocks_per_sm: int = 0, rare_batch: int = 8,
-                 inner_moves: int = 8):
+    def __init__(self, clouds, block_size: int = 256, blocks_per_sm: int = 0, rare_batch: int = 16,
+                 inner_moves: int = 32):
         c0 = clouds[0]
         n = np.array([c.n_cells for c in clouds], dtype=np.int32)
         self.offsets = np.concatenate([[0], np.cumsum(n)]).astype(np.int32)
