@@ -23,10 +23,11 @@ static std::atomic<unsigned long long> g_launches{0};
 void launch_counter_add(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 cudaError_t launch_freq_tables(cudaStream_t st, int F, const double *nu, const double *J, const double *spec,
-                               double *dnu, double *src_cdf_d, float *src_cdf_f, double *src_sum);
+                               double *dnu, double *src_cdf_d, uint32_t *src_alias, double *src_sum);
 cudaError_t launch_node_tables(cudaStream_t st, int F, int n, int n_pow2, double T_min, double T_max,
                                const double *nu, const double *kabs, const double *dnu, double *Lnode_d,
-                               float *Lnode_f, double *lnT, float *dcdf_f, double *dcdf_d);
+                               float *Lnode_f, double *lnT, uint32_t *dalias, double *dcdf_d, uint16_t *nguide,
+                               int *nmeta);
 cudaError_t launch_geometry(cudaStream_t st, int n_models, ModelDesc *desc, int n_cells_total, int n_bnd,
                             const double *radii, const double *rho, double length_unit_cm, const double *src_sum,
                             double L_point, double *r2d, float *r2f, double *rhod, float *rhof, double *inv_mass,
@@ -83,8 +84,8 @@ bool finite_nonneg(const double *a, int n) {
 struct Layout {
   size_t desc, radii, rho_in, r2d, r2f, rhod, rhof, inv_mass, inv_massf, geo, rhoe, E, Eprev, Ecur, T, sed;
   size_t sed_q, inj_q, dir_q;
-  size_t freq, kabs, ksca, g, J, spec, dnu, src_cdf_d, src_cdf_f, src_sum;
-  size_t Lnode_d, Lnode_f, lnT, dcdf_f, dcdf_d;
+  size_t freq, kabs, ksca, g, J, spec, dnu, src_cdf_d, src_alias, src_sum;
+  size_t Lnode_d, Lnode_f, lnT, dalias, dcdf_d, nguide, nmeta;
   size_t counters, energies, queue, status, diag;
   size_t total;
 };
@@ -174,13 +175,15 @@ struct Problem {
     L.spec = seg(kMaxFreq * 8);
     L.dnu = seg(kMaxFreq * 8);
     L.src_cdf_d = seg(2 * kMaxFreq * 8);
-    L.src_cdf_f = seg(2 * kMaxFreq * 4);
+    L.src_alias = seg(2 * kMaxFreq * 4);
     L.src_sum = seg(2 * 8);
     L.Lnode_d = seg(np2 * 8);
     L.Lnode_f = seg(np2 * 4);
     L.lnT = seg(np2 * 8);
-    L.dcdf_f = seg(nt * kMaxFreq * 4);
+    L.dalias = seg(nt * kMaxFreq * 4);
     L.dcdf_d = seg(nt * kMaxFreq * 8);
+    L.nguide = seg(kGuide * 2);
+    L.nmeta = seg(2 * 4);
     L.counters = seg(16 * 8);
     L.energies = seg(8 * 8);
     L.queue = seg(2 * 8);
@@ -279,11 +282,11 @@ struct Problem {
       if ((rc = upload(offs[i], pad.data() + i * kMaxFreq, kMaxFreq * 8))) return rc;
     DIES_CUDA(launch_freq_tables(stream, F, at<double>(lay.freq), has_ext ? at<double>(lay.J) : nullptr,
                                  (L_point > 0.0) ? at<double>(lay.spec) : nullptr, at<double>(lay.dnu),
-                                 at<double>(lay.src_cdf_d), at<float>(lay.src_cdf_f), at<double>(lay.src_sum)));
+                                 at<double>(lay.src_cdf_d), at<uint32_t>(lay.src_alias), at<double>(lay.src_sum)));
     DIES_CUDA(launch_node_tables(stream, F, n_tnodes, next_pow2(n_tnodes), T_min, T_max, at<double>(lay.freq),
                                  at<double>(lay.kabs), at<double>(lay.dnu), at<double>(lay.Lnode_d),
-                                 at<float>(lay.Lnode_f), at<double>(lay.lnT), at<float>(lay.dcdf_f),
-                                 at<double>(lay.dcdf_d)));
+                                 at<float>(lay.Lnode_f), at<double>(lay.lnT), at<uint32_t>(lay.dalias),
+                                 at<double>(lay.dcdf_d), at<uint16_t>(lay.nguide), at<int>(lay.nmeta)));
     DIES_CUDA(launch_geometry(stream, n_models, at<ModelDesc>(lay.desc), n_cells, n_cells + n_models,
                               at<double>(lay.radii), at<double>(lay.rho_in), length_unit_cm, at<double>(lay.src_sum),
                               L_point, at<double>(lay.r2d), at<float>(lay.r2f), at<double>(lay.rhod),
@@ -319,7 +322,10 @@ struct Problem {
     P.src_cdf_d = at<double>(lay.src_cdf_d);
     P.Lnode_d = at<double>(lay.Lnode_d);
     P.Lnode_f = at<float>(lay.Lnode_f);
-    P.dcdf_f = at<float>(lay.dcdf_f);
+    P.dalias = at<uint32_t>(lay.dalias);
+    P.src_alias = at<uint32_t>(lay.src_alias);
+    P.nguide = at<uint16_t>(lay.nguide);
+    P.nmeta = at<int>(lay.nmeta);
     P.dcdf_d = at<double>(lay.dcdf_d);
     P.n_tnodes = n_tnodes;
     P.n_tnodes_pow2 = next_pow2(n_tnodes);

@@ -96,7 +96,10 @@ struct TransportParams {
   // temperature tables
   const double *Lnode_d;    // [n_tnodes]
   const float *Lnode_f;
-  const float *dcdf_f;      // [n_tnodes][kMaxFreq]
+  const uint32_t *dalias;   // FP32 forms: [n_tnodes][kMaxFreq] alias tables of the re-emission rows
+  const uint32_t *src_alias;  // FP32 forms: [2][kMaxFreq] alias tables of the source spectra
+  const uint16_t *nguide;   // FP32 forms: [kGuide] first node of each bucket of float(Lambda) bits
+  const int *nmeta;         // {bits of Lambda_0, bucket shift}
   const double *dcdf_d;
   int n_tnodes;
   int n_tnodes_pow2;        // smallest power of two >= n_tnodes
@@ -127,7 +130,13 @@ struct TransportParams {
   int r64;          // MIXED form: some model has FP64 crossing distances in its inner shells
   int batch_min;    // lanes that must wait for a rare event before a warp runs them together
   int inner;        // moves per lane between two warp-collective sections (>= 1)
+  unsigned chunk;   // work items a warp takes from the counter at a time (multiple of 32, >= 32)
 };
+
+// Alias-table entries (FP32 forms): bits 6..31 the 26-bit acceptance
+// threshold of the slot, bits 0..5 the alias bin; a slot that is full has
+// itself as alias.
+constexpr int kGuide = 1024;  // buckets of the node guide table
 
 constexpr float kQuantum = 16777216.0f;  // 2^24 fixed-point units per package energy
 

@@ -23,6 +23,44 @@ __device__ __forceinline__ double planck(double nu, double T) {
   return 2.0 * kH * nu * nu * nu / (kC * kC) / expm1(x);
 }
 
+// Alias table over kMaxFreq slots (Walker's method, built with Vose's
+// linear-time pairing of under- and over-full slots) for the distribution
+// proportional to w[0..kMaxFreq) (uniform over the first F bins if all w are
+// 0).  Entry: 26-bit acceptance threshold << 6 | alias bin.  One thread.
+__device__ void build_alias(const double *w, int F, uint32_t *out) {
+  double q[kMaxFreq], sum = 0.0;
+  int small[kMaxFreq], large[kMaxFreq], ns = 0, nl = 0;
+  uint32_t alias[kMaxFreq];
+  for (int k = 0; k < kMaxFreq; ++k) sum += w[k];
+  for (int k = 0; k < kMaxFreq; ++k) {
+    const double p = (sum > 0.0) ? w[k] / sum : (k < F ? 1.0 / F : 0.0);
+    q[k] = p * kMaxFreq;
+    alias[k] = (uint32_t)k;
+    if (q[k] < 1.0) small[ns++] = k; else large[nl++] = k;
+  }
+  // pair an under-full slot with an over-full bin that tops it up
+  while (ns > 0 && nl > 0) {
+    const int s = small[--ns], l = large[--nl];
+    alias[s] = (uint32_t)l;
+    q[l] = (q[l] + q[s]) - 1.0;
+    if (q[l] < 1.0) small[ns++] = l; else large[nl++] = l;
+  }
+  // what is left is full up to rounding
+  while (nl > 0) q[large[--nl]] = 1.0;
+  while (ns > 0) q[small[--ns]] = 1.0;
+  for (int k = 0; k < kMaxFreq; ++k) {
+    uint32_t t;
+    if (q[k] >= 1.0) {
+      t = (1u << 26) - 1u;
+      alias[k] = (uint32_t)k;
+    } else {
+      const double x = q[k] * 67108864.0;  // 2^26
+      t = (x >= 67108863.0) ? (1u << 26) - 1u : (uint32_t)(x + 0.5);
+    }
+    out[k] = (t << 6) | alias[k];
+  }
+}
+
 // inclusive scan over the 64 threads of a block (two warps); `sh` holds 2 doubles
 __device__ double block64_inclusive_scan(double v, double *sh) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -50,9 +88,10 @@ __device__ double bin_width(const double *nu, int F, int k) {
 
 // One block of 64 threads: bin widths, source CDFs and the source spectral sums.
 __global__ void k_freq_tables(int F, const double *nu, const double *J, const double *spec, double *dnu,
-                              double *src_cdf_d, float *src_cdf_f, double *src_sum) {
+                              double *src_cdf_d, uint32_t *src_alias, double *src_sum) {
   __shared__ double sh[2];
   __shared__ double total;
+  __shared__ double wsh[kMaxFreq];
   const int k = threadIdx.x;
   const double w = (k < F) ? bin_width(nu, F, k) : 0.0;
   dnu[k] = w;
@@ -67,8 +106,11 @@ __global__ void k_freq_tables(int F, const double *nu, const double *J, const do
     double v = (T > 0.0) ? c / T : (double)(k + 1) / F;
     if (k >= F - 1) v = 1.0;
     src_cdf_d[s * kMaxFreq + k] = v;
-    src_cdf_f[s * kMaxFreq + k] = (float)v;
     if (k == 0) src_sum[s] = T;
+    wsh[k] = p;
+    __syncthreads();
+    if (k == 0) build_alias(wsh, F, src_alias + s * kMaxFreq);
+    __syncthreads();
   }
 }
 
@@ -79,10 +121,11 @@ __global__ void k_freq_tables(int F, const double *nu, const double *J, const do
 //   with the node-0 spectrum itself.
 // Blocks j >= n pad the search tables with +inf up to a power of two.
 __global__ void k_node_tables(int F, int n, double T_min, double T_max, const double *nu, const double *kabs,
-                              const double *dnu, double *Lnode_d, float *Lnode_f, double *lnT, float *dcdf_f,
+                              const double *dnu, double *Lnode_d, float *Lnode_f, double *lnT, uint32_t *dalias,
                               double *dcdf_d) {
   __shared__ double sh[2];
   __shared__ double total;
+  __shared__ double wsh[kMaxFreq];
   const int j = blockIdx.x, k = threadIdx.x;
   if (j >= n) {
     if (k == 0) {
@@ -115,7 +158,30 @@ __global__ void k_node_tables(int F, int n, double T_min, double T_max, const do
   double v = (tot > 0.0) ? c / tot : (double)(k + 1) / F;
   if (k >= F - 1) v = 1.0;
   dcdf_d[(size_t)j * kMaxFreq + k] = v;
-  dcdf_f[(size_t)j * kMaxFreq + k] = (float)v;
+  wsh[k] = (k < F) ? d : 0.0;
+  __syncthreads();
+  if (k == 0) build_alias(wsh, F, dalias + (size_t)j * kMaxFreq);
+}
+
+// Guide table of the node search (FP32 forms): for a positive float e, the
+// bucket b = (bits(e) - bits(Lambda_0)) >> shift (clamped to [0, kGuide)) is
+// monotone in e; guide[b] = number of nodes with Lambda_j below the smallest
+// e of bucket b, so the count of nodes <= e is reached from guide[b] by a
+// short forward scan.  One block of kGuide threads.
+__global__ void k_node_guide(int n, const float *Lnode_f, uint16_t *guide, int *meta) {
+  const int b = threadIdx.x;
+  const int b0 = __float_as_int(Lnode_f[0]);
+  const int span = __float_as_int(Lnode_f[n - 1]) - b0;
+  int sh = 0;
+  while ((span >> sh) >= kGuide) ++sh;
+  const float lo = __int_as_float(b0 + (b << sh));
+  int c = 0;
+  for (int j = 0; j < n; ++j) c += (Lnode_f[j] < lo) ? 1 : 0;
+  guide[b] = (uint16_t)c;
+  if (b == 0) {
+    meta[0] = b0;
+    meta[1] = sh;
+  }
 }
 
 // Per-boundary R^2.
@@ -204,18 +270,20 @@ __global__ void k_frozen_cdf(int F, const double *nu, const double *kabs, const 
 }  // namespace
 
 cudaError_t launch_freq_tables(cudaStream_t st, int F, const double *nu, const double *J, const double *spec,
-                               double *dnu, double *src_cdf_d, float *src_cdf_f, double *src_sum) {
-  k_freq_tables<<<1, kMaxFreq, 0, st>>>(F, nu, J, spec, dnu, src_cdf_d, src_cdf_f, src_sum);
+                               double *dnu, double *src_cdf_d, uint32_t *src_alias, double *src_sum) {
+  k_freq_tables<<<1, kMaxFreq, 0, st>>>(F, nu, J, spec, dnu, src_cdf_d, src_alias, src_sum);
   launch_counter_add(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_node_tables(cudaStream_t st, int F, int n, int n_pow2, double T_min, double T_max,
                                const double *nu, const double *kabs, const double *dnu, double *Lnode_d,
-                               float *Lnode_f, double *lnT, float *dcdf_f, double *dcdf_d) {
-  k_node_tables<<<n_pow2, kMaxFreq, 0, st>>>(F, n, T_min, T_max, nu, kabs, dnu, Lnode_d, Lnode_f, lnT, dcdf_f,
+                               float *Lnode_f, double *lnT, uint32_t *dalias, double *dcdf_d, uint16_t *nguide,
+                               int *nmeta) {
+  k_node_tables<<<n_pow2, kMaxFreq, 0, st>>>(F, n, T_min, T_max, nu, kabs, dnu, Lnode_d, Lnode_f, lnT, dalias,
                                              dcdf_d);
-  launch_counter_add(1);
+  k_node_guide<<<1, kGuide, 0, st>>>(n, Lnode_f, nguide, nmeta);
+  launch_counter_add(2);
   return cudaGetLastError();
 }
 

@@ -10,8 +10,10 @@
 // with a pending rare event; the warp leaves the move loop once enough lanes
 // wait (or after inner_moves steps) and runs the rare-event path for all
 // parked lanes together, so one pass through the Philox, HG-inversion or
-// table-search code serves many lanes instead of one.  Finished lanes refill from a device work
-// counter with one atomic per refill (ballot + popc).  Per-frequency tables
+// table-search code serves many lanes instead of one.  Finished lanes refill
+// from their warp's chunk of work items; lane 0 takes a new chunk from the
+// device work counter when it runs out (one atomic per chunk of 32-1024
+// packages instead of one per refill).  Per-frequency tables
 // and the emission table are staged in shared memory; the per-cell geometry
 // is one 16-byte record read through L1.
 //
@@ -36,6 +38,7 @@ namespace {
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kCheck = 4;  // moves between two early-exit ballots of the move loop
+constexpr int kMaxWarps = 8;  // warps per CTA (block size <= 256)
 
 // Lane states.  0-2: the package moves; 3: it left the cloud, its escape
 // is tallied with the warp's rare events; 4-7: parked until the warp runs its
@@ -68,7 +71,9 @@ struct Shared {
   float kabs_f[kMaxFreq], ksca_f[kMaxFreq];
   float inv_ka_f[kMaxFreq], inv_ks_f[kMaxFreq];  // 1 / coefficient (inf where it is 0)
   float hg_a[kMaxFreq], hg_b[kMaxFreq], hg_c[kMaxFreq], hg_1pg2[kMaxFreq], hg_inv2g[kMaxFreq];
-  float src_cdf_f[2][kMaxFreq];
+  uint32_t src_alias[2][kMaxFreq];   // FP32 forms: source spectra as alias tables
+  uint16_t nguide[kGuide];           // FP32 forms: node-search guide
+  int g_b0, g_sh;
   double kabs_d[kMaxFreq], ksca_d[kMaxFreq], g_d[kMaxFreq];
   double src_cdf_d[2][kMaxFreq];
   // FP32 forms, single model: 64-bit fixed-point tallies kept as 32-bit
@@ -76,6 +81,9 @@ struct Shared {
   unsigned int sed_lo[2][kMaxFreq], sed_hi[2][kMaxFreq];
   unsigned int inj_lo[2], inj_hi[2], dir_lo[2], dir_hi[2];
   unsigned int rare[CNT_COUNT];            // per-package counters
+  // per-warp work cursor [next, end) within the warp's current chunk;
+  // read and written by lane 0 of that warp only
+  unsigned long long wq_next[kMaxWarps], wq_end[kMaxWarps];
 };
 
 template <class Real>
@@ -154,6 +162,27 @@ __device__ __forceinline__ int cdf_pick_ldg(const T *row, T u) {
   for (int step = 32; step > 0; step >>= 1)
     if (__ldg(row + k + step - 1) < u) k += step;
   return k;
+}
+
+// FP32 forms: bin drawn from an alias table row by the 23-bit uniform m
+// (top 6 bits: the slot; the other 17: the acceptance test).
+__device__ __forceinline__ int alias_pick(const uint32_t *row, uint32_t m23) {
+  const uint32_t e = row[m23 >> 17];
+  return ((m23 & 0x1ffffu) << 9) < (e >> 6) ? (int)(m23 >> 17) : (int)(e & 63u);
+}
+__device__ __forceinline__ int alias_pick_ldg(const uint32_t *row, uint32_t m23) {
+  const uint32_t e = __ldg(row + (m23 >> 17));
+  return ((m23 & 0x1ffffu) << 9) < (e >> 6) ? (int)(m23 >> 17) : (int)(e & 63u);
+}
+
+// FP32 forms: number of nodes with Lambda_j <= e (e >= 0) from the guide
+// bucket of e and a short forward scan.
+__device__ __forceinline__ int node_count_guided(const Shared &S, const float *L, int n, float e) {
+  const int d = __float_as_int(e) - S.g_b0;
+  const int b = d < 0 ? 0 : min(d >> S.g_sh, kGuide - 1);
+  int j = S.nguide[b];
+  while (j < n && L[j] <= e) ++j;
+  return j;
 }
 
 // number of table nodes with Lambda_j <= e (table padded with +inf to pow2)
@@ -420,7 +449,8 @@ __device__ __forceinline__ void move(const TransportParams &P, Shared &S, Lane<t
 template <int PREC, bool RECORD>
 __device__ __forceinline__ void assign(const TransportParams &P, Lane<typename RealOf<PREC>::T> &L,
                                        unsigned long long g) {
-  const unsigned long long slot = g / P.pkg_len;
+  // source slot of work item g (a single model has at most two)
+  const unsigned long long slot = (P.n_models == 1) ? (g >= P.pkg_len ? 1ull : 0ull) : g / P.pkg_len;
   const unsigned long long pkg = P.pkg_begin + (g - slot * P.pkg_len);
   int m = 0;
   if (P.n_models > 1) {
@@ -493,7 +523,7 @@ __device__ __forceinline__ void inject(const TransportParams &P, Shared &S, Lane
       L.u_type = u01d(c.z, c.w);
     }
   } else {
-    set_freq<PREC>(S, L, cdf_pick(S.src_cdf_f[L.src], u01f_word(a.x)));
+    set_freq<PREC>(S, L, alias_pick(S.src_alias[L.src], a.x >> 9));
     const float v = u01f_fine(a.y);  // 1 - u of the direction draw
     set_paths(S, L, -__logf(u01f_word(a.z)), -__logf(u01f_word(a.w)));
     if (L.src == 0) {
@@ -668,7 +698,7 @@ __device__ __forceinline__ void absorb(const TransportParams &P, Shared &S, cons
     L.tauA = -log(u01d(c.z, c.w));
   } else {
     // one Philox block gives five 23-bit uniforms (4 x top bits + 1 from the low bits)
-    const float u_e = u01f_word(a.x), u_nu = u01f_word(a.y), u_mu = u01f_word(a.z);
+    const float u_e = u01f_word(a.x), u_mu = u01f_word(a.z);  // a.y: the re-emission bin
     const float u_ts = u01f_word(a.w);
     const float u_ta = u01f((a.x & 0x1ffu) | ((a.y & 0x1ffu) << 9) | ((a.z & 0x1fu) << 18));
     const float dEf = L.w * L.eps;
@@ -683,10 +713,10 @@ __device__ __forceinline__ void absorb(const TransportParams &P, Shared &S, cons
     }
     const float de = dEf * im;
     const float es = fmaf(u_e, de, eo);
-    const int j = node_count_f(sLnode, P.n_tnodes_pow2, es);
+    const int j = node_count_guided(S, sLnode, P.n_tnodes, es);
     if (eo + de > sLnode[P.n_tnodes - 1]) atomicAdd(&S.rare[CNT_CLAMP_HI], 1u);
     const int row = min(j, P.n_tnodes - 1);
-    set_freq<PREC>(S, L, cdf_pick_ldg(P.dcdf_f + ((size_t)row << kFreqShift), u_nu));
+    set_freq<PREC>(S, L, alias_pick_ldg(P.dalias + ((size_t)row << kFreqShift), a.y >> 9));
     // isotropic re-emission: mu' = 2u - 1, sin^2 = 4u(1-u)
     const float r2 = L.p2 + L.s * L.s;
     const float r = sqrtf(r2);
@@ -799,7 +829,7 @@ __global__ void __launch_bounds__(256) k_transport(const TransportParams P) {
     S.hg_inv2g[k] = iso ? 0.0f : (float)(0.5 / g);
     for (int s = 0; s < 2; ++s) {
       S.src_cdf_d[s][k] = P.src_cdf_d[s * kMaxFreq + k];
-      S.src_cdf_f[s][k] = (float)P.src_cdf_d[s * kMaxFreq + k];
+      S.src_alias[s][k] = P.src_alias[s * kMaxFreq + k];
       S.sed_lo[s][k] = 0u;
       S.sed_hi[s][k] = 0u;
     }
@@ -809,7 +839,13 @@ __global__ void __launch_bounds__(256) k_transport(const TransportParams P) {
     S.dir_lo[threadIdx.x] = S.dir_hi[threadIdx.x] = 0u;
   }
   if (threadIdx.x < CNT_COUNT) S.rare[threadIdx.x] = 0u;
+  if (threadIdx.x < kMaxWarps) S.wq_next[threadIdx.x] = S.wq_end[threadIdx.x] = 0ull;
   for (int j = threadIdx.x; j < P.n_tnodes_pow2; j += blockDim.x) sLnode[j] = P.Lnode_f[j];
+  for (int b = threadIdx.x; b < kGuide; b += blockDim.x) S.nguide[b] = P.nguide[b];
+  if (threadIdx.x == 0) {
+    S.g_b0 = P.nmeta[0];
+    S.g_sh = P.nmeta[1];
+  }
   __syncthreads();
 
   Tally T;
@@ -869,16 +905,37 @@ __global__ void __launch_bounds__(256) k_transport(const TransportParams P) {
     }
     idle = 0;
     if (L.st == ST_ESCAPE) escape<PREC, RECORD>(P, S, L);
-    if (L.st == ST_DEAD) {
-      // refill from the work counter: one atomic for the lanes here together
-      const unsigned m = __activemask();
-      const int leader = __ffs(m) - 1;
-      unsigned long long base = 0;
-      if (lane == leader) base = atomicAdd(P.queue, (unsigned long long)__popc(m));
-      base = __shfl_sync(m, base, leader);
-      const unsigned long long g = base + __popc(m & lanes_below);
-      if (g < P.total) assign<PREC, RECORD>(P, L, g);
-      else L.st = ST_DONE;
+    // refill the finished lanes from the warp's chunk of work items (a
+    // full-warp collective: lane 0 alone touches the warp's cursor and takes
+    // a new chunk from the device counter when this one runs out)
+    const unsigned dead = __ballot_sync(kFull, L.st == ST_DEAD);
+    if (dead != 0u) {
+      const unsigned c = __popc(dead);
+      unsigned long long b1 = 0, b2 = 0;
+      unsigned n1 = 0;
+      if (lane == 0) {
+        // P.chunk >= 32 >= c, so one new chunk always covers the shortfall
+        const int w = threadIdx.x >> 5;
+        const unsigned long long nx = S.wq_next[w];
+        n1 = (unsigned)min((unsigned long long)c, S.wq_end[w] - nx);
+        b1 = nx;
+        if (n1 < c) {
+          b2 = atomicAdd(P.queue, (unsigned long long)P.chunk);
+          S.wq_next[w] = b2 + (c - n1);
+          S.wq_end[w] = b2 + P.chunk;
+        } else {
+          S.wq_next[w] = nx + n1;
+        }
+      }
+      b1 = __shfl_sync(kFull, b1, 0);
+      b2 = __shfl_sync(kFull, b2, 0);
+      n1 = __shfl_sync(kFull, n1, 0);
+      if (L.st == ST_DEAD) {
+        const unsigned r = __popc(dead & lanes_below);
+        const unsigned long long g = (r < n1) ? b1 + r : b2 + (r - n1);
+        if (g < P.total) assign<PREC, RECORD>(P, L, g);
+        else L.st = ST_DONE;
+      }
     }
     if ((unsigned)(L.st - ST_SCATTER) <= (unsigned)(ST_FFIEND - ST_SCATTER)) rare<PREC, MODE, RECORD>(P, S, sLnode, L, T);
     if ((++sections & 31u) == 0 && L.st != ST_DONE && (globaltimer() - t0) > P.time_budget_ns) {
@@ -971,12 +1028,24 @@ __global__ void k_merge_batches(int n_cells, float *Eprev, float *Ecur) {
   }
 }
 
+// Work chunk of a warp: about 1/64 of a warp's share of the launch, so that
+// the last chunks (at most kChunkMax / 32 packages per lane) end close together.
+constexpr unsigned long long kChunkMin = 32, kChunkMax = 1024;
+unsigned chunk_size(unsigned long long total, int grid, int block) {
+  const unsigned long long warps = (unsigned long long)grid * (unsigned long long)(block / 32);
+  unsigned long long c = total / (warps * 64ull + 1ull);
+  c = c < kChunkMin ? kChunkMin : (c > kChunkMax ? kChunkMax : c);
+  return (unsigned)(c & ~31ull);
+}
+
 template <int PREC, int MODE, bool RECORD, int OPT = 0>
 cudaError_t launch_one(const TransportParams &P, int grid, int block, size_t smem, cudaStream_t st) {
   auto kern = k_transport<PREC, MODE, RECORD, OPT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<grid, block, smem, st>>>(P);
+  TransportParams Q = P;
+  Q.chunk = chunk_size(P.total, grid, block);
+  kern<<<grid, block, smem, st>>>(Q);
   launch_counter_add(1);
   return cudaGetLastError();
 }

@@ -116,6 +116,29 @@ def test_empty_cloud_sed_is_the_source(D, oracle):
     assert m.stats()["absorbed"] == 0
 
 
+@pytest.mark.parametrize("point", [False, True])
+def test_empty_cloud_mixed_sed_samples_the_source(D, oracle, point):
+    """Zero density: in the FP32 forms every package leaves at the frequency
+    its source spectrum's alias table gave it, so the escaping SED is a
+    multinomial sample of L_k = L dnu_k S_k / sum (each bin within 5 sigma)."""
+    cloud = W.config1()
+    if point:
+        cloud = cloud.replace(J_ext=None, L_point=W.L_SUN, point_spec=W.blackbody(cloud.freq, 6000.0))
+    cloud = cloud.replace(rho=np.zeros(cloud.n_cells))
+    N = 50_000_000
+    m = D.Model(cloud, precision="mixed").run(N, seed=3)
+    sed = m.sed()
+    L = sed.sum()
+    S = (cloud.point_spec if point else cloud.J_ext) * oracle.freq_weights(cloud.freq)
+    p = S / S.sum()
+    expect = L * p
+    sig = L * np.sqrt(p * (1 - p) / N)
+    ok = p > 1e-6
+    z = np.abs(sed[ok] - expect[ok]) / sig[ok]
+    assert z.max() < 5.0, (z.max(), np.argmax(z))
+    assert np.all(sed[~ok] <= L * 1e-5)
+
+
 def test_single_shell_and_single_package(D, oracle):
     cloud = W.grey_model(1, 1.0, albedo=0.3, g=0.5)
     T = np.array([20.0])
