@@ -5,6 +5,8 @@ counts and path hashes, absorbed energies within 1e-5 relative.
 Full IRE: per-shell temperatures within 1 % and within the combined standard
 error over 16 seeds.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -200,3 +202,25 @@ def test_repeated_runs_finish_every_package(D, prec):
         assert st["escaped"] == 100_000 and st["killed_cap"] == 0
         assert st["E_escaped"] + st["E_lost"] == pytest.approx(st["E_injected"], rel=1e-9)
         m.close()
+
+
+def test_time_budget_stops_the_kernel_and_the_context_stays_usable(D):
+    """Failure path without a GPU fault: a launch that runs out of its
+    wall-clock budget stops early (device flag 1), the run reports
+    DIES_ETIMEOUT, and the same handle then completes a normal run."""
+    cloud = W.config5_internal()
+    m = D.Model(cloud, precision="mixed")
+    D.dies_set_time_budget(m.h, 2e-3)
+    with pytest.raises(D.DiesError) as ei:
+        m.run(200_000_000, seed=1)
+    assert ei.value.code == D.DIES_ETIMEOUT
+    raw = D.dies_stats()
+    assert D.load().dies_get_stats(m.h, ctypes.byref(raw)) == D.DIES_ETIMEOUT
+    st = raw.as_dict()
+    assert st["status_word"] & 1
+    assert st["injected"] < 200_000_000
+    D.dies_set_time_budget(m.h, 120.0)
+    m.run(200_000, seed=2)
+    st = m.stats()
+    assert st["status_word"] == 0 and st["injected"] == 200_000
+    assert st["E_escaped"] + st["E_lost"] == pytest.approx(st["E_injected"], rel=1e-9)
