@@ -164,6 +164,17 @@ int dies_set_launch(dies_model *m, int block_size, int blocks_per_sm, int rare_b
  * launch that reaches it stops early and the run returns DIES_ETIMEOUT. */
 int dies_set_time_budget(dies_model *m, double seconds);
 
+/* Graph mode (no counterpart in the paper; launch-overhead removal for
+ * repeated runs such as seed ensembles): enable = 1 makes each run replay
+ * one CUDA graph of the per-run device work (accumulator reset, transport,
+ * tallies, temperatures), captured on the first run of a configuration and
+ * captured again when the package count, precision, launch shape, tables'
+ * sizes or workspace change.  The seed reaches the kernels through a pinned
+ * host word that the graph copies first, so in graph mode dies_run_async
+ * waits for the handle's previous run before enqueueing.  Results are the
+ * same as without a graph.  enable must be 0 or 1 (default 0). */
+int dies_set_graph(dies_model *m, int enable);
+
 /* Device memory.  By default the library allocates its own device memory.
  * Alternatively the caller provides one device buffer of at least
  * dies_workspace_bytes() bytes (256-byte aligned, e.g. from a PyTorch
@@ -249,6 +260,8 @@ int dies_batch_set_dust(dies_batch *b, const double *freq_hz, int n_freq, const 
 int dies_batch_set_sources(dies_batch *b, const double *J_ext, double L_point, const double *point_spectrum);
 int dies_batch_set_stream(dies_batch *b, void *cuda_stream);
 int dies_batch_set_launch(dies_batch *b, int block_size, int blocks_per_sm, int rare_batch, int inner_moves);
+/* Graph mode for the batch, as dies_set_graph. */
+int dies_batch_set_graph(dies_batch *b, int enable);
 int dies_run_batch(dies_batch *b, uint64_t n_packages_per_model, uint64_t seed);
 int dies_run_batch_async(dies_batch *b, uint64_t n_packages_per_model, uint64_t seed);
 /* Results: concatenated per-shell arrays (n_total = shell_offsets[n_models])
@@ -268,6 +281,32 @@ uint64_t dies_launch_count(void);
 
 /* Library version string. */
 const char *dies_version(void);
+
+/* ------------------------------------------------------- measurement */
+
+/* Measured rates of the units that bound the transport (no counterpart in
+ * the paper; the roofline denominators of its hot path): whole-GPU
+ * operations per second of FP32 fused multiply-add, 32-bit integer
+ * multiply-add, MUFU base-2 logarithm and FP64 fused multiply-add (each from
+ * 8 independent chains per thread, 8 CTAs of 256 threads per SM), and of the
+ * L2 FP64 atomic add with return that each absorption performs (Sect. 2.1),
+ * to 2^20 distinct addresses, to 64 addresses and to one address. */
+typedef struct {
+  double fp32_fma_per_s;
+  double int_mad_per_s;
+  double mufu_per_s;
+  double fp64_fma_per_s;
+  double atomic_f64_ret_distinct_per_s;
+  double atomic_f64_ret_64addr_per_s;
+  double atomic_f64_ret_same_per_s;
+  int sm_count;
+} dies_peaks;
+
+/* Runs the microbenchmarks on the current device (legacy default stream,
+ * ~0.3 s, 8 MiB of device memory allocated and freed).  Errors:
+ * DIES_EINVAL (out NULL), DIES_ENOMEM, DIES_ECUDA (no device, launch
+ * failure). */
+int dies_measure_peaks(dies_peaks *out);
 
 #ifdef __cplusplus
 }

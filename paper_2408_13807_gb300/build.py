@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdies.so")
-SOURCES = ("dies_api.cu", "dies_tables.cu", "dies_transport.cu")
+SOURCES = ("dies_api.cu", "dies_tables.cu", "dies_transport.cu", "dies_peaks.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

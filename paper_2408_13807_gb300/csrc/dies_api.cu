@@ -86,7 +86,7 @@ struct Layout {
   size_t sed_q, inj_q, dir_q;
   size_t freq, kabs, ksca, g, J, spec, dnu, src_cdf_d, src_alias, src_sum;
   size_t Lnode_d, Lnode_f, lnT, dalias, dcdf_d, nguide, nmeta;
-  size_t counters, energies, queue, status, diag;
+  size_t counters, energies, queue, status, diag, seedw;
   size_t total;
 };
 
@@ -128,8 +128,33 @@ struct Problem {
   bool stats_pending = false;
   unsigned long long launches_at_start = 0;
   dies_stats stats{};
+  // graph replay of the per-run device work (dies_set_graph)
+  bool use_graph = false;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  unsigned long long *seed_host = nullptr;  // pinned; copied to the device by the graph
+  struct GraphKey {
+    TransportParams P;
+    uint64_t n;
+    int prec, n_batches, grid, block, n_cells, n_models, n_tnodes;
+  };
+  GraphKey gkey{};
+  bool graph_valid = false;
+  unsigned long long graph_kernels = 0;
+
+  void drop_graph() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    gexec = nullptr;
+    graph = nullptr;
+    graph_valid = false;
+  }
 
   ~Problem() {
+    drop_graph();
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (seed_host) cudaFreeHost(seed_host);
     if (ws_owned && ws) cudaFree(ws);
     for (auto &e : ev)
       if (e) cudaEventDestroy(e);
@@ -189,6 +214,7 @@ struct Problem {
     L.queue = seg(2 * 8);
     L.status = seg(4);
     L.diag = seg(16 * 4);
+    L.seedw = seg(8);
     L.total = o;
     return L;
   }
@@ -364,19 +390,20 @@ struct Problem {
     return DIES_OK;
   }
 
-  int reset_accumulators() {
-    DIES_CUDA(cudaMemsetAsync(ws + lay.E, 0, (size_t)n_cells * 8, stream));
-    DIES_CUDA(cudaMemsetAsync(ws + lay.Eprev, 0, (size_t)n_cells * 4, stream));
-    DIES_CUDA(cudaMemsetAsync(ws + lay.Ecur, 0, (size_t)n_cells * 4, stream));
-    DIES_CUDA(cudaMemsetAsync(ws + lay.sed, 0, (size_t)n_models * kMaxFreq * 8, stream));
-    DIES_CUDA(cudaMemsetAsync(ws + lay.sed_q, 0, (size_t)n_models * 2 * kMaxFreq * 8, stream));
-    DIES_CUDA(cudaMemsetAsync(ws + lay.inj_q, 0, (size_t)n_models * 2 * 8, stream));
-    DIES_CUDA(cudaMemsetAsync(ws + lay.dir_q, 0, (size_t)n_models * 2 * 8, stream));
-    DIES_CUDA(cudaMemsetAsync(ws + lay.counters, 0, 16 * 8 + 0, stream));
-    DIES_CUDA(cudaMemsetAsync(ws + lay.energies, 0, 8 * 8, stream));
-    DIES_CUDA(cudaMemsetAsync(ws + lay.queue, 0, 2 * 8, stream));
-    DIES_CUDA(cudaMemsetAsync(ws + lay.status, 0, 4, stream));
-    DIES_CUDA(cudaMemsetAsync(ws + lay.diag, 0, 16 * 4, stream));
+  int reset_accumulators() { return reset_accumulators_on(stream); }
+  int reset_accumulators_on(cudaStream_t st) {
+    DIES_CUDA(cudaMemsetAsync(ws + lay.E, 0, (size_t)n_cells * 8, st));
+    DIES_CUDA(cudaMemsetAsync(ws + lay.Eprev, 0, (size_t)n_cells * 4, st));
+    DIES_CUDA(cudaMemsetAsync(ws + lay.Ecur, 0, (size_t)n_cells * 4, st));
+    DIES_CUDA(cudaMemsetAsync(ws + lay.sed, 0, (size_t)n_models * kMaxFreq * 8, st));
+    DIES_CUDA(cudaMemsetAsync(ws + lay.sed_q, 0, (size_t)n_models * 2 * kMaxFreq * 8, st));
+    DIES_CUDA(cudaMemsetAsync(ws + lay.inj_q, 0, (size_t)n_models * 2 * 8, st));
+    DIES_CUDA(cudaMemsetAsync(ws + lay.dir_q, 0, (size_t)n_models * 2 * 8, st));
+    DIES_CUDA(cudaMemsetAsync(ws + lay.counters, 0, 16 * 8 + 0, st));
+    DIES_CUDA(cudaMemsetAsync(ws + lay.energies, 0, 8 * 8, st));
+    DIES_CUDA(cudaMemsetAsync(ws + lay.queue, 0, 2 * 8, st));
+    DIES_CUDA(cudaMemsetAsync(ws + lay.status, 0, 4, st));
+    DIES_CUDA(cudaMemsetAsync(ws + lay.diag, 0, 16 * 4, st));
     return DIES_OK;
   }
 
@@ -400,11 +427,30 @@ struct Problem {
       table_built_this_run = true;
     }
     DIES_CUDA(cudaEventRecord(ev[1], stream));
-    if ((rc = reset_accumulators())) return rc;
     int grid;
     if ((rc = grid_for(prec, MODE_IRE, &grid))) return rc;
+    if (use_graph) {
+      if ((rc = replay_graph(n, seed, grid))) return rc;
+    } else {
+      if ((rc = enqueue_body(stream, n, seed, grid, nullptr))) return rc;
+    }
+    DIES_CUDA(cudaEventRecord(ev[4], stream));
+    has_result = true;
+    stats_pending = true;
+    return DIES_OK;
+  }
+
+  // The per-run device work after the table build: accumulator reset, the
+  // transport launch(es), tallies and temperatures, on stream st.  With
+  // seed_dev set (graph capture) the kernels read the seed from there and
+  // the timing events are recorded as graph nodes.
+  int enqueue_body(cudaStream_t st, uint64_t n, uint64_t seed, int grid, const unsigned long long *seed_dev) {
+    int rc;
+    const unsigned rec_flags = seed_dev ? cudaEventRecordExternal : cudaEventRecordDefault;
+    if ((rc = reset_accumulators_on(st))) return rc;
     TransportParams P = params(MODE_IRE, n, seed);
-    DIES_CUDA(cudaEventRecord(ev[2], stream));
+    P.seed_dev = seed_dev;
+    DIES_CUDA(cudaEventRecordWithFlags(ev[2], st, rec_flags));
     const int nb = (prec == PREC_FP32) ? n_batches : 1;
     const uint64_t per = (n + nb - 1) / nb;
     for (int b = 0; b < nb; ++b) {
@@ -415,21 +461,76 @@ struct Problem {
       P.pkg_len = len;
       P.total = total_slots() * len;
       P.queue = at<unsigned long long>(lay.queue) + (b & 1);
-      if (b > 0) DIES_CUDA(cudaMemsetAsync(P.queue, 0, 8, stream));
-      DIES_CUDA(launch_transport(prec, MODE_IRE, false, P, grid, block, stream));
-      if (prec == PREC_FP32) DIES_CUDA(launch_merge(stream, n_cells, at<float>(lay.Eprev), at<float>(lay.Ecur)));
+      if (b > 0) DIES_CUDA(cudaMemsetAsync(P.queue, 0, 8, st));
+      DIES_CUDA(launch_transport(prec, MODE_IRE, false, P, grid, block, st));
+      if (prec == PREC_FP32) DIES_CUDA(launch_merge(st, n_cells, at<float>(lay.Eprev), at<float>(lay.Ecur)));
     }
-    DIES_CUDA(cudaEventRecord(ev[3], stream));
+    DIES_CUDA(cudaEventRecordWithFlags(ev[3], st, rec_flags));
     if (prec != PREC_FP64)
-      DIES_CUDA(launch_tally(stream, n_models, at<ModelDesc>(lay.desc), n, at<unsigned long long>(lay.sed_q),
+      DIES_CUDA(launch_tally(st, n_models, at<ModelDesc>(lay.desc), n, at<unsigned long long>(lay.sed_q),
                              at<unsigned long long>(lay.inj_q), at<unsigned long long>(lay.dir_q), at<double>(lay.sed),
                              at<double>(lay.energies)));
-    DIES_CUDA(launch_finalize(stream, n_cells, at<double>(lay.E), at<float>(lay.Eprev), at<float>(lay.Ecur),
+    DIES_CUDA(launch_finalize(st, n_cells, at<double>(lay.E), at<float>(lay.Eprev), at<float>(lay.Ecur),
                               prec == PREC_FP32, at<double>(lay.inv_mass), at<double>(lay.Lnode_d),
                               at<double>(lay.lnT), n_tnodes, at<double>(lay.T)));
-    DIES_CUDA(cudaEventRecord(ev[4], stream));
-    has_result = true;
-    stats_pending = true;
+    return DIES_OK;
+  }
+
+  // Graph mode: capture enqueue_body once per configuration (on a private
+  // stream), then replay it on the handle's stream; the seed travels through
+  // a pinned host word that the graph copies to the device first.
+  int replay_graph(uint64_t n, uint64_t seed, int grid) {
+    GraphKey k;
+    std::memset(&k, 0, sizeof k);
+    k.P = params(MODE_IRE, n, 0);
+    k.n = n;
+    k.prec = prec;
+    k.n_batches = n_batches;
+    k.grid = grid;
+    k.block = block;
+    k.n_cells = n_cells;
+    k.n_models = n_models;
+    k.n_tnodes = n_tnodes;
+    if (!graph_valid || std::memcmp(&k, &gkey, sizeof k) != 0) {
+      drop_graph();
+      if (!cap_stream) DIES_CUDA(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
+      if (!seed_host) {
+        void *h = nullptr;
+        cudaError_t e = cudaHostAlloc(&h, 8, cudaHostAllocDefault);
+        if (e != cudaSuccess) return fail(DIES_ENOMEM, "pinned seed word: %s", cudaGetErrorString(e));
+        seed_host = static_cast<unsigned long long *>(h);
+      }
+      // the capture stream must not run ahead of work already on the handle's stream
+      DIES_CUDA(cudaStreamSynchronize(stream));
+      const unsigned long long before = g_launches.load();
+      DIES_CUDA(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeRelaxed));
+      const unsigned long long *seed_dev = at<unsigned long long>(lay.seedw);
+      cudaError_t e = cudaMemcpyAsync(ws + lay.seedw, seed_host, 8, cudaMemcpyHostToDevice, cap_stream);
+      int rc = (e == cudaSuccess) ? enqueue_body(cap_stream, n, 0, grid, seed_dev)
+                                  : fail(DIES_ECUDA, "capture: %s", cudaGetErrorString(e));
+      cudaGraph_t g = nullptr;
+      const cudaError_t ee = cudaStreamEndCapture(cap_stream, &g);
+      graph_kernels = g_launches.load() - before;
+      g_launches.fetch_sub(graph_kernels);  // captured, not launched
+      if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+      }
+      if (ee != cudaSuccess) return fail(DIES_ECUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(ee));
+      graph = g;
+      e = cudaGraphInstantiate(&gexec, graph, 0);
+      if (e != cudaSuccess) {
+        drop_graph();
+        return fail(DIES_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+      }
+      gkey = k;
+      graph_valid = true;
+    }
+    // the previous replay may not have copied its seed yet
+    DIES_CUDA(cudaStreamSynchronize(stream));
+    *seed_host = seed;
+    DIES_CUDA(cudaGraphLaunch(gexec, stream));
+    launch_counter_add((unsigned)graph_kernels);
     return DIES_OK;
   }
 
@@ -745,6 +846,13 @@ int dies_set_time_budget(dies_model *m, double seconds) {
   return DIES_OK;
 }
 
+int dies_set_graph(dies_model *m, int enable) {
+  if (!m) return fail(DIES_EINVAL, "model is NULL");
+  if (enable != 0 && enable != 1) return fail(DIES_EINVAL, "enable must be 0 or 1");
+  m->p.use_graph = enable != 0;
+  return DIES_OK;
+}
+
 int dies_workspace_bytes(const dies_model *m, size_t *bytes) {
   if (!m || !bytes) return fail(DIES_EINVAL, "NULL argument");
   *bytes = m->p.layout().total;
@@ -965,6 +1073,13 @@ int dies_batch_set_stream(dies_batch *b, void *s) {
 int dies_batch_set_launch(dies_batch *b, int block_size, int blocks_per_sm, int rare_batch, int inner_moves) {
   if (!b) return fail(DIES_EINVAL, "batch is NULL");
   return set_launch(b->p, block_size, blocks_per_sm, rare_batch, inner_moves);
+}
+
+int dies_batch_set_graph(dies_batch *b, int enable) {
+  if (!b) return fail(DIES_EINVAL, "batch is NULL");
+  if (enable != 0 && enable != 1) return fail(DIES_EINVAL, "enable must be 0 or 1");
+  b->p.use_graph = enable != 0;
+  return DIES_OK;
 }
 
 int dies_run_batch_async(dies_batch *b, uint64_t n, uint64_t seed) {

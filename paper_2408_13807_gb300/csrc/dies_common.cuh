@@ -113,6 +113,7 @@ struct TransportParams {
   unsigned long long pkg_len;     // packages per source in this launch
   unsigned long long n_per_source;  // packages per source in the whole run (sets eps)
   unsigned long long seed;
+  const unsigned long long *seed_dev;  // if set, the seed is read from here (graph replays)
   unsigned long long *queue;
   unsigned long long *counters;   // [CNT_COUNT]
   double *energies;               // [EN_COUNT]

@@ -74,6 +74,7 @@ struct Shared {
   uint32_t src_alias[2][kMaxFreq];   // FP32 forms: source spectra as alias tables
   uint16_t nguide[kGuide];           // FP32 forms: node-search guide
   int g_b0, g_sh;
+  uint32_t key[2];                   // Philox key (the run's seed)
   double kabs_d[kMaxFreq], ksca_d[kMaxFreq], g_d[kMaxFreq];
   double src_cdf_d[2][kMaxFreq];
   // FP32 forms, single model: 64-bit fixed-point tallies kept as 32-bit
@@ -110,9 +111,8 @@ struct Tally {
 };
 
 template <int PREC>
-__device__ __forceinline__ U4 draw(const TransportParams &P, Lane<typename RealOf<PREC>::T> &L) {
-  const U4 r = philox10(L.pkg_lo, L.pkg_hi, L.blk, (uint32_t)L.model ^ ((uint32_t)L.src << 24), (uint32_t)P.seed,
-                        (uint32_t)(P.seed >> 32));
+__device__ __forceinline__ U4 draw(const Shared &S, Lane<typename RealOf<PREC>::T> &L) {
+  const U4 r = philox10(L.pkg_lo, L.pkg_hi, L.blk, (uint32_t)L.model ^ ((uint32_t)L.src << 24), S.key[0], S.key[1]);
   ++L.blk;
   return r;
 }
@@ -497,7 +497,7 @@ __device__ __forceinline__ void inject(const TransportParams &P, Shared &S, Lane
   if constexpr (PREC == PREC_FP64) {
     const double u_f = u01d(a.x, a.y), u_mu = u01d(a.z, a.w);
     set_freq<PREC>(S, L, cdf_pick(S.src_cdf_d[L.src], u_f));
-    const U4 b = draw<PREC>(P, L);
+    const U4 b = draw<PREC>(S, L);
     L.tauS = -log(u01d(b.x, b.y));
     L.tauA = -log(u01d(b.z, b.w));
     if (L.src == 0) {
@@ -518,7 +518,7 @@ __device__ __forceinline__ void inject(const TransportParams &P, Shared &S, Lane
       L.cell = __ldg(&D->point_cell);
     }
     if (P.ffi) {
-      const U4 c = draw<PREC>(P, L);
+      const U4 c = draw<PREC>(S, L);
       u_int = u01d(c.x, c.y);
       L.u_type = u01d(c.z, c.w);
     }
@@ -549,7 +549,7 @@ __device__ __forceinline__ void inject(const TransportParams &P, Shared &S, Lane
       L.cell = __ldg(&D->point_cell);
     }
     if (P.ffi) {
-      const U4 c = draw<PREC>(P, L);
+      const U4 c = draw<PREC>(S, L);
       u_int = u01f_word(c.x);
       L.u_type = u01f_word(c.y);
     }
@@ -612,7 +612,7 @@ __device__ __forceinline__ void scatter(const TransportParams &P, Shared &S, Lan
       L.s = 0.0;
       L.p2 = 0.0;
     }
-    const U4 b = draw<PREC>(P, L);
+    const U4 b = draw<PREC>(S, L);
     L.tauS = -log(u01d(b.x, b.y));
     L.tauA = -log(u01d(b.z, b.w));
   } else {
@@ -687,13 +687,13 @@ __device__ __forceinline__ void absorb(const TransportParams &P, Shared &S, cons
       f = cdf_pick_ldg(P.dcdf_d + ((size_t)row << kFreqShift), u_nu);
     }
     set_freq<PREC>(S, L, f);
-    const U4 b = draw<PREC>(P, L);
+    const U4 b = draw<PREC>(S, L);
     const double mu = 2.0 * u01d(b.x, b.y) - 1.0;
     const double r2 = L.p2 + L.s * L.s;
     const double r = sqrt(r2);
     L.s = r * mu;
     L.p2 = fmax(r2 - L.s * L.s, 0.0);
-    const U4 c = draw<PREC>(P, L);
+    const U4 c = draw<PREC>(S, L);
     L.tauS = -log(u01d(c.x, c.y));
     L.tauA = -log(u01d(c.z, c.w));
   } else {
@@ -791,7 +791,7 @@ __device__ __forceinline__ void rare(const TransportParams &P, Shared &S, const 
       return;
     }
   }
-  const U4 a = draw<PREC>(P, L);  // every rare event starts with one Philox block
+  const U4 a = draw<PREC>(S, L);  // every rare event starts with one Philox block
   L.st = ST_NORMAL;
   if (kind == ST_INJECT) inject<PREC, RECORD>(P, S, L, T, a);
   else if (kind == ST_SCATTER) scatter<PREC, RECORD>(P, S, L, T, a);
@@ -845,6 +845,9 @@ __global__ void __launch_bounds__(256) k_transport(const TransportParams P) {
   if (threadIdx.x == 0) {
     S.g_b0 = P.nmeta[0];
     S.g_sh = P.nmeta[1];
+    const unsigned long long seed = P.seed_dev ? *P.seed_dev : P.seed;
+    S.key[0] = (uint32_t)seed;
+    S.key[1] = (uint32_t)(seed >> 32);
   }
   __syncthreads();
 

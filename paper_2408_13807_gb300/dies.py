@@ -37,12 +37,15 @@ PREC = {"mixed": DIES_PREC_MIXED, "fp32": DIES_PREC_FP32, "fp64": DIES_PREC_FP64
 # every symbol include/dies.h declares
 EXPORTS = (
     "dies_create_model", "dies_set_dust", "dies_set_sources", "dies_set_weighting", "dies_set_precision",
-    "dies_set_tgrid", "dies_set_stream", "dies_set_launch", "dies_set_time_budget", "dies_workspace_bytes",
+    "dies_set_tgrid", "dies_set_stream", "dies_set_launch", "dies_set_time_budget", "dies_set_graph",
+    "dies_workspace_bytes",
     "dies_set_workspace", "dies_run", "dies_run_async", "dies_get_temperatures", "dies_get_absorbed",
     "dies_get_escaping_sed", "dies_get_stats", "dies_run_frozen", "dies_destroy_model", "dies_create_batch",
     "dies_batch_set_dust", "dies_batch_set_sources", "dies_batch_set_stream", "dies_batch_set_launch",
+    "dies_batch_set_graph",
     "dies_run_batch", "dies_run_batch_async", "dies_batch_get_temperatures", "dies_batch_get_escaping_sed",
     "dies_batch_get_stats", "dies_destroy_batch", "dies_last_error", "dies_launch_count", "dies_version",
+    "dies_measure_peaks",
     "dies_run_frozen_static",
 )
 
@@ -70,6 +73,18 @@ class dies_stats(ctypes.Structure):
         return d
 
 
+class dies_peaks(ctypes.Structure):
+    _fields_ = [
+        ("fp32_fma_per_s", ctypes.c_double), ("int_mad_per_s", ctypes.c_double), ("mufu_per_s", ctypes.c_double),
+        ("fp64_fma_per_s", ctypes.c_double), ("atomic_f64_ret_distinct_per_s", ctypes.c_double),
+        ("atomic_f64_ret_64addr_per_s", ctypes.c_double), ("atomic_f64_ret_same_per_s", ctypes.c_double),
+        ("sm_count", ctypes.c_int),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _P = ctypes.POINTER
 _dp = _P(ctypes.c_double)
 _vp = ctypes.c_void_p
@@ -95,6 +110,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "dies_set_stream": (i, [_vp, _vp]),
         "dies_set_launch": (i, [_vp, i, i, i, i]),
         "dies_set_time_budget": (i, [_vp, d]),
+        "dies_set_graph": (i, [_vp, i]),
+        "dies_batch_set_graph": (i, [_vp, i]),
         "dies_workspace_bytes": (i, [_vp, _P(ctypes.c_size_t)]),
         "dies_set_workspace": (i, [_vp, _vp, ctypes.c_size_t]),
         "dies_run": (i, [_vp, u64, u64]),
@@ -120,6 +137,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "dies_last_error": (c, []),
         "dies_launch_count": (u64, []),
         "dies_version": (c, []),
+        "dies_measure_peaks": (i, [_vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -183,6 +201,14 @@ def dies_set_launch(h, block_size: int, blocks_per_sm: int = 0, rare_batch: int 
 
 def dies_set_time_budget(h, seconds: float):
     return _check(load().dies_set_time_budget(h, float(seconds)))
+
+
+def dies_set_graph(h, enable: bool):
+    return _check(load().dies_set_graph(h, int(bool(enable))))
+
+
+def dies_batch_set_graph(h, enable: bool):
+    return _check(load().dies_batch_set_graph(h, int(bool(enable))))
 
 
 def dies_workspace_bytes(h) -> int:
@@ -322,6 +348,13 @@ def dies_version() -> str:
     return load().dies_version().decode()
 
 
+def dies_measure_peaks() -> dict:
+    """Measured whole-GPU rates of the units that bound the transport."""
+    p = dies_peaks()
+    _check(load().dies_measure_peaks(ctypes.byref(p)))
+    return p.as_dict()
+
+
 # ---------------------------------------------------------- conveniences
 def _torch_stream_and_workspace(nbytes: int, device):
     import torch
@@ -338,7 +371,7 @@ class Model:
 
     def __init__(self, cloud, precision: str = "mixed", n_batches: int = 1, fp64_radius: float = 0.0,
                  tgrid=(2.7, 1500.0, 1024), torch_memory: bool = True, device: int = 0, block_size: int = 256,
-                 blocks_per_sm: int = 0, rare_batch: int = 16, inner_moves: int = 32):
+                 blocks_per_sm: int = 0, rare_batch: int = 16, inner_moves: int = 32, graph: bool = False):
         self.cloud = cloud
         self.h = dies_create_model(cloud.radii, cloud.rho, cloud.length_unit_cm)
         self.n_cells = cloud.n_cells
@@ -350,6 +383,7 @@ class Model:
         dies_set_precision(self.h, PREC[precision], n_batches, fp64_radius)
         dies_set_tgrid(self.h, *tgrid)
         dies_set_launch(self.h, block_size, blocks_per_sm, rare_batch, inner_moves)
+        dies_set_graph(self.h, graph)
         if torch_memory:
             stream, self._ws = _torch_stream_and_workspace(dies_workspace_bytes(self.h), device)
             dies_set_stream(self.h, stream)
@@ -398,7 +432,7 @@ class Batch:
     spectrum) in one persistent launch."""
 
     def __init__(self, clouds, block_size: int = 256, blocks_per_sm: int = 0, rare_batch: int = 16,
-                 inner_moves: int = 32):
+                 inner_moves: int = 32, graph: bool = False):
         c0 = clouds[0]
         n = np.array([c.n_cells for c in clouds], dtype=np.int32)
         self.offsets = np.concatenate([[0], np.cumsum(n)]).astype(np.int32)
@@ -414,6 +448,7 @@ class Batch:
         pt = next((c for c in clouds if c.L_point > 0), None)
         dies_batch_set_sources(self.h, J, pt.L_point if pt else 0.0, pt.point_spec if pt else None)
         dies_batch_set_launch(self.h, block_size, blocks_per_sm, rare_batch, inner_moves)
+        dies_batch_set_graph(self.h, graph)
 
     def set_stream(self, stream_handle: int):
         dies_batch_set_stream(self.h, stream_handle)

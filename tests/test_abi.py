@@ -47,6 +47,7 @@ def test_create_and_set_validate_inputs(lib):
         D.dies_set_precision(h, D.DIES_PREC_FP32, 50, 0.0)
         D.dies_set_tgrid(h, 2.7, 1500.0, 1024)
         D.dies_set_launch(h, 128, 0, 12, 4)
+        D.dies_set_graph(h, True)
         assert D.dies_workspace_bytes(h) > 0
         bad = [
             lambda: D.dies_set_dust(h, m.freq[::-1], m.kabs, m.ksca, m.g),
@@ -67,6 +68,9 @@ def test_create_and_set_validate_inputs(lib):
             lambda: D.dies_set_launch(h, 128, 0, 0),
             lambda: D.dies_set_launch(h, 128, 0, 33),
             lambda: D.dies_set_launch(h, 128, 0, 8, 0),
+            lambda: D.dies_set_launch(h, 128, 0, 8, 65),
+            lambda: D._check(D.load().dies_set_graph(h, 2)),
+            lambda: D.dies_set_time_budget(h, 0.0),
         ]
         for call in bad:
             with pytest.raises(D.DiesError) as e:

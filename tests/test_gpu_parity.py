@@ -224,3 +224,61 @@ def test_time_budget_stops_the_kernel_and_the_context_stays_usable(D):
     st = m.stats()
     assert st["status_word"] == 0 and st["injected"] == 200_000
     assert st["E_escaped"] + st["E_lost"] == pytest.approx(st["E_injected"], rel=1e-9)
+
+
+def test_measured_unit_peaks_are_plausible(D):
+    """The roofline denominators: whole-GPU rates within broad physical
+    bounds of an sm_100-class part (152 SMs near 2 GHz)."""
+    p = D.dies_measure_peaks()
+    sms = p["sm_count"]
+    assert sms > 0
+    clk = 2.2e9
+    assert 0.2 * sms * 128 * 1.0e9 < p["fp32_fma_per_s"] <= 1.05 * sms * 128 * clk
+    assert 0.0 < p["mufu_per_s"] < p["fp32_fma_per_s"]
+    assert 0.0 < p["fp64_fma_per_s"] < p["fp32_fma_per_s"]
+    assert 0.0 < p["int_mad_per_s"] <= 1.05 * sms * 128 * clk
+    assert p["atomic_f64_ret_distinct_per_s"] > p["atomic_f64_ret_same_per_s"] > 0.0
+
+
+def test_graph_replays_match_plain_runs(D):
+    """Graph mode: per-seed replays of one captured graph give the same
+    statistics as plain runs (pooled shells of 6 batch models, 8 seeds each),
+    conserve energy, really use each seed, and recapture when the package
+    count changes."""
+    clouds = W.config4_models(6, seed=11)
+    N = 200_000
+    bg = D.Batch(clouds, graph=True)
+    bp = D.Batch(clouds, graph=False)
+    Tg, Tp = [], []
+    for s in range(8):
+        l0 = D.dies_launch_count()
+        bg.run(N, seed=s)
+        st = bg.stats()
+        assert st["injected"] == N * len(clouds) and st["status_word"] == 0
+        assert st["E_escaped"] + st["E_lost"] == pytest.approx(st["E_injected"], rel=1e-9)
+        assert D.dies_launch_count() - l0 >= 3  # transport, tally, finalize replayed
+        Tg.append(bg.temperatures())
+        Tp.append(bp.run(N, seed=100 + s).temperatures())
+    Tg, Tp = np.array(Tg), np.array(Tp)
+    assert not np.array_equal(Tg[0], Tg[1])
+    z = []
+    for i in range(len(clouds)):
+        r = compare_ensembles(Tg[:, bg.offsets[i]:bg.offsets[i + 1]], Tp[:, bp.offsets[i]:bp.offsets[i + 1]], 0.02)
+        z.append(r["z"][r["gated"]])
+    z = np.concatenate(z)
+    assert len(z) >= 50 and np.mean(z > 3.0) <= 0.05 and z.max() <= 6.0, (len(z), np.mean(z > 3), z.max())
+    bg.run(N // 2, seed=9)
+    assert bg.stats()["injected"] == (N // 2) * len(clouds)
+    bg.run(N, seed=10)
+    assert bg.stats()["injected"] == N * len(clouds)
+    bg.close()
+    bp.close()
+
+
+def test_graph_mode_single_model_matches_oracle(D, oracle):
+    cloud = W.config1()
+    N = 1_000_000
+    m = D.Model(cloud, precision="mixed", graph=True)
+    Tg = np.array([m.run(N, seed=s).temperatures() for s in range(16)])
+    To = np.array([r["T"] for r in oracle.run_seeds(cloud, N, range(100, 116))])
+    assert_ensembles_agree(Tg, To, 0.01, min_gated=cloud.n_cells // 2)
