@@ -336,7 +336,7 @@ def run_ours(args):
     from paper_2408_13807_gb300 import autotune
     if args.block:
         shapes = [{"block_size": args.block, "blocks_per_sm": args.blocks_per_sm, "rare_batch": args.rare_batch,
-                   "inner_moves": args.inner_moves} for _ in clouds]
+                   "inner_moves": args.inner_moves, "aggregate_atomics": args.aggregate_atomics} for _ in clouds]
     else:
         shapes = [autotune.best_launch(c, "mixed") for c in clouds]  # tuned here if not cached (untimed)
     models = [D.Model(c, precision="mixed", fp64_radius=args.fp64_radius, **sh) for c, sh in zip(clouds, shapes)]
@@ -487,6 +487,7 @@ def main():
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--rare-batch", type=int, default=16)
     ap.add_argument("--inner-moves", type=int, default=32)
+    ap.add_argument("--aggregate-atomics", type=int, default=0)
     ap.add_argument("--fp64-radius", type=float, default=0.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

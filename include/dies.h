@@ -156,9 +156,15 @@ int dies_set_stream(dies_model *m, void *cuda_stream);
  * absorptions and package starts together once this many of its lanes wait
  * for one (or when no lane can move on); inner_moves in [1, 64]: boundary
  * crossings a lane may make between two such rare-event passes (taken in
- * steps of 4, the warp checking its parked lanes after each step).
- * Defaults 256, 0, 16, 32.  Results do not depend on these values. */
-int dies_set_launch(dies_model *m, int block_size, int blocks_per_sm, int rare_batch, int inner_moves);
+ * steps of 4, the warp checking its parked lanes after each step);
+ * aggregate_atomics 0 or 1 (FP32 forms): lanes of a warp absorbing in the
+ * same shell in the same pass add their energies with one atomic, each lane
+ * taking as its E_old the returned value plus the energies of the lower
+ * lanes (the order of a serial run; for absorption-heavy models with hot
+ * inner shells).  Defaults 256, 0, 16, 32, 0.  Results do not depend on
+ * these values beyond FP32 rounding. */
+int dies_set_launch(dies_model *m, int block_size, int blocks_per_sm, int rare_batch, int inner_moves,
+                    int aggregate_atomics);
 
 /* Wall-clock budget of one transport launch in seconds (default 120).  A
  * launch that reaches it stops early and the run returns DIES_ETIMEOUT. */
@@ -259,7 +265,8 @@ int dies_batch_set_dust(dies_batch *b, const double *freq_hz, int n_freq, const 
                         const double *kappa_sca, const double *g);
 int dies_batch_set_sources(dies_batch *b, const double *J_ext, double L_point, const double *point_spectrum);
 int dies_batch_set_stream(dies_batch *b, void *cuda_stream);
-int dies_batch_set_launch(dies_batch *b, int block_size, int blocks_per_sm, int rare_batch, int inner_moves);
+int dies_batch_set_launch(dies_batch *b, int block_size, int blocks_per_sm, int rare_batch, int inner_moves,
+                          int aggregate_atomics);
 /* Graph mode for the batch, as dies_set_graph. */
 int dies_batch_set_graph(dies_batch *b, int enable);
 int dies_run_batch(dies_batch *b, uint64_t n_packages_per_model, uint64_t seed);

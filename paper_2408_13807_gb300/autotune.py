@@ -1,8 +1,8 @@
 """Launch-shape autotuner for the IRE transport kernel.
 
 For a cloud model (or a batch of models) it times short runs over a small
-grid of (block size, CTAs per SM, rare_batch, inner moves) and keeps the
-fastest.  Results
+grid of (block size, CTAs per SM, rare_batch, inner moves, aggregated
+absorption atomics) and keeps the fastest.  Results
 are cached per "config class" (precision, weighting, source kind, shell-count
 and optical-depth buckets) in ``tune_cache.json`` next to this file; a class
 missing from the cache is tuned on the spot (on the GPU, through the same C
@@ -20,11 +20,12 @@ from . import dies as D
 
 CACHE_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_cache.json")
 GRID_BLOCK = (128, 256)
-GRID_RARE = (12, 16, 20, 24)
-GRID_INNER = (16, 32, 64)
+GRID_RARE = (12, 16, 24)
+GRID_INNER = (32, 64)
+GRID_AGG = (0, 1)
 GRID_BPS = (0,)
-KEYS = ("block_size", "blocks_per_sm", "rare_batch", "inner_moves")
-DEFAULT = {"block_size": 256, "blocks_per_sm": 0, "rare_batch": 16, "inner_moves": 32}
+KEYS = ("block_size", "blocks_per_sm", "rare_batch", "inner_moves", "aggregate_atomics")
+DEFAULT = {"block_size": 256, "blocks_per_sm": 0, "rare_batch": 16, "inner_moves": 32, "aggregate_atomics": 0}
 
 _lock = threading.Lock()
 _cache: Optional[Dict[str, dict]] = None
@@ -81,15 +82,19 @@ def _cached(c: Dict[str, dict], key: str) -> Optional[dict]:
 
 def tune(cloud, precision: str = "mixed", n: int = 20_000_000, blocks: Iterable[int] = GRID_BLOCK,
          rare: Iterable[int] = GRID_RARE, bps: Iterable[int] = GRID_BPS,
-         inner: Iterable[int] = GRID_INNER) -> Tuple[dict, dict]:
+         inner: Iterable[int] = GRID_INNER, agg: Iterable[int] = GRID_AGG) -> Tuple[dict, dict]:
     """Time every shape of the grid on ``cloud``; return (best shape, timings)."""
     times = {}
+    if precision == "fp64":
+        agg = (0,)  # the FP64 form has no aggregated path
     for b in blocks:
         for k in bps:
             for r in rare:
                 for i in inner:
-                    shape = {"block_size": b, "blocks_per_sm": k, "rare_batch": r, "inner_moves": i}
-                    times[f"{b}/{k}/{r}/{i}"] = _time_model(cloud, precision, shape, n)
+                    for a in agg:
+                        shape = {"block_size": b, "blocks_per_sm": k, "rare_batch": r, "inner_moves": i,
+                                 "aggregate_atomics": a}
+                        times[f"{b}/{k}/{r}/{i}/{a}"] = _time_model(cloud, precision, shape, n)
     key = min(times, key=times.get)
     best = dict(zip(KEYS, (int(x) for x in key.split("/"))))
     return dict(best, ms=times[key], n=n), times
@@ -125,19 +130,20 @@ def best_batch_launch(clouds, allow_tuning: bool = True, n_per_model: int = 20_0
     for b in GRID_BLOCK:
         for r in GRID_RARE:
             for i in GRID_INNER:
-                bt = D.Batch(clouds, block_size=b, rare_batch=r, inner_moves=i)
-                try:
-                    bt.run(2_000, seed=3)
-                    best = float("inf")
-                    for rep in range(2):
-                        bt.run(n_per_model, seed=5 + rep)
-                        best = min(best, bt.stats()["transport_ms"])
-                    times[(b, r, i)] = best
-                finally:
-                    bt.close()
-    (b, r, i) = min(times, key=times.get)
-    rec = {"block_size": b, "blocks_per_sm": 0, "rare_batch": r, "inner_moves": i, "ms": times[(b, r, i)],
-           "n": n_per_model}
+                for a in GRID_AGG:
+                    bt = D.Batch(clouds, block_size=b, rare_batch=r, inner_moves=i, aggregate_atomics=a)
+                    try:
+                        bt.run(2_000, seed=3)
+                        best = float("inf")
+                        for rep in range(2):
+                            bt.run(n_per_model, seed=5 + rep)
+                            best = min(best, bt.stats()["transport_ms"])
+                        times[(b, r, i, a)] = best
+                    finally:
+                        bt.close()
+    (b, r, i, a) = min(times, key=times.get)
+    rec = {"block_size": b, "blocks_per_sm": 0, "rare_batch": r, "inner_moves": i, "aggregate_atomics": a,
+           "ms": times[(b, r, i, a)], "n": n_per_model}
     with _lock:
         _load()[key] = rec
         _save()

@@ -112,7 +112,7 @@ struct Problem {
   double T_min = 2.7, T_max = 1500.0;
   int n_tnodes = 1024;
   cudaStream_t stream = nullptr;
-  int block = 256, blocks_per_sm = 0, rare_batch = 16, inner = 32;
+  int block = 256, blocks_per_sm = 0, rare_batch = 16, inner = 32, agg = 0;
   double time_budget_s = 120.0;
   // device
   unsigned char *ws = nullptr;
@@ -376,6 +376,7 @@ struct Problem {
     P.r64 = (prec == PREC_MIXED && fp64_radius > 0.0);
     P.batch_min = rare_batch;
     P.inner = inner;
+    P.agg = agg;
     return P;
   }
 
@@ -822,21 +823,24 @@ int dies_set_stream(dies_model *m, void *s) {
   return DIES_OK;
 }
 
-static int set_launch(Problem &p, int block, int bps, int rare_batch, int inner) {
+static int set_launch(Problem &p, int block, int bps, int rare_batch, int inner, int agg) {
   if (block < 64 || block > 256 || block % 32) return fail(DIES_EINVAL, "block_size must be a multiple of 32 in [64, 256]");
   if (bps < 0) return fail(DIES_EINVAL, "blocks_per_sm must be >= 0");
   if (rare_batch < 1 || rare_batch > 32) return fail(DIES_EINVAL, "rare_batch must be in [1, 32]");
   if (inner < 1 || inner > 64) return fail(DIES_EINVAL, "inner_moves must be in [1, 64]");
+  if (agg != 0 && agg != 1) return fail(DIES_EINVAL, "aggregate_atomics must be 0 or 1");
   p.block = block;
   p.blocks_per_sm = bps;
   p.rare_batch = rare_batch;
   p.inner = inner;
+  p.agg = agg;
   return DIES_OK;
 }
 
-int dies_set_launch(dies_model *m, int block_size, int blocks_per_sm, int rare_batch, int inner_moves) {
+int dies_set_launch(dies_model *m, int block_size, int blocks_per_sm, int rare_batch, int inner_moves,
+                    int aggregate_atomics) {
   if (!m) return fail(DIES_EINVAL, "model is NULL");
-  return set_launch(m->p, block_size, blocks_per_sm, rare_batch, inner_moves);
+  return set_launch(m->p, block_size, blocks_per_sm, rare_batch, inner_moves, aggregate_atomics);
 }
 
 int dies_set_time_budget(dies_model *m, double seconds) {
@@ -1070,9 +1074,10 @@ int dies_batch_set_stream(dies_batch *b, void *s) {
   return DIES_OK;
 }
 
-int dies_batch_set_launch(dies_batch *b, int block_size, int blocks_per_sm, int rare_batch, int inner_moves) {
+int dies_batch_set_launch(dies_batch *b, int block_size, int blocks_per_sm, int rare_batch, int inner_moves,
+                          int aggregate_atomics) {
   if (!b) return fail(DIES_EINVAL, "batch is NULL");
-  return set_launch(b->p, block_size, blocks_per_sm, rare_batch, inner_moves);
+  return set_launch(b->p, block_size, blocks_per_sm, rare_batch, inner_moves, aggregate_atomics);
 }
 
 int dies_batch_set_graph(dies_batch *b, int enable) {

@@ -132,6 +132,7 @@ struct TransportParams {
   int batch_min;    // lanes that must wait for a rare event before a warp runs them together
   int inner;        // moves per lane between two warp-collective sections (>= 1)
   unsigned chunk;   // work items a warp takes from the counter at a time (multiple of 32, >= 32)
+  int agg;          // FP32 forms: warp-aggregated absorption atomics (lanes sharing a cell add once)
 };
 
 // Alias-table entries (FP32 forms): bits 6..31 the 26-bit acceptance

@@ -704,7 +704,29 @@ __device__ __forceinline__ void absorb(const TransportParams &P, Shared &S, cons
     const float dEf = L.w * L.eps;
     const float im = __ldg(P.inv_massf + gc);
     float eo;
-    if constexpr (PREC == PREC_MIXED) {
+    if (P.agg) {
+      // Lanes of this warp absorbing in the same cell add their energies
+      // with one atomic; each lane's E_old is the group's old value plus the
+      // energies of the group's lower lanes (the order of a serial run).
+      const unsigned am = __activemask();
+      const unsigned grp = __match_any_sync(am, gc);
+      const int lane = threadIdx.x & 31, lead = __ffs(grp) - 1;
+      const unsigned below = grp & ((1u << lane) - 1u);
+      float pre = 0.0f, tot = 0.0f;
+      for (unsigned rest = grp; rest != 0u; rest &= rest - 1u) {
+        const int j = __ffs(rest) - 1;
+        const float v = __shfl_sync(grp, dEf, j);
+        tot += v;
+        if (below & (1u << j)) pre += v;
+      }
+      float old = 0.0f;
+      if constexpr (PREC == PREC_MIXED) {
+        if (lane == lead) old = d2f_nonneg(atomicAdd(P.E + gc, f2d_nonneg(tot)));
+      } else {
+        if (lane == lead) old = __ldg(P.Eprev + gc) + atomicAdd(P.Ecur + gc, tot);
+      }
+      eo = (__shfl_sync(grp, old, lead) + pre) * im;
+    } else if constexpr (PREC == PREC_MIXED) {
       // FP64 accumulator; its old value gives e_old, the lookup is FP32
       eo = d2f_nonneg(atomicAdd(P.E + gc, f2d_nonneg(dEf))) * im;
     } else {

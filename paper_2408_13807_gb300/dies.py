@@ -108,7 +108,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "dies_set_precision": (i, [_vp, i, i, d]),
         "dies_set_tgrid": (i, [_vp, d, d, i]),
         "dies_set_stream": (i, [_vp, _vp]),
-        "dies_set_launch": (i, [_vp, i, i, i, i]),
+        "dies_set_launch": (i, [_vp, i, i, i, i, i]),
         "dies_set_time_budget": (i, [_vp, d]),
         "dies_set_graph": (i, [_vp, i]),
         "dies_batch_set_graph": (i, [_vp, i]),
@@ -127,7 +127,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "dies_batch_set_dust": (i, [_vp, _dp, i, _dp, _dp, _dp]),
         "dies_batch_set_sources": (i, [_vp, _dp, d, _dp]),
         "dies_batch_set_stream": (i, [_vp, _vp]),
-        "dies_batch_set_launch": (i, [_vp, i, i, i, i]),
+        "dies_batch_set_launch": (i, [_vp, i, i, i, i, i]),
         "dies_run_batch": (i, [_vp, u64, u64]),
         "dies_run_batch_async": (i, [_vp, u64, u64]),
         "dies_batch_get_temperatures": (i, [_vp, _dp, i]),
@@ -195,8 +195,10 @@ def dies_set_stream(h, stream_handle: int):
     return _check(load().dies_set_stream(h, _vp(stream_handle)))
 
 
-def dies_set_launch(h, block_size: int, blocks_per_sm: int = 0, rare_batch: int = 16, inner_moves: int = 32):
-    return _check(load().dies_set_launch(h, int(block_size), int(blocks_per_sm), int(rare_batch), int(inner_moves)))
+def dies_set_launch(h, block_size: int, blocks_per_sm: int = 0, rare_batch: int = 16, inner_moves: int = 32,
+                    aggregate_atomics: int = 0):
+    return _check(load().dies_set_launch(h, int(block_size), int(blocks_per_sm), int(rare_batch), int(inner_moves),
+                                         int(aggregate_atomics)))
 
 
 def dies_set_time_budget(h, seconds: float):
@@ -300,9 +302,10 @@ def dies_batch_set_stream(h, stream_handle: int):
     return _check(load().dies_batch_set_stream(h, _vp(stream_handle)))
 
 
-def dies_batch_set_launch(h, block_size: int, blocks_per_sm: int = 0, rare_batch: int = 16, inner_moves: int = 32):
+def dies_batch_set_launch(h, block_size: int, blocks_per_sm: int = 0, rare_batch: int = 16, inner_moves: int = 32,
+                          aggregate_atomics: int = 0):
     return _check(load().dies_batch_set_launch(h, int(block_size), int(blocks_per_sm), int(rare_batch),
-                                               int(inner_moves)))
+                                               int(inner_moves), int(aggregate_atomics)))
 
 
 def dies_run_batch(h, n_packages_per_model: int, seed: int):
@@ -371,7 +374,8 @@ class Model:
 
     def __init__(self, cloud, precision: str = "mixed", n_batches: int = 1, fp64_radius: float = 0.0,
                  tgrid=(2.7, 1500.0, 1024), torch_memory: bool = True, device: int = 0, block_size: int = 256,
-                 blocks_per_sm: int = 0, rare_batch: int = 16, inner_moves: int = 32, graph: bool = False):
+                 blocks_per_sm: int = 0, rare_batch: int = 16, inner_moves: int = 32, aggregate_atomics: int = 0,
+                 graph: bool = False):
         self.cloud = cloud
         self.h = dies_create_model(cloud.radii, cloud.rho, cloud.length_unit_cm)
         self.n_cells = cloud.n_cells
@@ -382,7 +386,7 @@ class Model:
         dies_set_weighting(self.h, cloud.k_bg, cloud.ffi)
         dies_set_precision(self.h, PREC[precision], n_batches, fp64_radius)
         dies_set_tgrid(self.h, *tgrid)
-        dies_set_launch(self.h, block_size, blocks_per_sm, rare_batch, inner_moves)
+        dies_set_launch(self.h, block_size, blocks_per_sm, rare_batch, inner_moves, aggregate_atomics)
         dies_set_graph(self.h, graph)
         if torch_memory:
             stream, self._ws = _torch_stream_and_workspace(dies_workspace_bytes(self.h), device)
@@ -432,7 +436,7 @@ class Batch:
     spectrum) in one persistent launch."""
 
     def __init__(self, clouds, block_size: int = 256, blocks_per_sm: int = 0, rare_batch: int = 16,
-                 inner_moves: int = 32, graph: bool = False):
+                 inner_moves: int = 32, aggregate_atomics: int = 0, graph: bool = False):
         c0 = clouds[0]
         n = np.array([c.n_cells for c in clouds], dtype=np.int32)
         self.offsets = np.concatenate([[0], np.cumsum(n)]).astype(np.int32)
@@ -447,7 +451,7 @@ class Batch:
         J = next((c.J_ext for c in clouds if c.J_ext is not None), None)
         pt = next((c for c in clouds if c.L_point > 0), None)
         dies_batch_set_sources(self.h, J, pt.L_point if pt else 0.0, pt.point_spec if pt else None)
-        dies_batch_set_launch(self.h, block_size, blocks_per_sm, rare_batch, inner_moves)
+        dies_batch_set_launch(self.h, block_size, blocks_per_sm, rare_batch, inner_moves, aggregate_atomics)
         dies_batch_set_graph(self.h, graph)
 
     def set_stream(self, stream_handle: int):

@@ -69,6 +69,7 @@ def test_create_and_set_validate_inputs(lib):
             lambda: D.dies_set_launch(h, 128, 0, 33),
             lambda: D.dies_set_launch(h, 128, 0, 8, 0),
             lambda: D.dies_set_launch(h, 128, 0, 8, 65),
+            lambda: D.dies_set_launch(h, 128, 0, 8, 8, 2),
             lambda: D._check(D.load().dies_set_graph(h, 2)),
             lambda: D.dies_set_time_budget(h, 0.0),
         ]

@@ -72,14 +72,15 @@ def test_frozen_pass_ragged_sizes(D, oracle):
         assert np.array_equal(ev, ref["n_events"]) and np.array_equal(hs, ref["hash"]), N
 
 
-@pytest.mark.parametrize("prec", ["mixed", "fp64"])
-def test_ire_config1_matches_oracle_16_seeds(D, oracle, prec):
+@pytest.mark.parametrize("prec,agg", [("mixed", 0), ("mixed", 1), ("fp64", 0)])
+def test_ire_config1_matches_oracle_16_seeds(D, oracle, prec, agg):
     cloud = W.config1()
     N = 1_000_000
-    Tg = np.array([D.Model(cloud, precision=prec).run(N, seed=s).temperatures() for s in range(16)])
+    m = D.Model(cloud, precision=prec, aggregate_atomics=agg)
+    Tg = np.array([m.run(N, seed=s).temperatures() for s in range(16)])
     To = np.array([r["T"] for r in oracle.run_seeds(cloud, N, range(100, 116))])
     r = assert_ensembles_agree(Tg, To, 0.01, min_gated=cloud.n_cells // 2)
-    print(f"{prec}: max rel (gated) {r['max_rel_gated']:.4f}, max z {r['max_z']:.2f}, gated {r['gated'].sum()}")
+    print(f"{prec} agg={agg}: max rel (gated) {r['max_rel_gated']:.4f}, max z {r['max_z']:.2f}, gated {r['gated'].sum()}")
 
 
 @pytest.mark.parametrize("prec", ["mixed", "fp64", "fp32"])
@@ -154,10 +155,12 @@ def test_single_shell_and_single_package(D, oracle):
     assert st["injected"] == 1 and st["escaped"] == 1
 
 
-def test_fp32_form_matches_oracle_with_batches(D, oracle):
+@pytest.mark.parametrize("agg", [0, 1])
+def test_fp32_form_matches_oracle_with_batches(D, oracle, agg):
     cloud = W.config1()
     N = 1_000_000
-    Tg = np.array([D.Model(cloud, precision="fp32", n_batches=50).run(N, seed=s).temperatures() for s in range(16)])
+    m = D.Model(cloud, precision="fp32", n_batches=50, aggregate_atomics=agg)
+    Tg = np.array([m.run(N, seed=s).temperatures() for s in range(16)])
     To = np.array([r["T"] for r in oracle.run_seeds(cloud, N, range(200, 216))])
     assert_ensembles_agree(Tg, To, 0.01, min_gated=cloud.n_cells // 2)
 

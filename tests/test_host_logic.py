@@ -57,12 +57,13 @@ def test_autotune_uses_cache_without_gpu(tmp_path, monkeypatch):
     key = autotune.config_class(m, "mixed")
     old = autotune.config_class(W.config3(), "mixed")
     cache.write_text(json.dumps({key: {"block_size": 128, "blocks_per_sm": 0, "rare_batch": 12, "inner_moves": 16,
-                                       "ms": 1.0},
+                                       "aggregate_atomics": 1, "ms": 1.0},
                                  old: {"block_size": 128, "blocks_per_sm": 0, "rare_batch": 12, "ms": 1.0}}))
     monkeypatch.setattr(autotune, "CACHE_PATH", str(cache))
     monkeypatch.setattr(autotune, "_cache", None)
     assert autotune.best_launch(m, "mixed", allow_tuning=False) == {"block_size": 128, "blocks_per_sm": 0,
-                                                                    "rare_batch": 12, "inner_moves": 16}
+                                                                    "rare_batch": 12, "inner_moves": 16,
+                                                                    "aggregate_atomics": 1}
     # an entry without every knob counts as missing
     assert autotune.best_launch(W.config3(), "mixed", allow_tuning=False) == autotune.DEFAULT
     assert autotune.best_launch(W.config5_internal(), "mixed", allow_tuning=False) == autotune.DEFAULT
