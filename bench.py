@@ -143,6 +143,16 @@ def max_over_ranks(dist, x: float, device=None) -> float:
     return float(t.item())
 
 
+def job_value(world: int, packages_per_step: int, steps: int, total_ms: float) -> float:
+    """Whole-job packages/s: every rank's packages over the slowest rank's time."""
+    return world * packages_per_step * steps / (total_ms * 1e-3)
+
+
+def replica_seed_base(rank: int) -> int:
+    """Each rank is an independent replica with its own seeds."""
+    return 1_000_000 * rank
+
+
 # ---------------------------------------------------------------- oracle
 def oracle_rate(clouds, seconds_target: float, seed0: int = 1000):
     """Packages/s of the serial FP64 oracle on a bounded sample of the same
@@ -341,7 +351,7 @@ def run_ours(args):
         shapes = [autotune.best_launch(c, "mixed") for c in clouds]  # tuned here if not cached (untimed)
     models = [D.Model(c, precision="mixed", fp64_radius=args.fp64_radius, **sh) for c, sh in zip(clouds, shapes)]
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    seed_base = 1_000_000 * rank
+    seed_base = replica_seed_base(rank)
 
     def step(seed):
         for i, m in enumerate(models):
@@ -380,7 +390,7 @@ def run_ours(args):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = max_over_ranks(dist, sum(step_ms), dev)
     pk_step = len(models) * n
-    value = world * pk_step * args.steps / (total_ms * 1e-3)
+    value = job_value(world, pk_step, args.steps, total_ms)
 
     # ---- end-to-end through the public API, host arrays in and out
     e2e_dts, h2d, d2h = [], 0, 0
