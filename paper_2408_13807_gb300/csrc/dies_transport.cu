@@ -292,19 +292,22 @@ __device__ __forceinline__ void boundary(const TransportParams &P, const Lane<ty
     rho = __ldg(P.rhoe + gi);
     const float d_in = (G.x - L.p2) + G.y;
     const bool inward = (L.s < 0.0f) & (d_in > 0.0f);
-    const float d = inward ? d_in : (G.z - L.p2) + G.w;
+    // sqrt from the hardware reciprocal square root (relative error ~1e-7),
+    // signed on the way; a non-positive d (rounding at a tangent) counts as 1e-36
+    const float d = fmaxf(inward ? d_in : (G.z - L.p2) + G.w, 1.0e-36f);
     next = inward ? c - 1 : c + 1;
-    // sqrt from the hardware reciprocal square root (relative error ~1e-7)
-    float sq = (d > 0.0f) ? d * rsqrtf(d) : 0.0f;
+    sb = (inward ? -d : d) * rsqrtf(d);
     if constexpr ((OPT & OPT_R64) != 0) {
       if ((unsigned)c < (unsigned)L.n64) {
         // optional FP64 crossing distance in the innermost shells
         const double t2 = __ldg(P.r2d + L.gbase - 1 + c + (inward ? 0 : 1));
-        sq = (float)sqrt(fmax(t2 - (double)L.p2, 0.0));
+        const float sq = (float)sqrt(fmax(t2 - (double)L.p2, 0.0));
+        sb = inward ? -sq : sq;
       }
     }
-    sb = inward ? -sq : sq;
-    l = fmaxf(sb - L.s, 0.0f);
+    // sb - s >= 0 up to rounding; a step negative by rounding is harmless
+    // (the column decreases by a rounding amount, the crossing stands)
+    l = sb - L.s;
   }
 }
 
