@@ -27,6 +27,19 @@
  *     2 k_bg mu^(2-1/k_bg) (Sect. 2.2.1, Eq. 5);
  *   - forced first interaction (Sect. 2.2.2, Eqs. 9-12), with the extinction
  *     optical depth (absorption + scattering) as the forced variable;
+ *   - direction weighting of re-emission (Sect. 2.2.1, Eq. 6): the new
+ *     direction from a Henyey-Greenstein function of parameter g_E about the
+ *     reference direction (towards the centre for packages of the external
+ *     field, away from it for the point source), weight = isotropic pdf /
+ *     HG pdf;
+ *   - direction weighting of scattering (Sect. 2.2.1, Eq. 7): the new
+ *     direction from an HG function of parameter g_S about the reference
+ *     direction, weight = dust HG pdf of the scattering angle / HG(g_S) pdf
+ *     of the angle to the reference direction;
+ *   - free-path weighting (Sect. 2.2.3, Eq. 8): tau = -ln(u) / k with weight
+ *     e^(tau (k - 1)) / k, separately for absorption (k_A) and scattering
+ *     (k_S); optionally k_A per cell, linear in log density from k_A_lo at the
+ *     lowest cell density to k_A_hi at the highest;
  *   - the weight floor: a package whose weight has fallen ten orders of
  *     magnitude is terminated (Sect. 2.2.1).
  *
@@ -47,7 +60,9 @@
  * {u_tauS, u_tauA}; forced first interaction {u_int, u_type}; scattering
  * {u_mu_s, u_phi}, {u_tauS, u_tauA}; absorption {u_e, u_nu}, {u_mu, u_phi},
  * {u_tauS, u_tauA}.  u_e is reserved for table-based temperature updates and
- * is drawn but unused here.
+ * is drawn but unused here.  The weighted directions use the same blocks:
+ * {u_mu, u_phi} give the cosine to the reference direction and the azimuth
+ * about it.
  */
 #include <math.h>
 #include <stdint.h>
@@ -86,6 +101,12 @@ typedef struct {
   const double *point_spec; /* n_freq L_nu shape, or NULL */
   double k_bg;              /* 0.5 = unweighted */
   int32_t ffi;              /* forced first interaction */
+  double g_E;               /* re-emission direction weighting (Eq. 6); 0 = off */
+  int32_t scat_w;           /* scattering direction weighting (Eq. 7) on */
+  double g_S;               /* its HG parameter */
+  double k_A, k_S;          /* free-path weighting (Eq. 8); 1 = off */
+  int32_t kA_rho;           /* density-dependent k_A */
+  double kA_lo, kA_hi;      /* k_A at the lowest and at the highest cell density */
   double T_min, T_max;      /* reporting range of the temperatures */
   uint32_t model_id;
   uint64_t max_events;      /* per package; 0 = 1e8 */
@@ -269,6 +290,20 @@ double orc_hg_mu(double g, double u)
   return mu;
 }
 
+/* Henyey-Greenstein density of the cosine mu without the common factor
+ * 1/2: (1 - g^2) / (1 + g^2 - 2 g mu)^(3/2) (Eq. 6); 1 for g = 0. */
+double orc_hg_pdf2(double g, double mu)
+{
+  double q = 1.0 + g * g - 2.0 * g * mu;
+  return (1.0 - g * g) / (q * sqrt(q));
+}
+
+/* Free-path weight of Eq. 8 for a path tau drawn from k e^(-k tau). */
+double orc_path_weight(double k, double tau)
+{
+  return exp(tau * (k - 1.0)) / k;
+}
+
 /* smallest k with cdf[k] >= u (cdf[F-1] == 1) */
 static int sample_cdf(int F, const double *cdf, double u)
 {
@@ -337,6 +372,8 @@ typedef struct {
   double eps[2];           /* package energy per source, erg/s */
   int active[2];
   double *mass;            /* n: 4 pi rho V L_u^2, so that E = mass * Lambda(T) */
+  double *kA;              /* n: absorption free-path weighting factor per cell */
+  double kA_void;          /* ... in the central void (and empty cells) */
   double *E;               /* n: absorbed energy */
   double *T;               /* n: current temperature */
   double *Bcur;            /* n*F: kabs_k B_k(T_cur) dnu_k for the cell */
@@ -428,26 +465,63 @@ static void lose(orc_ctx *C, orc_pkg *p, int s, int why)
   C->st[ST_E_LOST] += p->w * C->eps[s];
 }
 
+/* Reference direction of the weighted direction distributions (Sect.
+ * 2.2.1): towards the centre for packages of the external field (s = 0),
+ * away from it for the point source (s = 1). */
+static void reference_direction(const orc_pkg *p, int s, double *ref)
+{
+  double xr = sqrt(dot3(p->x, p->x));
+  double rhat[3] = {0.0, 0.0, 1.0};
+  if (xr > 0.0)
+    for (int i = 0; i < 3; ++i) rhat[i] = p->x[i] / xr;
+  for (int i = 0; i < 3; ++i) ref[i] = (s == 0) ? -rhat[i] : rhat[i];
+}
+
+/* Both free paths (Eq. 1) from one block, each weighted by Eq. 8 when its k
+ * differs from 1; k_A is that of the package's current cell. */
+static void draw_paths(orc_ctx *C, orc_pkg *p, orc_stream *rs)
+{
+  double u1, u2;
+  draw2(rs, &u1, &u2);
+  double kS = C->M->k_S;
+  double kA = (p->cell >= 0 && p->cell < C->n) ? C->kA[p->cell] : C->kA_void;
+  p->tauS = -log(u1) / kS;
+  p->tauA = -log(u2) / kA;
+  if (kS != 1.0) p->w *= orc_path_weight(kS, p->tauS);
+  if (kA != 1.0) p->w *= orc_path_weight(kA, p->tauA);
+}
+
 /* Scattering (Sect. 2.1): new direction from the HG phase function of the
  * current frequency, azimuth measured from the plane of the radius vector and
- * the old direction; both free paths redrawn (Eq. 1). */
-static void do_scatter(orc_ctx *C, orc_pkg *p, orc_stream *rs)
+ * the old direction; with scattering weighting (Eq. 7) from an HG function
+ * of g_S about the reference direction instead, azimuth from the plane of
+ * the reference and the old direction.  Both free paths redrawn (Eq. 1). */
+static void do_scatter(orc_ctx *C, orc_pkg *p, orc_stream *rs, int s)
 {
-  double u_mu, u_phi, u1, u2;
+  double u_mu, u_phi;
   draw2(rs, &u_mu, &u_phi);
-  double mu_s = orc_hg_mu(C->M->g[p->f], u_mu);
   double phi = 2.0 * ORC_PI * u_phi;
-  double st = sqrt(fmax(0.0, 1.0 - mu_s * mu_s));
-  double e1[3], e2[3];
-  double xr = sqrt(dot3(p->x, p->x));
-  frame(p->d, xr > 0.0 ? p->x : NULL, e1, e2);
-  double dn[3];
-  for (int i = 0; i < 3; ++i) dn[i] = mu_s * p->d[i] + st * (cos(phi) * e1[i] + sin(phi) * e2[i]);
-  normalise3(dn);
+  double e1[3], e2[3], dn[3];
+  if (C->M->scat_w) {
+    double ref[3];
+    reference_direction(p, s, ref);
+    double mr = orc_hg_mu(C->M->g_S, u_mu);
+    double sr = sqrt(fmax(0.0, 1.0 - mr * mr));
+    frame(ref, p->d, e1, e2);
+    for (int i = 0; i < 3; ++i) dn[i] = mr * ref[i] + sr * (cos(phi) * e1[i] + sin(phi) * e2[i]);
+    normalise3(dn);
+    double mu_s = dot3(p->d, dn);
+    p->w *= orc_hg_pdf2(C->M->g[p->f], mu_s) / orc_hg_pdf2(C->M->g_S, mr);
+  } else {
+    double mu_s = orc_hg_mu(C->M->g[p->f], u_mu);
+    double st = sqrt(fmax(0.0, 1.0 - mu_s * mu_s));
+    double xr = sqrt(dot3(p->x, p->x));
+    frame(p->d, xr > 0.0 ? p->x : NULL, e1, e2);
+    for (int i = 0; i < 3; ++i) dn[i] = mu_s * p->d[i] + st * (cos(phi) * e1[i] + sin(phi) * e2[i]);
+    normalise3(dn);
+  }
   memcpy(p->d, dn, sizeof dn);
-  draw2(rs, &u1, &u2);
-  p->tauS = -log(u1);
-  p->tauA = -log(u2);
+  draw_paths(C, p, rs);
   p->nev[0] += 1;
   C->st[ST_SCATTER] += 1.0;
   record(p, ORC_EV_SCATTER, p->cell, p->f);
@@ -467,7 +541,7 @@ static int do_absorb(orc_ctx *C, orc_pkg *p, orc_stream *rs, int s)
     record(p, ORC_EV_ABSORB, c, p->f);
     return 0;
   }
-  double u_e, u_nu, u_mu, u_phi, u1, u2;
+  double u_e, u_nu, u_mu, u_phi;
   draw2(rs, &u_e, &u_nu);
   (void)u_e;
   double E_new = C->E[c] + dE;
@@ -499,21 +573,32 @@ static int do_absorb(orc_ctx *C, orc_pkg *p, orc_stream *rs, int s)
     fn = sample_cdf(F, C->cdf_frozen + (size_t)c * F, u_nu);
   }
   p->f = fn;
-  /* isotropic new direction: mu uniform in [-1,1] about the radius vector */
   draw2(rs, &u_mu, &u_phi);
-  double mu = 2.0 * u_mu - 1.0, phi = 2.0 * ORC_PI * u_phi;
-  double st = sqrt(fmax(0.0, 1.0 - mu * mu));
-  double rhat[3] = {0.0, 0.0, 1.0};
-  double xr = sqrt(dot3(p->x, p->x));
-  if (xr > 0.0)
-    for (int i = 0; i < 3; ++i) rhat[i] = p->x[i] / xr;
+  double phi = 2.0 * ORC_PI * u_phi;
   double e1[3], e2[3];
-  frame(rhat, NULL, e1, e2);
-  for (int i = 0; i < 3; ++i) p->d[i] = mu * rhat[i] + st * (cos(phi) * e1[i] + sin(phi) * e2[i]);
+  if (M->g_E != 0.0) {
+    /* weighted re-emission (Eq. 6): HG(g_E) about the reference direction,
+     * weight = isotropic density / HG density */
+    double ref[3];
+    reference_direction(p, s, ref);
+    double mr = orc_hg_mu(M->g_E, u_mu);
+    double sr = sqrt(fmax(0.0, 1.0 - mr * mr));
+    frame(ref, NULL, e1, e2);
+    for (int i = 0; i < 3; ++i) p->d[i] = mr * ref[i] + sr * (cos(phi) * e1[i] + sin(phi) * e2[i]);
+    p->w /= orc_hg_pdf2(M->g_E, mr);
+  } else {
+    /* isotropic new direction: mu uniform in [-1,1] about the radius vector */
+    double mu = 2.0 * u_mu - 1.0;
+    double st = sqrt(fmax(0.0, 1.0 - mu * mu));
+    double rhat[3] = {0.0, 0.0, 1.0};
+    double xr = sqrt(dot3(p->x, p->x));
+    if (xr > 0.0)
+      for (int i = 0; i < 3; ++i) rhat[i] = p->x[i] / xr;
+    frame(rhat, NULL, e1, e2);
+    for (int i = 0; i < 3; ++i) p->d[i] = mu * rhat[i] + st * (cos(phi) * e1[i] + sin(phi) * e2[i]);
+  }
   normalise3(p->d);
-  draw2(rs, &u1, &u2);
-  p->tauS = -log(u1);
-  p->tauA = -log(u2);
+  draw_paths(C, p, rs);
   record(p, ORC_EV_ABSORB, c, fn);
   return 1;
 }
@@ -560,12 +645,21 @@ static void simulate(orc_ctx *C, int s, uint64_t pkg, uint64_t seed, uint32_t *n
   p.w = 1.0;
 
   /* ---- injection (Sect. 2.1, Eqs. 1-3; weighting Eq. 5) */
-  double u_f, u_mu, u1, u2;
+  double u_f, u_mu;
   draw2(&rs, &u_f, &u_mu);
   p.f = sample_cdf(C->F, C->cdf_src[s], u_f);
-  draw2(&rs, &u1, &u2);
-  p.tauS = -log(u1);
-  p.tauA = -log(u2);
+  p.cell = (s == 0) ? C->n - 1 : ((M->radii[0] > 0.0) ? -1 : 0);
+  double w_path = 1.0;  /* free-path weight of the first flight (Eq. 8) */
+  if (M->ffi) {
+    double u1, u2;  /* the forced flight replaces these paths */
+    draw2(&rs, &u1, &u2);
+    p.tauS = -log(u1);
+    p.tauA = -log(u2);
+  } else {
+    draw_paths(C, &p, &rs);
+    w_path = p.w;
+    p.w = 1.0;
+  }
   double mu;
   if (s == 0) {
     if (M->k_bg == 0.5) {
@@ -575,17 +669,17 @@ static void simulate(orc_ctx *C, int s, uint64_t pkg, uint64_t seed, uint32_t *n
       p.w = 2.0 * M->k_bg * pow(mu, 2.0 - 1.0 / M->k_bg);
     }
     p.x[0] = 0.0; p.x[1] = 0.0; p.x[2] = -C->R;
-    p.cell = C->n - 1;
   } else {
     mu = 2.0 * u_mu - 1.0;
     p.x[0] = p.x[1] = p.x[2] = 0.0;
-    p.cell = (M->radii[0] > 0.0) ? -1 : 0;
   }
   p.d[0] = sqrt(fmax(0.0, 1.0 - mu * mu));
   p.d[1] = 0.0;
   p.d[2] = mu;
+  /* the injected energy is the source's: before the free-path weight */
   C->st[ST_INJECTED] += 1.0;
   C->st[ST_E_INJECTED] += p.w * C->eps[s];
+  p.w *= w_path;
   record(&p, ORC_EV_INJECT, p.cell, p.f);
 
   int alive = 1;
@@ -627,7 +721,11 @@ static void simulate(orc_ctx *C, int s, uint64_t pkg, uint64_t seed, uint32_t *n
           move(&p, li);
           p.events += 1;
           if (u_type * ke < ka) alive = do_absorb(C, &p, &rs, s);
-          else do_scatter(C, &p, &rs);
+          else do_scatter(C, &p, &rs, s);
+          if (alive && p.w < 1e-10) {
+            lose(C, &p, s, ST_KILL_WEIGHT);
+            alive = 0;
+          }
           break;
         }
         acc += ke * l;
@@ -656,7 +754,7 @@ static void simulate(orc_ctx *C, int s, uint64_t pkg, uint64_t seed, uint32_t *n
       /* tau_S ran out first; with no absorption in the cell (ka = 0, only
        * reachable when tau_A is exactly 0) the interaction is a scattering */
       move(&p, p.tauS / ks);
-      do_scatter(C, &p, &rs);
+      do_scatter(C, &p, &rs, s);
     } else {
       move(&p, p.tauA / ka);
       if (!do_absorb(C, &p, &rs, s)) break;
@@ -687,6 +785,9 @@ int orc_validate(const orc_model *M)
   if (!M->J_ext && !(M->L_point > 0.0)) return -6;
   if (M->L_point > 0.0 && !M->point_spec) return -6;
   if (!(M->k_bg > 0.0 && M->k_bg <= 1.0)) return -7;
+  if (!(fabs(M->g_E) < 1.0) || !(fabs(M->g_S) < 1.0)) return -7;
+  if (!(M->k_A > 0.0 && isfinite(M->k_A)) || !(M->k_S > 0.0 && isfinite(M->k_S))) return -7;
+  if (M->kA_rho && !(M->kA_lo > 0.0 && isfinite(M->kA_lo) && M->kA_hi > 0.0 && isfinite(M->kA_hi))) return -7;
   if (!(M->length_unit_cm > 0.0)) return -8;
   return 0;
 }
@@ -720,6 +821,36 @@ int orc_cell_mass(const orc_model *M, double *mass)
     double V = 4.0 * ORC_PI / 3.0 * (b - a) * (b * b + a * b + a * a);
     mass[i] = 4.0 * ORC_PI * M->rho[i] * V * Lu2;
   }
+  return 0;
+}
+
+/* Absorption free-path weighting factor k_A per cell (Sect. 2.2.3): the
+ * constant k_A, or with density dependence linear in log density from k_A_lo
+ * at the lowest positive cell density to k_A_hi at the highest; empty cells
+ * and the central void take k_A_lo. */
+int orc_kA_cells(const orc_model *M, double *kA, double *kA_void)
+{
+  int n = M->n_cells;
+  if (!M->kA_rho) {
+    for (int i = 0; i < n; ++i) kA[i] = M->k_A;
+    *kA_void = M->k_A;
+    return 0;
+  }
+  double lmin = 0.0, lmax = 0.0;
+  int any = 0;
+  for (int i = 0; i < n; ++i) {
+    if (!(M->rho[i] > 0.0)) continue;
+    double l = log(M->rho[i]);
+    if (!any || l < lmin) lmin = l;
+    if (!any || l > lmax) lmax = l;
+    any = 1;
+  }
+  for (int i = 0; i < n; ++i) {
+    if (!(M->rho[i] > 0.0)) kA[i] = M->kA_lo;
+    else if (!(lmax > lmin)) kA[i] = M->kA_hi;
+    else kA[i] = M->kA_hi + (M->kA_lo - M->kA_hi) * (lmax - log(M->rho[i])) / (lmax - lmin);
+  }
+  *kA_void = M->kA_lo;
   return 0;
 }
 
@@ -776,10 +907,12 @@ int orc_run(const orc_model *M, uint64_t N, uint64_t seed, int mode, const doubl
   C.T = (double *)calloc((size_t)n, sizeof(double));
   C.Bcur = (double *)calloc((size_t)n * F, sizeof(double));
   C.cdf_frozen = (double *)calloc((size_t)n * F, sizeof(double));
-  if (!C.mass || !C.E || !C.T || !C.Bcur || !C.cdf_frozen) {
-    free(C.mass); free(C.E); free(C.T); free(C.Bcur); free(C.cdf_frozen);
+  C.kA = (double *)calloc((size_t)n, sizeof(double));
+  if (!C.mass || !C.E || !C.T || !C.Bcur || !C.cdf_frozen || !C.kA) {
+    free(C.mass); free(C.E); free(C.T); free(C.Bcur); free(C.cdf_frozen); free(C.kA);
     return -10;
   }
+  orc_kA_cells(M, C.kA, &C.kA_void);
   orc_cell_mass(M, C.mass);
   C.Lmax = orc_emission(F, M->freq, C.dnu, M->kabs, M->T_max);
   C.L_lo = orc_emission(F, M->freq, C.dnu, M->kabs, ORC_T_LO);
@@ -812,7 +945,7 @@ int orc_run(const orc_model *M, uint64_t N, uint64_t seed, int mode, const doubl
       T_out[i] = T_frozen[i];
     }
   }
-  free(C.mass); free(C.E); free(C.T); free(C.Bcur); free(C.cdf_frozen);
+  free(C.mass); free(C.E); free(C.T); free(C.Bcur); free(C.cdf_frozen); free(C.kA);
   return 0;
 }
 

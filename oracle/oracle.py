@@ -49,6 +49,9 @@ class _Model(ctypes.Structure):
         ("freq", _dp), ("kabs", _dp), ("ksca", _dp), ("g", _dp),
         ("J_ext", _dp), ("L_point", ctypes.c_double), ("point_spec", _dp),
         ("k_bg", ctypes.c_double), ("ffi", ctypes.c_int32),
+        ("g_E", ctypes.c_double), ("scat_w", ctypes.c_int32), ("g_S", ctypes.c_double),
+        ("k_A", ctypes.c_double), ("k_S", ctypes.c_double),
+        ("kA_rho", ctypes.c_int32), ("kA_lo", ctypes.c_double), ("kA_hi", ctypes.c_double),
         ("T_min", ctypes.c_double), ("T_max", ctypes.c_double),
         ("model_id", ctypes.c_uint32), ("max_events", ctypes.c_uint64),
     ]
@@ -76,6 +79,11 @@ def lib():
         L.orc_temperature.restype = ctypes.c_double
         L.orc_hg_mu.argtypes = [ctypes.c_double, ctypes.c_double]
         L.orc_hg_mu.restype = ctypes.c_double
+        L.orc_hg_pdf2.argtypes = [ctypes.c_double, ctypes.c_double]
+        L.orc_hg_pdf2.restype = ctypes.c_double
+        L.orc_path_weight.argtypes = [ctypes.c_double, ctypes.c_double]
+        L.orc_path_weight.restype = ctypes.c_double
+        L.orc_kA_cells.argtypes = [_P(_Model), _dp, _dp]
         L.orc_validate.argtypes = [_P(_Model)]
         L.orc_source_luminosity.argtypes = [_P(_Model), _dp]
         L.orc_cell_mass.argtypes = [_P(_Model), _dp]
@@ -107,7 +115,12 @@ class _Bound:
             radii=_ptr(a["radii"]), rho=_ptr(a["rho"]), length_unit_cm=float(m.length_unit_cm),
             freq=_ptr(a["freq"]), kabs=_ptr(a["kabs"]), ksca=_ptr(a["ksca"]), g=_ptr(a["g"]),
             J_ext=_ptr(a["J_ext"]), L_point=float(m.L_point), point_spec=_ptr(a["point_spec"]),
-            k_bg=float(m.k_bg), ffi=int(bool(m.ffi)), T_min=float(T_min), T_max=float(T_max),
+            k_bg=float(m.k_bg), ffi=int(bool(m.ffi)),
+            g_E=float(getattr(m, "g_E", 0.0)), scat_w=int(bool(getattr(m, "scat_w", False))),
+            g_S=float(getattr(m, "g_S", 0.0)), k_A=float(getattr(m, "k_A", 1.0)),
+            k_S=float(getattr(m, "k_S", 1.0)), kA_rho=int(bool(getattr(m, "kA_rho", False))),
+            kA_lo=float(getattr(m, "kA_lo", 3.0)), kA_hi=float(getattr(m, "kA_hi", 1.0)),
+            T_min=float(T_min), T_max=float(T_max),
             model_id=int(model_id), max_events=int(max_events))
 
 
@@ -118,6 +131,25 @@ def philox(ctr, key) -> np.ndarray:
     o = np.zeros(4, dtype=np.uint32)
     lib().orc_philox4x32_10(_ptr(c, ctypes.c_uint32), _ptr(k, ctypes.c_uint32), _ptr(o, ctypes.c_uint32))
     return o
+
+
+def hg_pdf2(g: float, mu: float) -> float:
+    """(1 - g^2) / (1 + g^2 - 2 g mu)^(3/2): twice the HG density of mu (Eq. 6)."""
+    return lib().orc_hg_pdf2(float(g), float(mu))
+
+
+def path_weight(k: float, tau: float) -> float:
+    """Eq. 8: weight of a free path tau drawn from k e^(-k tau)."""
+    return lib().orc_path_weight(float(k), float(tau))
+
+
+def kA_cells(m) -> tuple:
+    """Per-cell absorption free-path factor k_A and its value in the void."""
+    b = _Bound(m)
+    out = np.zeros(b.s.n_cells)
+    v = ctypes.c_double(0.0)
+    lib().orc_kA_cells(ctypes.byref(b.s), _ptr(out), ctypes.byref(v))
+    return out, v.value
 
 
 def u01(a: int, b: int) -> float:

@@ -46,6 +46,12 @@ class CloudModel:
     J_ext       float64[F] isotropic external intensity (erg/s/cm^2/Hz/sr) or None.
     L_point     central point-source luminosity in erg/s (0 = none).
     point_spec  float64[F] shape of the point-source L_nu (any scale) or None.
+    k_bg        background-direction weighting mu = u^k_bg (0.5 = none).
+    ffi         forced first interaction.
+    g_E         re-emission direction weighting, HG parameter (0 = none).
+    scat_w      scattering direction weighting on, with HG parameter g_S.
+    k_A, k_S    free-path weighting factors (1 = none); kA_rho: k_A per cell,
+                linear in log density from kA_lo (lowest) to kA_hi (highest).
     """
 
     name: str
@@ -61,6 +67,14 @@ class CloudModel:
     point_spec: Optional[np.ndarray] = None
     k_bg: float = 0.5
     ffi: bool = False
+    g_E: float = 0.0
+    scat_w: bool = False
+    g_S: float = 0.0
+    k_A: float = 1.0
+    k_S: float = 1.0
+    kA_rho: bool = False
+    kA_lo: float = 3.0
+    kA_hi: float = 1.0
 
     @property
     def n_cells(self) -> int:

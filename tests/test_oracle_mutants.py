@@ -39,14 +39,31 @@ MUTANTS = {
     # Eq. 12 weight not applied
     "ffi_no_weight": ("    p.w *= q;\n", "\n", "test_weighted_injection_is_unbiased", {"k_bg": 0.5, "ffi": True}),
     # re-emission direction not isotropic
-    "reemit_not_isotropic": ("double mu = 2.0 * u_mu - 1.0, phi = 2.0 * ORC_PI * u_phi;",
-                             "double mu = u_mu, phi = 2.0 * ORC_PI * u_phi;",
+    "reemit_not_isotropic": ("double mu = 2.0 * u_mu - 1.0;",
+                             "double mu = u_mu;",
                              "test_absorb_reemit_grey_isotropic_invariant", {}),
     # cell emission normalisation without the 4 pi
     "mass_no_4pi": ("mass[i] = 4.0 * ORC_PI * M->rho[i] * V * Lu2;", "mass[i] = M->rho[i] * V * Lu2;",
                     "test_optically_thin_temperature", {}),
     # Philox with one Weyl increment wrong
     "philox_key_bump": ("k1 += 0xBB67AE85u;", "k1 += 0xBB67AE84u;", "test_philox_known_answer_vectors", {}),
+    # Eq. 7 weight inverted (sampling density over the dust density)
+    "scatter_weight_inverted": ("p->w *= orc_hg_pdf2(C->M->g[p->f], mu_s) / orc_hg_pdf2(C->M->g_S, mr);",
+                                "p->w *= orc_hg_pdf2(C->M->g_S, mr) / orc_hg_pdf2(C->M->g[p->f], mu_s);",
+                                "test_scattering_weighting_conserves_energy_on_average", {"g": 0.6, "g_S": -0.3}),
+    # Eq. 6 weight missing
+    "reemit_weight_missing": ("    p->w /= orc_hg_pdf2(M->g_E, mr);\n", "\n",
+                              "test_reemission_weighting_is_unbiased", {"g_E": 0.5}),
+    # Eq. 8 with the exponent's sign flipped
+    "path_weight_sign": ("return exp(tau * (k - 1.0)) / k;", "return exp(tau * (1.0 - k)) / k;",
+                         "test_weight_functions_have_unit_mean", {}),
+    # Eq. 8 weight not applied to the absorption path
+    "path_weight_unused": ("  if (kA != 1.0) p->w *= orc_path_weight(kA, p->tauA);\n", "\n",
+                           "test_free_path_weighting_is_unbiased", {"kw": {"k_A": 2.5}}),
+    # density-dependent k_A running the wrong way
+    "kA_rho_reversed": ("kA[i] = M->kA_hi + (M->kA_lo - M->kA_hi) * (lmax - log(M->rho[i])) / (lmax - lmin);",
+                        "kA[i] = M->kA_lo + (M->kA_hi - M->kA_lo) * (lmax - log(M->rho[i])) / (lmax - lmin);",
+                        "test_density_dependent_kA_is_log_linear", {}),
 }
 
 

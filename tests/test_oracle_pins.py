@@ -297,3 +297,103 @@ def test_absorb_reemit_grey_isotropic_invariant(oracle):
     n_abs = r["n_events"][:, 1].astype(np.float64)
     expect = CF.pure_scatterer_mean_events(m.radii, m.kabs[0] * m.rho)
     assert abs(n_abs.mean() - expect) < 4.5 * n_abs.std() / np.sqrt(N)
+
+
+# ------------------------------------------- weighted sampling (Sect. 2.2)
+def test_weight_functions_have_unit_mean(oracle):
+    """Quadrature: the HG density of Eq. 6 integrates to one; the weights of
+    Eqs. 6 (re-emission), 7 (scattering, for the dust HG of any g) and 8
+    (free paths) average to one under the distributions they are drawn from."""
+    x, wq = np.polynomial.legendre.leggauss(400)
+    for g in (-0.5, 0.0, 0.3, 0.8):
+        pdf = np.array([oracle.hg_pdf2(g, mu) for mu in x]) / 2.0
+        assert np.sum(wq * pdf) == pytest.approx(1.0, rel=1e-6)
+        # re-emission: E_HG[1 / pdf2] = integral of 1/2 = 1
+        assert np.sum(wq * pdf / (2.0 * pdf)) == pytest.approx(1.0, rel=1e-12)
+    for k in (0.4, 1.0, 2.5):
+        t = np.linspace(0.0, 80.0 / k, 400_001)
+        f = np.array([oracle.path_weight(k, tt) for tt in t[::1000]])
+        assert f[0] == pytest.approx(1.0 / k)
+        # closed form of the integral of W(tau) k e^(-k tau) over tau: e^-tau integrates to 1
+        dens = k * np.exp(-k * t) * np.exp(t * (k - 1.0)) / k
+        assert np.trapezoid(dens, t) == pytest.approx(1.0, rel=1e-6)
+        assert oracle.path_weight(k, 1.7) == pytest.approx(np.exp(1.7 * (k - 1.0)) / k, rel=1e-14)
+
+
+def test_density_dependent_kA_is_log_linear(oracle):
+    """k_A(rho) runs linearly in log density from k_A_lo at the lowest cell
+    density to k_A_hi at the highest; empty cells and the void take k_A_lo."""
+    rho = np.array([1e-3, 1e-2, 0.0, 1e-1, 1.0])
+    m = W.grey_model(5, 1.0).replace(rho=rho, kA_rho=True, kA_lo=3.0, kA_hi=1.0)
+    k, kv = oracle.kA_cells(m)
+    assert k[0] == pytest.approx(3.0) and k[4] == pytest.approx(1.0) and k[2] == 3.0 and kv == 3.0
+    assert k[1] == pytest.approx(3.0 - 2.0 / 3.0) and k[3] == pytest.approx(3.0 - 4.0 / 3.0)
+    m2 = m.replace(kA_rho=False, k_A=2.0)
+    assert np.all(oracle.kA_cells(m2)[0] == 2.0)
+
+
+@pytest.mark.parametrize("kw", [{"k_A": 0.5}, {"k_A": 2.5}, {"kA_rho": True}])
+def test_free_path_weighting_is_unbiased(oracle, kw):
+    """Eq. 8 free-path weighting (constant or density-dependent k_A) leaves the
+    expected absorption of a pure absorber unchanged (closed form)."""
+    m = W.grey_model(4, 0.8).replace(rho=np.array([0.2, 2.0, 0.7, 1.3]), **kw)
+    k = m.kabs[0] * m.rho
+    expect = CF.external_shell_absorption(m.radii, k)
+    L = oracle.source_luminosity(m)[0]
+    fr = np.array([_fractions(oracle.run(m, 20_000, s, mode="frozen_terminal", T_frozen=np.full(4, 10.0)), L)
+                   for s in range(12)])
+    mean, se = fr.mean(0), fr.std(0, ddof=1) / np.sqrt(len(fr))
+    assert np.all(np.abs(mean - expect) < 4.5 * se + 1e-9), (mean, expect, se)
+
+
+@pytest.mark.parametrize("g,g_S", [(0.0, 0.4), (0.6, 0.0), (0.6, -0.3)])
+def test_scattering_weighting_conserves_energy_on_average(oracle, g, g_S):
+    """Eq. 7 weighting of scattering directions in a pure scatterer: every
+    package escapes, and the escaping energy equals the injected energy in
+    expectation (exactly so without weighting)."""
+    m = W.grey_model(4, 1.5, albedo=1.0, g=g, r_in=0.1).replace(scat_w=True, g_S=g_S)
+    ratios = []
+    for s in range(12):
+        st = oracle.run(m, 8_000, s, mode="frozen", T_frozen=np.full(4, 10.0))["stats"]
+        assert st["escaped"] + st["kill_weight"] == 8_000
+        ratios.append((st["E_escaped"] + st["E_lost"]) / st["E_injected"])
+    ratios = np.array(ratios)
+    assert abs(ratios.mean() - 1.0) < 4.5 * ratios.std(ddof=1) / np.sqrt(len(ratios)) + 1e-12
+    assert abs(ratios.mean() - 1.0) < 0.2  # heavy-tailed weights can inflate the sample sigma
+    assert ratios.std() > 0.0  # the weights really vary
+
+
+@pytest.mark.parametrize("g_E", [0.5, -0.4])
+def test_reemission_weighting_is_unbiased(oracle, g_E):
+    """Eq. 6 weighting of re-emission directions: with grey opacity,
+    absorption + re-emission is conservative, so the escaping energy equals
+    the injected energy in expectation, and the absorbed energy per shell
+    matches the unweighted value, itself fixed by the isotropic-field
+    invariant (pin above)."""
+    m0 = W.grey_model(4, 0.9, albedo=0.0, r_in=0.2).replace(rho=np.array([2.5, 0.5, 1.2, 0.8]))
+    m = m0.replace(g_E=g_E)
+    Ew, E0, ratios = [], [], []
+    for s in range(12):
+        rw = oracle.run(m, 6_000, s, mode="frozen", T_frozen=np.full(4, 30.0))
+        r0 = oracle.run(m0, 6_000, 100 + s, mode="frozen", T_frozen=np.full(4, 30.0))
+        Ew.append(rw["E_abs"])
+        E0.append(r0["E_abs"])
+        st = rw["stats"]
+        ratios.append((st["E_escaped"] + st["E_lost"]) / st["E_injected"])
+    Ew, E0, ratios = np.array(Ew), np.array(E0), np.array(ratios)
+    se = np.sqrt(Ew.var(0, ddof=1) / len(Ew) + E0.var(0, ddof=1) / len(E0))
+    assert np.all(np.abs(Ew.mean(0) - E0.mean(0)) < 4.5 * se), (Ew.mean(0), E0.mean(0), se)
+    assert abs(ratios.mean() - 1.0) < 4.5 * ratios.std(ddof=1) / np.sqrt(len(ratios))
+
+
+def test_neutral_weighting_parameters_are_the_unweighted_run(oracle):
+    """g_E = 0, k_A = k_S = 1 and scattering weighting off reproduce the
+    unweighted run exactly (same streams, unit weights); scattering weighting
+    with g_S = 0 is a different run (isotropic about the reference direction,
+    not the dust phase function; Sect. 3)."""
+    m = W.external_cloud(8, 5.0)
+    a = oracle.run(m, 500, 3, record=True)
+    b = oracle.run(m.replace(g_E=0.0, k_A=1.0, k_S=1.0, scat_w=False), 500, 3, record=True)
+    assert np.array_equal(a["hash"], b["hash"]) and np.array_equal(a["T"], b["T"])
+    c = oracle.run(m.replace(scat_w=True, g_S=0.0), 500, 3, record=True)
+    assert not np.array_equal(a["hash"], c["hash"])
