@@ -135,6 +135,32 @@ int dies_set_sources(dies_model *m, const double *J_ext, double L_point, const d
  * exp(-tau0) in the escaping SED. */
 int dies_set_weighting(dies_model *m, double k_bg, int forced_first_interaction);
 
+/* All weighting options of Sect. 2.2 (Table 1).  Directional weighting of
+ * re-emission (Eq. 6) and scattering (Eq. 7) draws the new direction from a
+ * Henyey-Greenstein function about the reference direction (towards the
+ * centre for packages of the external field, away from it for the point
+ * source) and multiplies the package weight by the ratio of the true to the
+ * sampling density; free-path weighting (Eq. 8) draws tau from k e^(-k tau)
+ * with weight e^(tau (k - 1)) / k.  With these options a package's weight
+ * changes along its path, so energy is conserved in expectation only (the
+ * injected energy counts the source's share before any free-path weight). */
+typedef struct {
+  double k_bg;                   /* Eq. 5, (0, 1], 0.5 = unweighted */
+  int forced_first_interaction;  /* Eqs. 9-12 on the extinction optical depth */
+  double g_E;                    /* Eq. 6, (-1, 1), 0 = isotropic re-emission (off) */
+  int scatter_weighting;         /* Eq. 7 on (g_S = 0 is isotropic about the reference, not off) */
+  double g_S;                    /* Eq. 7 parameter, (-1, 1) */
+  double k_A, k_S;               /* Eq. 8 factors, > 0, 1 = off */
+  int k_A_density;               /* 1: k_A per shell, linear in log density from
+                                    k_A_low_density (lowest shell density; also the
+                                    void and empty shells) to k_A_high_density (highest) */
+  double k_A_low_density, k_A_high_density;
+} dies_weighting;
+
+/* Sets every weighting option at once (see dies_weighting).  Errors:
+ * DIES_EINVAL for NULL or out-of-range fields. */
+int dies_set_weighting_ex(dies_model *m, const dies_weighting *w);
+
 /* Precision form (DIES_PREC_*) and, for DIES_PREC_FP32, the number of
  * sequential batches n_batches >= 1 (Sect. 2.3).  fp64_radius: in
  * DIES_PREC_MIXED, shells whose outer radius is below fp64_radius * R use
@@ -267,6 +293,9 @@ int dies_batch_set_sources(dies_batch *b, const double *J_ext, double L_point, c
 int dies_batch_set_stream(dies_batch *b, void *cuda_stream);
 int dies_batch_set_launch(dies_batch *b, int block_size, int blocks_per_sm, int rare_batch, int inner_moves,
                           int aggregate_atomics);
+/* Weighting for all models of the batch (as dies_set_weighting_ex; with
+ * k_A_density the density range is each model's own). */
+int dies_batch_set_weighting(dies_batch *b, const dies_weighting *w);
 /* Graph mode for the batch, as dies_set_graph. */
 int dies_batch_set_graph(dies_batch *b, int enable);
 int dies_run_batch(dies_batch *b, uint64_t n_packages_per_model, uint64_t seed);

@@ -58,7 +58,11 @@ def config_class(cloud, precision: str) -> str:
                                                 (cloud.rho * (cloud.radii[1:] - cloud.radii[:-1])).sum()), 1e-3))))
     n_bucket = int(round(math.log2(max(cloud.n_cells, 1))))
     kind = ("ext" if cloud.J_ext is not None else "") + ("pt" if cloud.L_point > 0 else "")
-    return f"{precision}|{kind}|n2^{n_bucket}|tau10^{tau_bucket}|kbg{cloud.k_bg:.3f}|ffi{int(bool(cloud.ffi))}"
+    weighted = (getattr(cloud, "g_E", 0.0) != 0.0 or getattr(cloud, "scat_w", False) or
+                getattr(cloud, "k_A", 1.0) != 1.0 or getattr(cloud, "k_S", 1.0) != 1.0 or
+                getattr(cloud, "kA_rho", False))
+    return (f"{precision}|{kind}|n2^{n_bucket}|tau10^{tau_bucket}|kbg{cloud.k_bg:.3f}|ffi{int(bool(cloud.ffi))}"
+            + ("|w" if weighted else ""))
 
 
 def _time_model(cloud, precision: str, shape: dict, n: int, reps: int = 2) -> float:

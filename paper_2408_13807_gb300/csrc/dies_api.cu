@@ -37,7 +37,8 @@ cudaError_t launch_frozen_cdf(cudaStream_t st, int n_cells, int F, const double 
 size_t transport_smem_bytes(int n_tnodes_pow2);
 cudaError_t launch_transport(int prec, int mode, bool record, const TransportParams &P, int grid, int block,
                              cudaStream_t st);
-cudaError_t transport_occupancy(int prec, int mode, int block, int n_tnodes_pow2, bool r64, int *blocks_per_sm);
+cudaError_t transport_occupancy(int prec, int mode, int block, int n_tnodes_pow2, bool r64, bool ffi,
+                                int *blocks_per_sm);
 cudaError_t launch_finalize(cudaStream_t st, int n_cells, const double *E, const float *Eprev, const float *Ecur,
                             int fp32, const double *inv_mass, const double *Lnode, const double *lnT, int n,
                             double *T_out);
@@ -82,7 +83,7 @@ bool finite_nonneg(const double *a, int n) {
 
 // Offsets (bytes) of every segment of the device workspace.
 struct Layout {
-  size_t desc, radii, rho_in, r2d, r2f, rhod, rhof, inv_mass, inv_massf, geo, rhoe, E, Eprev, Ecur, T, sed;
+  size_t desc, radii, rho_in, r2d, r2f, rhod, rhof, inv_mass, inv_massf, kA_d, kA_f, geo, rhoe, E, Eprev, Ecur, T, sed;
   size_t sed_q, inj_q, dir_q;
   size_t freq, kabs, ksca, g, J, spec, dnu, src_cdf_d, src_alias, src_sum;
   size_t Lnode_d, Lnode_f, lnT, dalias, dcdf_d, nguide, nmeta;
@@ -107,6 +108,8 @@ struct Problem {
   std::vector<int> kind;  // per model: bit 0 external, bit 1 point (batch); 0 = follow the sources
   double k_bg = 0.5;
   int ffi = 0;
+  double g_E = 0.0, g_S = 0.0, k_A = 1.0, k_S = 1.0, kA_lo = 3.0, kA_hi = 1.0;
+  int scat_w = 0, kA_rho = 0;
   int prec = PREC_MIXED, n_batches = 1;
   double fp64_radius = 0.0;
   double T_min = 2.7, T_max = 1500.0;
@@ -182,6 +185,8 @@ struct Problem {
     L.rhof = seg(nc * 4);
     L.inv_mass = seg(nc * 8);
     L.inv_massf = seg(nc * 4);
+    L.kA_d = seg(nc * 8);
+    L.kA_f = seg(nc * 4);
     L.geo = seg(nb * 16);
     L.rhoe = seg(nb * 4);
     L.E = seg(nc * 8);
@@ -288,10 +293,46 @@ struct Problem {
     return DIES_OK;
   }
 
+  bool kA_weighting() const { return kA_rho || k_A != 1.0; }
+
+  // Absorption free-path factor per shell (Sect. 2.2.3): the constant k_A,
+  // or linear in log density from kA_lo at each model's lowest positive
+  // shell density to kA_hi at its highest (empty shells: kA_lo).
+  void kA_cells(std::vector<double> &out) const {
+    out.assign((size_t)n_cells, k_A);
+    if (!kA_rho) return;
+    for (int m = 0; m < n_models; ++m) {
+      const int c0 = desc[m].cell_off, n = desc[m].n_cells;
+      double lmin = 0.0, lmax = 0.0;
+      bool any = false;
+      for (int i = 0; i < n; ++i) {
+        const double r = rho[c0 + i];
+        if (!(r > 0.0)) continue;
+        const double l = std::log(r);
+        if (!any || l < lmin) lmin = l;
+        if (!any || l > lmax) lmax = l;
+        any = true;
+      }
+      for (int i = 0; i < n; ++i) {
+        const double r = rho[c0 + i];
+        if (!(r > 0.0)) out[c0 + i] = kA_lo;
+        else if (!(lmax > lmin)) out[c0 + i] = kA_hi;
+        else out[c0 + i] = kA_hi + (kA_lo - kA_hi) * (lmax - std::log(r)) / (lmax - lmin);
+      }
+    }
+  }
+
   int build_tables() {
     fill_desc();
     int rc;
     if ((rc = upload(lay.desc, desc.data(), desc.size() * sizeof(ModelDesc)))) return rc;
+    {
+      std::vector<double> kd;
+      kA_cells(kd);
+      std::vector<float> kf(kd.begin(), kd.end());
+      if ((rc = upload(lay.kA_d, kd.data(), kd.size() * 8))) return rc;
+      if ((rc = upload(lay.kA_f, kf.data(), kf.size() * 4))) return rc;
+    }
     if ((rc = upload(lay.radii, radii.data(), radii.size() * 8))) return rc;
     if ((rc = upload(lay.rho_in, rho.data(), rho.size() * 8))) return rc;
     std::vector<double> pad(6 * kMaxFreq, 0.0);
@@ -372,6 +413,17 @@ struct Problem {
     P.time_budget_ns = (unsigned long long)(time_budget_s * 1e9);
     P.inv_n = (float)(1.0 / (double)n);
     P.k_bg_f = (float)k_bg;
+    P.g_E = g_E;
+    P.g_S = g_S;
+    P.k_S = k_S;
+    P.scat_w = scat_w;
+    P.kA_d = kA_weighting() ? at<double>(lay.kA_d) : nullptr;
+    P.kA_f = kA_weighting() ? at<float>(lay.kA_f) : nullptr;
+    P.kA_void = kA_rho ? kA_lo : k_A;
+    P.g_E_f = (float)g_E;
+    P.g_S_f = (float)g_S;
+    P.k_S_f = (float)k_S;
+    P.kA_void_f = (float)P.kA_void;
     P.kbg_plain = (k_bg == 0.5);
     P.r64 = (prec == PREC_MIXED && fp64_radius > 0.0);
     P.batch_min = rare_batch;
@@ -384,7 +436,7 @@ struct Problem {
     int bps = blocks_per_sm;
     int occ = 0;
     const bool r64 = (prec_ == PREC_MIXED && mode == MODE_IRE && fp64_radius > 0.0);
-    DIES_CUDA(transport_occupancy(prec_, mode, block, next_pow2(n_tnodes), r64, &occ));
+    DIES_CUDA(transport_occupancy(prec_, mode, block, next_pow2(n_tnodes), r64, ffi != 0, &occ));
     if (occ < 1) return fail(DIES_ECUDA, "transport kernel cannot be resident with block size %d", block);
     if (bps <= 0 || bps > occ) bps = occ;
     *grid = sm_count * bps;
@@ -791,6 +843,35 @@ int dies_set_weighting(dies_model *m, double k_bg, int ffi) {
   return DIES_OK;
 }
 
+static int set_weighting_ex(Problem &p, const dies_weighting *w) {
+  if (!w) return fail(DIES_EINVAL, "weighting is NULL");
+  if (!(w->k_bg > 0.0 && w->k_bg <= 1.0)) return fail(DIES_EINVAL, "k_bg must lie in (0, 1]");
+  if (!(std::fabs(w->g_E) < 1.0)) return fail(DIES_EINVAL, "g_E must lie in (-1, 1)");
+  if (!(std::fabs(w->g_S) < 1.0)) return fail(DIES_EINVAL, "g_S must lie in (-1, 1)");
+  if (!(w->k_A > 0.0 && std::isfinite(w->k_A)) || !(w->k_S > 0.0 && std::isfinite(w->k_S)))
+    return fail(DIES_EINVAL, "k_A and k_S must be finite and > 0");
+  if (w->k_A_density && !(w->k_A_low_density > 0.0 && std::isfinite(w->k_A_low_density) &&
+                          w->k_A_high_density > 0.0 && std::isfinite(w->k_A_high_density)))
+    return fail(DIES_EINVAL, "k_A_low_density and k_A_high_density must be finite and > 0");
+  p.k_bg = w->k_bg;
+  p.ffi = w->forced_first_interaction ? 1 : 0;
+  p.g_E = w->g_E;
+  p.scat_w = w->scatter_weighting ? 1 : 0;
+  p.g_S = w->g_S;
+  p.k_A = w->k_A;
+  p.k_S = w->k_S;
+  p.kA_rho = w->k_A_density ? 1 : 0;
+  p.kA_lo = w->k_A_low_density;
+  p.kA_hi = w->k_A_high_density;
+  p.tables_valid = false;
+  return DIES_OK;
+}
+
+int dies_set_weighting_ex(dies_model *m, const dies_weighting *w) {
+  if (!m) return fail(DIES_EINVAL, "model is NULL");
+  return set_weighting_ex(m->p, w);
+}
+
 int dies_set_precision(dies_model *m, int mode, int n_batches, double fp64_radius) {
   if (!m) return fail(DIES_EINVAL, "model is NULL");
   if (mode != DIES_PREC_MIXED && mode != DIES_PREC_FP32 && mode != DIES_PREC_FP64)
@@ -1004,7 +1085,7 @@ int dies_run_frozen_static(dies_model *m, const double *T_frozen_dev, uint64_t n
   DIES_CUDA(launch_frozen_cdf(p.stream, p.n_cells, p.F, p.at<double>(p.lay.freq), p.at<double>(p.lay.kabs),
                               p.at<double>(p.lay.dnu), T_frozen_dev, cdf));
   int occ = 0;
-  DIES_CUDA(transport_occupancy(PREC_FP64, MODE_FROZEN, p.block, next_pow2(p.n_tnodes), false, &occ));
+  DIES_CUDA(transport_occupancy(PREC_FP64, MODE_FROZEN, p.block, next_pow2(p.n_tnodes), false, false, &occ));
   if (occ < 1) return fail(DIES_ECUDA, "transport kernel cannot be resident with block size %d", p.block);
   const int bps = (p.blocks_per_sm > 0 && p.blocks_per_sm < occ) ? p.blocks_per_sm : occ;
   const int mode = (flags == DIES_FROZEN_ABSORB_TERMINAL) ? MODE_FROZEN_TERMINAL : MODE_FROZEN;
@@ -1078,6 +1159,11 @@ int dies_batch_set_launch(dies_batch *b, int block_size, int blocks_per_sm, int 
                           int aggregate_atomics) {
   if (!b) return fail(DIES_EINVAL, "batch is NULL");
   return set_launch(b->p, block_size, blocks_per_sm, rare_batch, inner_moves, aggregate_atomics);
+}
+
+int dies_batch_set_weighting(dies_batch *b, const dies_weighting *w) {
+  if (!b) return fail(DIES_EINVAL, "batch is NULL");
+  return set_weighting_ex(b->p, w);
 }
 
 int dies_batch_set_graph(dies_batch *b, int enable) {

@@ -122,6 +122,13 @@ struct TransportParams {
   // options
   double k_bg;
   int ffi;
+  // weighted sampling beyond k_bg / FFI (Eqs. 6-8); kA_* null = no k_A weighting
+  double g_E, g_S, k_S;
+  int scat_w;
+  const double *kA_d;       // per cell k_A (FP64 form)
+  const float *kA_f;        // per cell k_A (FP32 forms)
+  double kA_void;
+  float g_E_f, g_S_f, k_S_f, kA_void_f;
   int mode;
   unsigned long long max_events;
   unsigned long long time_budget_ns;

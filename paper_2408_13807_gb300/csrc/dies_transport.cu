@@ -185,6 +185,36 @@ __device__ __forceinline__ int node_count_guided(const Shared &S, const float *L
   return j;
 }
 
+// ------------------------------------------- weighted sampling (Sect. 2.2)
+// Henyey-Greenstein cosine by inversion of its CDF (Eq. 6 form; |g| < 1e-6
+// is isotropic) and twice its density, (1 - g^2) / (1 + g^2 - 2 g mu)^(3/2).
+__device__ __forceinline__ double hg_mu_d(double g, double u) {
+  if (fabs(g) < 1e-6) return 2.0 * u - 1.0;
+  const double t = (1.0 - g * g) / (1.0 - g + 2.0 * g * u);
+  return fmin(fmax((1.0 + g * g - t * t) / (2.0 * g), -1.0), 1.0);
+}
+__device__ __forceinline__ double hg_pdf2_d(double g, double mu) {
+  const double q = 1.0 + g * g - 2.0 * g * mu;
+  return (1.0 - g * g) / (q * sqrt(q));
+}
+// FP32: the cosine and 1 - cosine^2 (cancellation-free for forward angles)
+__device__ __forceinline__ void hg_draw_f(float g, float u, float &mu, float &st2) {
+  if (fabsf(g) < 1e-6f) {
+    mu = 2.0f * u - 1.0f;
+    st2 = 4.0f * u * (1.0f - u);
+    return;
+  }
+  const float b = 1.0f - g, den = fmaf(2.0f * g, u, b);
+  const float t = __fdividef(1.0f - g * g, den);
+  mu = fminf(fmaxf((1.0f + g * g - t * t) * __fdividef(0.5f, g), -1.0f), 1.0f);
+  const float omt = fminf(__fdividef(b * (1.0f - u) * (t + b), den), 2.0f);
+  st2 = omt * (2.0f - omt);
+}
+__device__ __forceinline__ float hg_pdf2_f(float g, float mu) {
+  const float q = fmaf(-2.0f * g, mu, 1.0f + g * g);
+  return (1.0f - g * g) * rsqrtf(q) / q;
+}
+
 // number of table nodes with Lambda_j <= e (table padded with +inf to pow2)
 __device__ __forceinline__ int node_count_f(const float *L, int pow2, float e) {
   int j = 0;
@@ -339,11 +369,42 @@ __device__ __forceinline__ void set_freq(const Shared &S, Lane<typename RealOf<P
 // same column travelled, so only the smaller and which path it belongs to are
 // carried: one multiply-add-compare per crossing.  Interactions without
 // absorption and ties resolve as in the FP64 form.
-__device__ __forceinline__ void set_paths(const Shared &S, Lane<float> &L, float tS, float tA) {
+// With free-path weighting (Eq. 8) tau = -ln(u) / k and the package weight
+// gains e^(tau (k - 1)) / k per path; the factor is returned (k_A is that of
+// the package's current cell).
+__device__ __forceinline__ float set_paths(const TransportParams &P, const Shared &S, Lane<float> &L, float tS,
+                                           float tA) {
+  float wf = 1.0f;
+  if (P.k_S_f != 1.0f) {
+    const float k = P.k_S_f;
+    tS = __fdividef(tS, k);
+    wf *= __fdividef(__expf(tS * (k - 1.0f)), k);
+  }
+  if (P.kA_f) {
+    const float k = (L.cell >= 0) ? __ldg(P.kA_f + L.cell_off + L.cell) : P.kA_void_f;
+    if (k != 1.0f) {
+      tA = __fdividef(tA, k);
+      wf *= __fdividef(__expf(tA * (k - 1.0f)), k);
+    }
+  }
   const float nA = tA * S.inv_ka_f[L.f], nS = tS * S.inv_ks_f[L.f];
   L.acc = 0.0f;
   L.lim = fminf(nA, nS);
   L.next_ev = (nS < nA) ? ST_SCATTER : ST_ABSORB;
+  return wf;
+}
+
+// FP64 form: both free paths from one block, weighted as the oracle does
+// (scattering path first); returns the weight factor.
+__device__ __forceinline__ double paths_d(const TransportParams &P, Lane<double> &L, const U4 &b) {
+  const double kS = P.k_S;
+  const double kA = P.kA_d ? ((L.cell >= 0) ? __ldg(P.kA_d + L.cell_off + L.cell) : P.kA_void) : 1.0;
+  L.tauS = -log(u01d(b.x, b.y)) / kS;
+  L.tauA = -log(u01d(b.z, b.w)) / kA;
+  double wf = 1.0;
+  if (kS != 1.0) wf *= exp(L.tauS * (kS - 1.0)) / kS;
+  if (kA != 1.0) wf *= exp(L.tauA * (kA - 1.0)) / kA;
+  return wf;
 }
 
 // ----------------------------------- forced first interaction (Sect. 2.2.2)
@@ -497,12 +558,18 @@ __device__ __forceinline__ void inject(const TransportParams &P, Shared &S, Lane
   const ModelDesc *D = P.desc + L.model;
   L.w = Real(1);
   Real u_int = Real(0.5);
+  Real w_path = Real(1);  // free-path weight of the first flight (Eq. 8), applied after the injection tally
   if constexpr (PREC == PREC_FP64) {
     const double u_f = u01d(a.x, a.y), u_mu = u01d(a.z, a.w);
     set_freq<PREC>(S, L, cdf_pick(S.src_cdf_d[L.src], u_f));
     const U4 b = draw<PREC>(S, L);
-    L.tauS = -log(u01d(b.x, b.y));
-    L.tauA = -log(u01d(b.z, b.w));
+    L.cell = (L.src == 0) ? L.n - 1 : __ldg(&D->point_cell);
+    if (P.ffi) {  // the forced flight replaces these paths
+      L.tauS = -log(u01d(b.x, b.y));
+      L.tauA = -log(u01d(b.z, b.w));
+    } else {
+      w_path = paths_d(P, L, b);
+    }
     if (L.src == 0) {
       const double R = __ldg(&D->R);
       double mu;
@@ -528,7 +595,9 @@ __device__ __forceinline__ void inject(const TransportParams &P, Shared &S, Lane
   } else {
     set_freq<PREC>(S, L, alias_pick(S.src_alias[L.src], a.x >> 9));
     const float v = u01f_fine(a.y);  // 1 - u of the direction draw
-    set_paths(S, L, -__logf(u01f_word(a.z)), -__logf(u01f_word(a.w)));
+    L.cell = (L.src == 0) ? L.n - 1 : __ldg(&D->point_cell);
+    w_path = set_paths(P, S, L, -__logf(u01f_word(a.z)), -__logf(u01f_word(a.w)));
+    if (P.ffi) w_path = 1.0f;  // the forced flight replaces these paths
     if (L.src == 0) {
       const float Rf = __ldg(&D->Rf);
       float mu, sin2;
@@ -566,6 +635,7 @@ __device__ __forceinline__ void inject(const TransportParams &P, Shared &S, Lane
     else atomicAdd(P.inj_q + (size_t)L.model * 2 + L.src, q);
   }
   record<RECORD>(L, EV_INJECT, L.cell, L.f);
+  L.w *= w_path;
   if (L.w < Real(1e-10)) {
     lose<RECORD>(P, S, L, CNT_KILL_WEIGHT);
     return;
@@ -596,28 +666,54 @@ __device__ __forceinline__ void scatter(const TransportParams &P, Shared &S, Lan
   if constexpr (PREC == PREC_FP64) {
     const double u_mu = u01d(a.x, a.y), u_phi = u01d(a.z, a.w);
     const double g = S.g_d[L.f];
-    double mu_s;
-    if (fabs(g) < 1e-6) {
-      mu_s = 2.0 * u_mu - 1.0;
-    } else {
-      const double t = (1.0 - g * g) / (1.0 - g + 2.0 * g * u_mu);
-      mu_s = fmin(fmax((1.0 + g * g - t * t) / (2.0 * g), -1.0), 1.0);
-    }
-    const double st = sqrt(fmax(0.0, 1.0 - mu_s * mu_s));
     const double r2 = L.p2 + L.s * L.s;
     const double r = sqrt(r2);
-    if (r > 0.0) {
-      const double mu = L.s / r, sth = sqrt(fmax(L.p2, 0.0)) / r;
-      const double mup = mu * mu_s + sth * st * cos(kTwoPi * u_phi);
-      L.s = r * mup;
+    if (P.scat_w) {
+      // Eq. 7: cosine mr to the reference direction (sg r_hat) from HG(g_S),
+      // azimuth about it from the plane of the reference and the old direction
+      const double sg = (L.src == 0) ? -1.0 : 1.0;
+      const double dref = (r > 0.0) ? sg * L.s / r : 1.0;
+      const double mr = hg_mu_d(P.g_S, u_mu), sr = sqrt(fmax(0.0, 1.0 - mr * mr));
+      const double cos_t = dref * mr + sqrt(fmax(0.0, 1.0 - dref * dref)) * sr * cos(kTwoPi * u_phi);
+      L.w *= hg_pdf2_d(g, cos_t) / hg_pdf2_d(P.g_S, mr);
+      L.s = r * (sg * mr);
       L.p2 = fmax(r2 - L.s * L.s, 0.0);
     } else {
-      L.s = 0.0;
-      L.p2 = 0.0;
+      const double mu_s = hg_mu_d(g, u_mu);
+      const double st = sqrt(fmax(0.0, 1.0 - mu_s * mu_s));
+      if (r > 0.0) {
+        const double mu = L.s / r, sth = sqrt(fmax(L.p2, 0.0)) / r;
+        const double mup = mu * mu_s + sth * st * cos(kTwoPi * u_phi);
+        L.s = r * mup;
+        L.p2 = fmax(r2 - L.s * L.s, 0.0);
+      } else {
+        L.s = 0.0;
+        L.p2 = 0.0;
+      }
     }
     const U4 b = draw<PREC>(S, L);
-    L.tauS = -log(u01d(b.x, b.y));
-    L.tauA = -log(u01d(b.z, b.w));
+    L.w *= paths_d(P, L, b);
+  } else if (P.scat_w) {
+    // Eq. 7 in FP32: cosine to the reference direction from HG(g_S)
+    const float u = u01f_word(a.x), u_phi = u01f_word(a.y);
+    const float sg = (L.src == 0) ? -1.0f : 1.0f;
+    const float r2 = L.p2 + L.s * L.s;
+    float mr, sr2;
+    hg_draw_f(P.g_S_f, u, mr, sr2);
+    if (r2 > 0.0f) {
+      const float rinv = rsqrtf(r2);
+      const float dref = sg * L.s * rinv, sth = sqrtf(L.p2) * rinv;  // sth = sin of the old radial angle
+      const float cos_t = fminf(fmaxf(fmaf(dref, mr, sth * sqrtf(sr2) * __cosf(6.2831853f * u_phi)), -1.0f), 1.0f);
+      L.w *= __fdividef(hg_pdf2_f(S.hg_c[L.f] * 0.5f, cos_t), hg_pdf2_f(P.g_S_f, mr));
+      L.s = r2 * rinv * (sg * mr);
+      L.p2 = r2 * sr2;
+    } else {
+      // at r = 0 the reference direction is taken along the old one
+      L.w *= __fdividef(hg_pdf2_f(S.hg_c[L.f] * 0.5f, mr), hg_pdf2_f(P.g_S_f, mr));
+      L.s = 0.0f;
+      L.p2 = 0.0f;
+    }
+    L.w *= set_paths(P, S, L, -__logf(u01f_word(a.z)), -__logf(u01f_word(a.w)));
   } else {
     const float u = u01f_word(a.x), u_phi = u01f_word(a.y);
     const int f = L.f;
@@ -651,7 +747,7 @@ __device__ __forceinline__ void scatter(const TransportParams &P, Shared &S, Lan
       L.s = 0.0f;
       L.p2 = 0.0f;
     }
-    set_paths(S, L, -__logf(u01f_word(a.z)), -__logf(u01f_word(a.w)));
+    L.w *= set_paths(P, S, L, -__logf(u01f_word(a.z)), -__logf(u01f_word(a.w)));
   }
   T.scat++;
   if constexpr (RECORD) L.nsca++;
@@ -691,14 +787,22 @@ __device__ __forceinline__ void absorb(const TransportParams &P, Shared &S, cons
     }
     set_freq<PREC>(S, L, f);
     const U4 b = draw<PREC>(S, L);
-    const double mu = 2.0 * u01d(b.x, b.y) - 1.0;
+    double mu;
+    if (P.g_E != 0.0) {
+      // Eq. 6: cosine to the reference direction from HG(g_E), weight
+      // isotropic density / HG density
+      const double mr = hg_mu_d(P.g_E, u01d(b.x, b.y));
+      mu = (L.src == 0) ? -mr : mr;
+      L.w /= hg_pdf2_d(P.g_E, mr);
+    } else {
+      mu = 2.0 * u01d(b.x, b.y) - 1.0;
+    }
     const double r2 = L.p2 + L.s * L.s;
     const double r = sqrt(r2);
     L.s = r * mu;
     L.p2 = fmax(r2 - L.s * L.s, 0.0);
     const U4 c = draw<PREC>(S, L);
-    L.tauS = -log(u01d(c.x, c.y));
-    L.tauA = -log(u01d(c.z, c.w));
+    L.w *= paths_d(P, L, c);
   } else {
     // one Philox block gives five 23-bit uniforms (4 x top bits + 1 from the low bits)
     const float u_e = u01f_word(a.x), u_mu = u01f_word(a.z);  // a.y: the re-emission bin
@@ -742,12 +846,21 @@ __device__ __forceinline__ void absorb(const TransportParams &P, Shared &S, cons
     if (eo + de > sLnode[P.n_tnodes - 1]) atomicAdd(&S.rare[CNT_CLAMP_HI], 1u);
     const int row = min(j, P.n_tnodes - 1);
     set_freq<PREC>(S, L, alias_pick_ldg(P.dalias + ((size_t)row << kFreqShift), a.y >> 9));
-    // isotropic re-emission: mu' = 2u - 1, sin^2 = 4u(1-u)
     const float r2 = L.p2 + L.s * L.s;
     const float r = sqrtf(r2);
-    L.s = r * (2.0f * u_mu - 1.0f);
-    L.p2 = r2 * (4.0f * u_mu * (1.0f - u_mu));
-    set_paths(S, L, -__logf(u_ts), -__logf(u_ta));
+    if (P.g_E_f != 0.0f) {
+      // Eq. 6: cosine to the reference direction from HG(g_E)
+      float mr, sr2;
+      hg_draw_f(P.g_E_f, u_mu, mr, sr2);
+      L.s = r * ((L.src == 0) ? -mr : mr);
+      L.p2 = r2 * sr2;
+      L.w *= __fdividef(1.0f, hg_pdf2_f(P.g_E_f, mr));
+    } else {
+      // isotropic re-emission: mu' = 2u - 1, sin^2 = 4u(1-u)
+      L.s = r * (2.0f * u_mu - 1.0f);
+      L.p2 = r2 * (4.0f * u_mu * (1.0f - u_mu));
+    }
+    L.w *= set_paths(P, S, L, -__logf(u_ts), -__logf(u_ta));
   }
   record<RECORD>(L, EV_ABSORB, L.cell, L.f);
 }
@@ -821,6 +934,9 @@ __device__ __forceinline__ void rare(const TransportParams &P, Shared &S, const 
   if (kind == ST_INJECT) inject<PREC, RECORD>(P, S, L, T, a);
   else if (kind == ST_SCATTER) scatter<PREC, RECORD>(P, S, L, T, a);
   else absorb<PREC, MODE, RECORD>(P, S, sLnode, L, T, a);
+  // weighted directions and free paths (Eqs. 6-8) change the weight at events:
+  // the floor of Sect. 2.2.1 applies after each
+  if (kind != ST_INJECT && L.st == ST_NORMAL && L.w < 1e-10f) lose<RECORD>(P, S, L, CNT_KILL_WEIGHT);
 }
 
 __device__ __forceinline__ unsigned long long globaltimer() {
@@ -1116,15 +1232,20 @@ cudaError_t launch_transport(int prec, int mode, bool record, const TransportPar
   }
 }
 
-cudaError_t transport_occupancy(int prec, int mode, int block, int n_tnodes_pow2, bool r64, int *blocks_per_sm) {
+cudaError_t transport_occupancy(int prec, int mode, int block, int n_tnodes_pow2, bool r64, bool ffi,
+                                int *blocks_per_sm) {
   const size_t smem = transport_smem_bytes(n_tnodes_pow2);
   if (mode != MODE_IRE) return occupancy_one<PREC_FP64, MODE_FROZEN, true>(block, smem, blocks_per_sm);
   switch (prec) {
     case PREC_MIXED:
-      // the variants differ by a few registers at most; the FFI ones are the larger
-      return r64 ? occupancy_one<PREC_MIXED, MODE_IRE, false, OPT_R64>(block, smem, blocks_per_sm)
-                 : occupancy_one<PREC_MIXED, MODE_IRE, false, 0>(block, smem, blocks_per_sm);
-    case PREC_FP32: return occupancy_one<PREC_FP32, MODE_IRE, false>(block, smem, blocks_per_sm);
+      if (ffi)
+        return r64 ? occupancy_one<PREC_MIXED, MODE_IRE, false, OPT_R64>(block, smem, blocks_per_sm)
+                   : occupancy_one<PREC_MIXED, MODE_IRE, false, 0>(block, smem, blocks_per_sm);
+      return r64 ? occupancy_one<PREC_MIXED, MODE_IRE, false, OPT_R64 | OPT_NOFFI>(block, smem, blocks_per_sm)
+                 : occupancy_one<PREC_MIXED, MODE_IRE, false, OPT_NOFFI>(block, smem, blocks_per_sm);
+    case PREC_FP32:
+      return ffi ? occupancy_one<PREC_FP32, MODE_IRE, false, 0>(block, smem, blocks_per_sm)
+                 : occupancy_one<PREC_FP32, MODE_IRE, false, OPT_NOFFI>(block, smem, blocks_per_sm);
     default: return occupancy_one<PREC_FP64, MODE_IRE, false>(block, smem, blocks_per_sm);
   }
 }

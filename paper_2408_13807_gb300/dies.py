@@ -36,13 +36,14 @@ PREC = {"mixed": DIES_PREC_MIXED, "fp32": DIES_PREC_FP32, "fp64": DIES_PREC_FP64
 
 # every symbol include/dies.h declares
 EXPORTS = (
-    "dies_create_model", "dies_set_dust", "dies_set_sources", "dies_set_weighting", "dies_set_precision",
+    "dies_create_model", "dies_set_dust", "dies_set_sources", "dies_set_weighting", "dies_set_weighting_ex",
+    "dies_set_precision",
     "dies_set_tgrid", "dies_set_stream", "dies_set_launch", "dies_set_time_budget", "dies_set_graph",
     "dies_workspace_bytes",
     "dies_set_workspace", "dies_run", "dies_run_async", "dies_get_temperatures", "dies_get_absorbed",
     "dies_get_escaping_sed", "dies_get_stats", "dies_run_frozen", "dies_destroy_model", "dies_create_batch",
     "dies_batch_set_dust", "dies_batch_set_sources", "dies_batch_set_stream", "dies_batch_set_launch",
-    "dies_batch_set_graph",
+    "dies_batch_set_graph", "dies_batch_set_weighting",
     "dies_run_batch", "dies_run_batch_async", "dies_batch_get_temperatures", "dies_batch_get_escaping_sed",
     "dies_batch_get_stats", "dies_destroy_batch", "dies_last_error", "dies_launch_count", "dies_version",
     "dies_measure_peaks",
@@ -71,6 +72,24 @@ class dies_stats(ctypes.Structure):
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["diag"] = list(self.diag)
         return d
+
+
+class dies_weighting(ctypes.Structure):
+    _fields_ = [
+        ("k_bg", ctypes.c_double), ("forced_first_interaction", ctypes.c_int), ("g_E", ctypes.c_double),
+        ("scatter_weighting", ctypes.c_int), ("g_S", ctypes.c_double), ("k_A", ctypes.c_double),
+        ("k_S", ctypes.c_double), ("k_A_density", ctypes.c_int), ("k_A_low_density", ctypes.c_double),
+        ("k_A_high_density", ctypes.c_double),
+    ]
+
+
+def weighting_of(cloud) -> dies_weighting:
+    """The weighting options of a workloads.CloudModel as the C struct."""
+    return dies_weighting(
+        k_bg=float(cloud.k_bg), forced_first_interaction=int(bool(cloud.ffi)), g_E=float(cloud.g_E),
+        scatter_weighting=int(bool(cloud.scat_w)), g_S=float(cloud.g_S), k_A=float(cloud.k_A), k_S=float(cloud.k_S),
+        k_A_density=int(bool(cloud.kA_rho)), k_A_low_density=float(cloud.kA_lo),
+        k_A_high_density=float(cloud.kA_hi))
 
 
 class dies_peaks(ctypes.Structure):
@@ -111,6 +130,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "dies_set_launch": (i, [_vp, i, i, i, i, i]),
         "dies_set_time_budget": (i, [_vp, d]),
         "dies_set_graph": (i, [_vp, i]),
+        "dies_set_weighting_ex": (i, [_vp, _vp]),
+        "dies_batch_set_weighting": (i, [_vp, _vp]),
         "dies_batch_set_graph": (i, [_vp, i]),
         "dies_workspace_bytes": (i, [_vp, _P(ctypes.c_size_t)]),
         "dies_set_workspace": (i, [_vp, _vp, ctypes.c_size_t]),
@@ -203,6 +224,14 @@ def dies_set_launch(h, block_size: int, blocks_per_sm: int = 0, rare_batch: int 
 
 def dies_set_time_budget(h, seconds: float):
     return _check(load().dies_set_time_budget(h, float(seconds)))
+
+
+def dies_set_weighting_ex(h, w: dies_weighting):
+    return _check(load().dies_set_weighting_ex(h, ctypes.byref(w)))
+
+
+def dies_batch_set_weighting(h, w: dies_weighting):
+    return _check(load().dies_batch_set_weighting(h, ctypes.byref(w)))
 
 
 def dies_set_graph(h, enable: bool):
@@ -383,7 +412,7 @@ class Model:
         self._ws = None
         dies_set_dust(self.h, cloud.freq, cloud.kabs, cloud.ksca, cloud.g)
         dies_set_sources(self.h, cloud.J_ext, cloud.L_point, cloud.point_spec)
-        dies_set_weighting(self.h, cloud.k_bg, cloud.ffi)
+        dies_set_weighting_ex(self.h, weighting_of(cloud))
         dies_set_precision(self.h, PREC[precision], n_batches, fp64_radius)
         dies_set_tgrid(self.h, *tgrid)
         dies_set_launch(self.h, block_size, blocks_per_sm, rare_batch, inner_moves, aggregate_atomics)
@@ -453,6 +482,7 @@ class Batch:
         dies_batch_set_sources(self.h, J, pt.L_point if pt else 0.0, pt.point_spec if pt else None)
         dies_batch_set_launch(self.h, block_size, blocks_per_sm, rare_batch, inner_moves, aggregate_atomics)
         dies_batch_set_graph(self.h, graph)
+        dies_batch_set_weighting(self.h, weighting_of(c0))
 
     def set_stream(self, stream_handle: int):
         dies_batch_set_stream(self.h, stream_handle)

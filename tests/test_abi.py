@@ -48,6 +48,7 @@ def test_create_and_set_validate_inputs(lib):
         D.dies_set_tgrid(h, 2.7, 1500.0, 1024)
         D.dies_set_launch(h, 128, 0, 12, 4)
         D.dies_set_graph(h, True)
+        D.dies_set_weighting_ex(h, D.weighting_of(m.replace(g_E=0.3, scat_w=True, g_S=-0.2, k_A=2.0, kA_rho=True)))
         assert D.dies_workspace_bytes(h) > 0
         bad = [
             lambda: D.dies_set_dust(h, m.freq[::-1], m.kabs, m.ksca, m.g),
@@ -72,6 +73,11 @@ def test_create_and_set_validate_inputs(lib):
             lambda: D.dies_set_launch(h, 128, 0, 8, 8, 2),
             lambda: D._check(D.load().dies_set_graph(h, 2)),
             lambda: D.dies_set_time_budget(h, 0.0),
+            lambda: D.dies_set_weighting_ex(h, D.weighting_of(m.replace(g_E=1.0))),
+            lambda: D.dies_set_weighting_ex(h, D.weighting_of(m.replace(scat_w=True, g_S=-1.5))),
+            lambda: D.dies_set_weighting_ex(h, D.weighting_of(m.replace(k_A=0.0))),
+            lambda: D.dies_set_weighting_ex(h, D.weighting_of(m.replace(k_S=float("inf")))),
+            lambda: D.dies_set_weighting_ex(h, D.weighting_of(m.replace(kA_rho=True, kA_lo=-1.0))),
         ]
         for call in bad:
             with pytest.raises(D.DiesError) as e:

@@ -36,6 +36,12 @@ FROZEN_CASES = {
     "point_log_void": lambda: W.point_source_cloud(40, 1e-3, 30.0),
     "grey_void_scatter": lambda: W.grey_model(7, 3.0, albedo=0.6, g=0.7, r_in=0.2),
     "both_sources": lambda: W.external_cloud(12, 5.0).replace(L_point=W.L_SUN, point_spec=W.blackbody(W.freq_grid(), 6000.0)),
+    # weighted sampling of Sect. 2.2 (Eqs. 6-8)
+    "weighted_gE_kA_kS": lambda: W.external_cloud(16, 5.0).replace(g_E=0.5, k_A=2.0, k_S=0.7),
+    "weighted_gS_scatter": lambda: W.grey_model(7, 3.0, albedo=0.6, g=0.7, r_in=0.2).replace(scat_w=True, g_S=0.3),
+    "weighted_point_kA_rho": lambda: W.point_source_cloud(24, 1e-3, 20.0).replace(g_E=-0.3, kA_rho=True),
+    "weighted_all_ffi": lambda: W.external_cloud(12, 0.8, ffi=True, k_bg=1.0 / 3.0).replace(
+        g_E=0.4, scat_w=True, g_S=-0.2, k_A=1.5),
 }
 
 
@@ -59,6 +65,9 @@ def test_frozen_pass_bit_exact(D, oracle, name, terminal):
     assert st["absorbed"] == ref["stats"]["absorb"]
     assert st["scattered"] == ref["stats"]["scatter"]
     assert st["crossed"] == ref["stats"]["cross"]
+    assert st["killed_weight"] == ref["stats"]["kill_weight"]
+    assert st["E_injected"] == pytest.approx(ref["stats"]["E_injected"], rel=1e-9)
+    assert st["E_lost"] == pytest.approx(ref["stats"]["E_lost"], rel=1e-5, abs=1e-12 * ref["stats"]["E_injected"])
 
 
 def test_frozen_pass_ragged_sizes(D, oracle):
@@ -284,4 +293,30 @@ def test_graph_mode_single_model_matches_oracle(D, oracle):
     m = D.Model(cloud, precision="mixed", graph=True)
     Tg = np.array([m.run(N, seed=s).temperatures() for s in range(16)])
     To = np.array([r["T"] for r in oracle.run_seeds(cloud, N, range(100, 116))])
+    assert_ensembles_agree(Tg, To, 0.01, min_gated=cloud.n_cells // 2)
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp32"])
+def test_weighted_sampling_matches_oracle_16_seeds(D, oracle, prec):
+    """Directional (Eqs. 6, 7) and free-path (Eq. 8) weighting in the FP32
+    forms against the FP64 oracle with the same options."""
+    cloud = W.config1().replace(g_E=0.3, scat_w=True, g_S=0.2, k_A=1.5, k_S=0.8)
+    N = 1_000_000
+    m = D.Model(cloud, precision=prec, n_batches=50 if prec == "fp32" else 1)
+    Tg = np.array([m.run(N, seed=s).temperatures() for s in range(16)])
+    To = np.array([r["T"] for r in oracle.run_seeds(cloud, N, range(400, 416))])
+    r = assert_ensembles_agree(Tg, To, 0.01, min_gated=cloud.n_cells // 2)
+    st = m.stats()
+    assert st["status_word"] == 0
+    # the injected energy is the sources' (weights of Eqs. 6-8 act after the injection tally)
+    assert st["E_injected"] == pytest.approx(oracle.source_luminosity(cloud).sum(), rel=1e-6)
+    print(f"{prec} weighted: max rel (gated) {r['max_rel_gated']:.4f}, max z {r['max_z']:.2f}")
+
+
+def test_density_dependent_kA_matches_oracle(D, oracle):
+    cloud = W.external_cloud(32, 0.5).replace(kA_rho=True, kA_lo=3.0, kA_hi=1.0)
+    N = 1_000_000
+    m = D.Model(cloud, precision="mixed")
+    Tg = np.array([m.run(N, seed=s).temperatures() for s in range(16)])
+    To = np.array([r["T"] for r in oracle.run_seeds(cloud, N, range(500, 516))])
     assert_ensembles_agree(Tg, To, 0.01, min_gated=cloud.n_cells // 2)
