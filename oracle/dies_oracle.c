@@ -36,6 +36,10 @@
  *     direction from an HG function of parameter g_S about the reference
  *     direction, weight = dust HG pdf of the scattering angle / HG(g_S) pdf
  *     of the angle to the reference direction;
+ *   - optionally, re-emission from a point drawn uniformly over the volume of
+ *     the absorbing cell instead of the absorption point (the test variant
+ *     of Sect. 4): r^3 uniform between the cell's inner and outer r^3, the
+ *     angular position kept (irrelevant by symmetry);
  *   - free-path weighting (Sect. 2.2.3, Eq. 8): tau = -ln(u) / k with weight
  *     e^(tau (k - 1)) / k, separately for absorption (k_A) and scattering
  *     (k_S); optionally k_A per cell, linear in log density from k_A_lo at the
@@ -60,7 +64,8 @@
  * {u_tauS, u_tauA}; forced first interaction {u_int, u_type}; scattering
  * {u_mu_s, u_phi}, {u_tauS, u_tauA}; absorption {u_e, u_nu}, {u_mu, u_phi},
  * {u_tauS, u_tauA}.  u_e is reserved for table-based temperature updates and
- * is drawn but unused here.  The weighted directions use the same blocks:
+ * is drawn but unused here.  With the re-emission point randomised, one more
+ * block {u_r, unused} follows {u_e, u_nu}.  The weighted directions use the same blocks:
  * {u_mu, u_phi} give the cosine to the reference direction and the azimuth
  * about it.
  */
@@ -107,6 +112,7 @@ typedef struct {
   double k_A, k_S;          /* free-path weighting (Eq. 8); 1 = off */
   int32_t kA_rho;           /* density-dependent k_A */
   double kA_lo, kA_hi;      /* k_A at the lowest and at the highest cell density */
+  int32_t remit_random;     /* re-emit from a point uniform over the cell volume */
   double T_min, T_max;      /* reporting range of the temperatures */
   uint32_t model_id;
   uint64_t max_events;      /* per package; 0 = 1e8 */
@@ -296,6 +302,13 @@ double orc_hg_pdf2(double g, double mu)
 {
   double q = 1.0 + g * g - 2.0 * g * mu;
   return (1.0 - g * g) / (q * sqrt(q));
+}
+
+/* Radius of a point uniform over the volume of the shell [ri, ro]. */
+double orc_shell_radius(double ri, double ro, double u)
+{
+  double a = ri * ri * ri, b = ro * ro * ro;
+  return cbrt(a + u * (b - a));
 }
 
 /* Free-path weight of Eq. 8 for a path tau drawn from k e^(-k tau). */
@@ -573,6 +586,18 @@ static int do_absorb(orc_ctx *C, orc_pkg *p, orc_stream *rs, int s)
     fn = sample_cdf(F, C->cdf_frozen + (size_t)c * F, u_nu);
   }
   p->f = fn;
+  if (M->remit_random) {
+    double u_r, u_spare;
+    draw2(rs, &u_r, &u_spare);
+    (void)u_spare;
+    double rn = orc_shell_radius(M->radii[c], M->radii[c + 1], u_r);
+    double xr = sqrt(dot3(p->x, p->x));
+    if (xr > 0.0) {
+      for (int i = 0; i < 3; ++i) p->x[i] *= rn / xr;
+    } else {
+      p->x[0] = 0.0; p->x[1] = 0.0; p->x[2] = rn;
+    }
+  }
   draw2(rs, &u_mu, &u_phi);
   double phi = 2.0 * ORC_PI * u_phi;
   double e1[3], e2[3];

@@ -52,6 +52,7 @@ class _Model(ctypes.Structure):
         ("g_E", ctypes.c_double), ("scat_w", ctypes.c_int32), ("g_S", ctypes.c_double),
         ("k_A", ctypes.c_double), ("k_S", ctypes.c_double),
         ("kA_rho", ctypes.c_int32), ("kA_lo", ctypes.c_double), ("kA_hi", ctypes.c_double),
+        ("remit_random", ctypes.c_int32),
         ("T_min", ctypes.c_double), ("T_max", ctypes.c_double),
         ("model_id", ctypes.c_uint32), ("max_events", ctypes.c_uint64),
     ]
@@ -84,6 +85,8 @@ def lib():
         L.orc_path_weight.argtypes = [ctypes.c_double, ctypes.c_double]
         L.orc_path_weight.restype = ctypes.c_double
         L.orc_kA_cells.argtypes = [_P(_Model), _dp, _dp]
+        L.orc_shell_radius.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        L.orc_shell_radius.restype = ctypes.c_double
         L.orc_validate.argtypes = [_P(_Model)]
         L.orc_source_luminosity.argtypes = [_P(_Model), _dp]
         L.orc_cell_mass.argtypes = [_P(_Model), _dp]
@@ -120,6 +123,7 @@ class _Bound:
             g_S=float(getattr(m, "g_S", 0.0)), k_A=float(getattr(m, "k_A", 1.0)),
             k_S=float(getattr(m, "k_S", 1.0)), kA_rho=int(bool(getattr(m, "kA_rho", False))),
             kA_lo=float(getattr(m, "kA_lo", 3.0)), kA_hi=float(getattr(m, "kA_hi", 1.0)),
+            remit_random=int(bool(getattr(m, "remit_random", False))),
             T_min=float(T_min), T_max=float(T_max),
             model_id=int(model_id), max_events=int(max_events))
 
@@ -150,6 +154,11 @@ def kA_cells(m) -> tuple:
     v = ctypes.c_double(0.0)
     lib().orc_kA_cells(ctypes.byref(b.s), _ptr(out), ctypes.byref(v))
     return out, v.value
+
+
+def shell_radius(ri: float, ro: float, u: float) -> float:
+    """Radius of a point uniform over the volume of the shell [ri, ro]."""
+    return lib().orc_shell_radius(float(ri), float(ro), float(u))
 
 
 def u01(a: int, b: int) -> float:

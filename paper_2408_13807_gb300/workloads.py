@@ -52,6 +52,7 @@ class CloudModel:
     scat_w      scattering direction weighting on, with HG parameter g_S.
     k_A, k_S    free-path weighting factors (1 = none); kA_rho: k_A per cell,
                 linear in log density from kA_lo (lowest) to kA_hi (highest).
+    remit_random  re-emit from a point uniform over the absorbing cell's volume.
     """
 
     name: str
@@ -75,6 +76,7 @@ class CloudModel:
     kA_rho: bool = False
     kA_lo: float = 3.0
     kA_hi: float = 1.0
+    remit_random: bool = False
 
     @property
     def n_cells(self) -> int:

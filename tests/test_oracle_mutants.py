@@ -60,6 +60,9 @@ MUTANTS = {
     # Eq. 8 weight not applied to the absorption path
     "path_weight_unused": ("  if (kA != 1.0) p->w *= orc_path_weight(kA, p->tauA);\n", "\n",
                            "test_free_path_weighting_is_unbiased", {"kw": {"k_A": 2.5}}),
+    # re-emission radius uniform in r instead of in volume
+    "remit_radius_linear": ("  return cbrt(a + u * (b - a));", "  return ri + u * (ro - ri);",
+                            "test_shell_radius_is_uniform_in_volume", {}),
     # density-dependent k_A running the wrong way
     "kA_rho_reversed": ("kA[i] = M->kA_hi + (M->kA_lo - M->kA_hi) * (lmax - log(M->rho[i])) / (lmax - lmin);",
                         "kA[i] = M->kA_lo + (M->kA_hi - M->kA_lo) * (lmax - log(M->rho[i])) / (lmax - lmin);",

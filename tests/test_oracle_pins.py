@@ -397,3 +397,32 @@ def test_neutral_weighting_parameters_are_the_unweighted_run(oracle):
     assert np.array_equal(a["hash"], b["hash"]) and np.array_equal(a["T"], b["T"])
     c = oracle.run(m.replace(scat_w=True, g_S=0.0), 500, 3, record=True)
     assert not np.array_equal(a["hash"], c["hash"])
+
+
+# ------------------------------------- randomised re-emission point (Sect. 4)
+def test_shell_radius_is_uniform_in_volume(oracle):
+    """Radius of a point uniform over a shell's volume: the mean radius of a
+    full sphere is 3/4 R, and r^3 is uniform between the shell's cubes."""
+    x, wq = np.polynomial.legendre.leggauss(200)
+    u = 0.5 * (x + 1.0)
+    r = np.array([oracle.shell_radius(0.0, 2.0, uu) for uu in u])
+    assert 0.5 * np.sum(wq * r) == pytest.approx(1.5, rel=1e-5)  # cbrt is singular at 0: slow quadrature
+    for ri, ro, uu in ((0.3, 0.7, 0.25), (1e-3, 2e-3, 0.9)):
+        rr = oracle.shell_radius(ri, ro, uu)
+        assert (rr ** 3 - ri ** 3) / (ro ** 3 - ri ** 3) == pytest.approx(uu, rel=1e-12)
+
+
+def test_randomised_reemission_keeps_the_grey_invariant(oracle):
+    """In the isotropic-field solution of grey absorption + re-emission the
+    absorption points are uniform over each cell's volume, so re-emitting from
+    a uniform point of the cell leaves the mean number of absorptions per
+    package at sum_c kabs_c V_c / (pi R^2) (the invariant pinned above)."""
+    m = W.grey_model(4, 0.9, albedo=0.0, r_in=0.2).replace(rho=np.array([2.5, 0.5, 1.2, 0.8]), remit_random=True)
+    N = 60_000
+    r = oracle.run(m, N, 8, mode="frozen", T_frozen=np.full(4, 30.0), record=True)
+    n_abs = r["n_events"][:, 1].astype(np.float64)
+    expect = CF.pure_scatterer_mean_events(m.radii, m.kabs[0] * m.rho)
+    assert abs(n_abs.mean() - expect) < 4.5 * n_abs.std() / np.sqrt(N)
+    base = oracle.run(m.replace(remit_random=False), 2_000, 8, mode="frozen", T_frozen=np.full(4, 30.0), record=True)
+    other = oracle.run(m, 2_000, 8, mode="frozen", T_frozen=np.full(4, 30.0), record=True)
+    assert not np.array_equal(base["hash"], other["hash"])  # the option really acts
