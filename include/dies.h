@@ -155,6 +155,9 @@ typedef struct {
                                     k_A_low_density (lowest shell density; also the
                                     void and empty shells) to k_A_high_density (highest) */
   double k_A_low_density, k_A_high_density;
+  int reemit_uniform_in_cell;    /* 1: re-emit from a point uniform over the absorbing
+                                    shell's volume instead of the absorption point (the
+                                    test variant discussed in Sect. 4; not a weighting) */
 } dies_weighting;
 
 /* Sets every weighting option at once (see dies_weighting).  Errors:

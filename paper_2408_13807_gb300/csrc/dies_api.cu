@@ -109,7 +109,7 @@ struct Problem {
   double k_bg = 0.5;
   int ffi = 0;
   double g_E = 0.0, g_S = 0.0, k_A = 1.0, k_S = 1.0, kA_lo = 3.0, kA_hi = 1.0;
-  int scat_w = 0, kA_rho = 0;
+  int scat_w = 0, kA_rho = 0, remit_random = 0;
   int prec = PREC_MIXED, n_batches = 1;
   double fp64_radius = 0.0;
   double T_min = 2.7, T_max = 1500.0;
@@ -424,6 +424,8 @@ struct Problem {
     P.g_S_f = (float)g_S;
     P.k_S_f = (float)k_S;
     P.kA_void_f = (float)P.kA_void;
+    P.remit_random = remit_random;
+    P.radii_d = at<double>(lay.radii);
     P.kbg_plain = (k_bg == 0.5);
     P.r64 = (prec == PREC_MIXED && fp64_radius > 0.0);
     P.batch_min = rare_batch;
@@ -863,6 +865,7 @@ static int set_weighting_ex(Problem &p, const dies_weighting *w) {
   p.kA_rho = w->k_A_density ? 1 : 0;
   p.kA_lo = w->k_A_low_density;
   p.kA_hi = w->k_A_high_density;
+  p.remit_random = w->reemit_uniform_in_cell ? 1 : 0;
   p.tables_valid = false;
   return DIES_OK;
 }

@@ -129,6 +129,8 @@ struct TransportParams {
   const float *kA_f;        // per cell k_A (FP32 forms)
   double kA_void;
   float g_E_f, g_S_f, k_S_f, kA_void_f;
+  int remit_random;         // re-emit from a point uniform over the absorbing cell
+  const double *radii_d;    // boundary radii (length units), boundary index cell_off + model + c
   int mode;
   unsigned long long max_events;
   unsigned long long time_budget_ns;

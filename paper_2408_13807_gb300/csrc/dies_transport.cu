@@ -786,6 +786,15 @@ __device__ __forceinline__ void absorb(const TransportParams &P, Shared &S, cons
       f = cdf_pick_ldg(P.dcdf_d + ((size_t)row << kFreqShift), u_nu);
     }
     set_freq<PREC>(S, L, f);
+    double rn = -1.0;  // re-emission radius; < 0: the absorption point
+    if (P.remit_random) {
+      // a point uniform over the cell's volume (the test variant of Sect. 4)
+      const U4 e = draw<PREC>(S, L);
+      const int bi = L.cell_off + L.model + L.cell;
+      const double ri = __ldg(P.radii_d + bi), ro = __ldg(P.radii_d + bi + 1);
+      const double a3 = ri * ri * ri;
+      rn = cbrt(a3 + u01d(e.x, e.y) * (ro * ro * ro - a3));
+    }
     const U4 b = draw<PREC>(S, L);
     double mu;
     if (P.g_E != 0.0) {
@@ -797,8 +806,8 @@ __device__ __forceinline__ void absorb(const TransportParams &P, Shared &S, cons
     } else {
       mu = 2.0 * u01d(b.x, b.y) - 1.0;
     }
-    const double r2 = L.p2 + L.s * L.s;
-    const double r = sqrt(r2);
+    const double r2 = (rn >= 0.0) ? rn * rn : L.p2 + L.s * L.s;
+    const double r = (rn >= 0.0) ? rn : sqrt(r2);
     L.s = r * mu;
     L.p2 = fmax(r2 - L.s * L.s, 0.0);
     const U4 c = draw<PREC>(S, L);
@@ -846,8 +855,17 @@ __device__ __forceinline__ void absorb(const TransportParams &P, Shared &S, cons
     if (eo + de > sLnode[P.n_tnodes - 1]) atomicAdd(&S.rare[CNT_CLAMP_HI], 1u);
     const int row = min(j, P.n_tnodes - 1);
     set_freq<PREC>(S, L, alias_pick_ldg(P.dalias + ((size_t)row << kFreqShift), a.y >> 9));
-    const float r2 = L.p2 + L.s * L.s;
-    const float r = sqrtf(r2);
+    float r2 = L.p2 + L.s * L.s;
+    float r = sqrtf(r2);
+    if (P.remit_random) {
+      // a point uniform over the cell's volume (the test variant of Sect. 4)
+      const U4 e = draw<PREC>(S, L);
+      const int bi = L.cell_off + L.model + L.cell;
+      const float ri2 = __ldg(P.r2f + bi), ro2 = __ldg(P.r2f + bi + 1);
+      const float a3 = ri2 * sqrtf(ri2);
+      r = cbrtf(fmaf(u01f_word(e.x), ro2 * sqrtf(ro2) - a3, a3));
+      r2 = r * r;
+    }
     if (P.g_E_f != 0.0f) {
       // Eq. 6: cosine to the reference direction from HG(g_E)
       float mr, sr2;

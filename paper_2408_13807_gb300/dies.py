@@ -79,7 +79,7 @@ class dies_weighting(ctypes.Structure):
         ("k_bg", ctypes.c_double), ("forced_first_interaction", ctypes.c_int), ("g_E", ctypes.c_double),
         ("scatter_weighting", ctypes.c_int), ("g_S", ctypes.c_double), ("k_A", ctypes.c_double),
         ("k_S", ctypes.c_double), ("k_A_density", ctypes.c_int), ("k_A_low_density", ctypes.c_double),
-        ("k_A_high_density", ctypes.c_double),
+        ("k_A_high_density", ctypes.c_double), ("reemit_uniform_in_cell", ctypes.c_int),
     ]
 
 
@@ -89,7 +89,7 @@ def weighting_of(cloud) -> dies_weighting:
         k_bg=float(cloud.k_bg), forced_first_interaction=int(bool(cloud.ffi)), g_E=float(cloud.g_E),
         scatter_weighting=int(bool(cloud.scat_w)), g_S=float(cloud.g_S), k_A=float(cloud.k_A), k_S=float(cloud.k_S),
         k_A_density=int(bool(cloud.kA_rho)), k_A_low_density=float(cloud.kA_lo),
-        k_A_high_density=float(cloud.kA_hi))
+        k_A_high_density=float(cloud.kA_hi), reemit_uniform_in_cell=int(bool(cloud.remit_random)))
 
 
 class dies_peaks(ctypes.Structure):

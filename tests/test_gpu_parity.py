@@ -42,6 +42,9 @@ FROZEN_CASES = {
     "weighted_point_kA_rho": lambda: W.point_source_cloud(24, 1e-3, 20.0).replace(g_E=-0.3, kA_rho=True),
     "weighted_all_ffi": lambda: W.external_cloud(12, 0.8, ffi=True, k_bg=1.0 / 3.0).replace(
         g_E=0.4, scat_w=True, g_S=-0.2, k_A=1.5),
+    # re-emission from a point uniform over the cell (the test variant of Sect. 4)
+    "remit_uniform_point": lambda: W.point_source_cloud(16, 1e-2, 30.0).replace(remit_random=True),
+    "remit_uniform_grey": lambda: W.grey_model(6, 4.0, albedo=0.3, g=0.5, r_in=0.1).replace(remit_random=True),
 }
 
 
@@ -320,3 +323,15 @@ def test_density_dependent_kA_matches_oracle(D, oracle):
     Tg = np.array([m.run(N, seed=s).temperatures() for s in range(16)])
     To = np.array([r["T"] for r in oracle.run_seeds(cloud, N, range(500, 516))])
     assert_ensembles_agree(Tg, To, 0.01, min_gated=cloud.n_cells // 2)
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp32"])
+def test_randomised_reemission_point_matches_oracle(D, oracle, prec):
+    cloud = W.point_source_cloud(32, 1e-2, 50.0).replace(remit_random=True)
+    N = 1_000_000
+    m = D.Model(cloud, precision=prec, n_batches=50 if prec == "fp32" else 1)
+    Tg = np.array([m.run(N, seed=s).temperatures() for s in range(16)])
+    To = np.array([r["T"] for r in oracle.run_seeds(cloud, N, range(600, 616))])
+    assert_ensembles_agree(Tg, To, 0.01, min_gated=cloud.n_cells // 2)
+    st = m.stats()
+    assert st["E_escaped"] + st["E_lost"] == pytest.approx(st["E_injected"], rel=1e-6)
