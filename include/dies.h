@@ -299,6 +299,9 @@ int dies_batch_set_launch(dies_batch *b, int block_size, int blocks_per_sm, int 
 /* Weighting for all models of the batch (as dies_set_weighting_ex; with
  * k_A_density the density range is each model's own). */
 int dies_batch_set_weighting(dies_batch *b, const dies_weighting *w);
+/* Precision form of the batch (as dies_set_precision; the N_B batches of the
+ * FP32 form then split every model's packages). */
+int dies_batch_set_precision(dies_batch *b, int mode, int n_batches, double fp64_radius);
 /* Graph mode for the batch, as dies_set_graph. */
 int dies_batch_set_graph(dies_batch *b, int enable);
 int dies_run_batch(dies_batch *b, uint64_t n_packages_per_model, uint64_t seed);

@@ -875,18 +875,26 @@ int dies_set_weighting_ex(dies_model *m, const dies_weighting *w) {
   return set_weighting_ex(m->p, w);
 }
 
-int dies_set_precision(dies_model *m, int mode, int n_batches, double fp64_radius) {
-  if (!m) return fail(DIES_EINVAL, "model is NULL");
+static int set_precision(Problem &p, int mode, int n_batches, double fp64_radius) {
   if (mode != DIES_PREC_MIXED && mode != DIES_PREC_FP32 && mode != DIES_PREC_FP64)
     return fail(DIES_EINVAL, "unknown precision mode %d", mode);
   if (n_batches < 1 || n_batches > 1000000) return fail(DIES_EINVAL, "n_batches must be in [1, 1e6]");
   if (!(fp64_radius >= 0.0 && fp64_radius <= 1.0)) return fail(DIES_EINVAL, "fp64_radius must lie in [0, 1]");
-  m->p.prec = mode;
-  m->p.n_batches = n_batches;
-  if (m->p.fp64_radius != fp64_radius) m->p.tables_valid = false;
-  m->p.fp64_radius = fp64_radius;
-  m->p.tables_valid = false;
+  p.prec = mode;
+  p.n_batches = n_batches;
+  p.fp64_radius = fp64_radius;
+  p.tables_valid = false;
   return DIES_OK;
+}
+
+int dies_set_precision(dies_model *m, int mode, int n_batches, double fp64_radius) {
+  if (!m) return fail(DIES_EINVAL, "model is NULL");
+  return set_precision(m->p, mode, n_batches, fp64_radius);
+}
+
+int dies_batch_set_precision(dies_batch *b, int mode, int n_batches, double fp64_radius) {
+  if (!b) return fail(DIES_EINVAL, "batch is NULL");
+  return set_precision(b->p, mode, n_batches, fp64_radius);
 }
 
 int dies_set_tgrid(dies_model *m, double T_min, double T_max, int n_nodes) {

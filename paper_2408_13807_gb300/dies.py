@@ -43,7 +43,7 @@ EXPORTS = (
     "dies_set_workspace", "dies_run", "dies_run_async", "dies_get_temperatures", "dies_get_absorbed",
     "dies_get_escaping_sed", "dies_get_stats", "dies_run_frozen", "dies_destroy_model", "dies_create_batch",
     "dies_batch_set_dust", "dies_batch_set_sources", "dies_batch_set_stream", "dies_batch_set_launch",
-    "dies_batch_set_graph", "dies_batch_set_weighting",
+    "dies_batch_set_graph", "dies_batch_set_weighting", "dies_batch_set_precision",
     "dies_run_batch", "dies_run_batch_async", "dies_batch_get_temperatures", "dies_batch_get_escaping_sed",
     "dies_batch_get_stats", "dies_destroy_batch", "dies_last_error", "dies_launch_count", "dies_version",
     "dies_measure_peaks",
@@ -132,6 +132,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "dies_set_graph": (i, [_vp, i]),
         "dies_set_weighting_ex": (i, [_vp, _vp]),
         "dies_batch_set_weighting": (i, [_vp, _vp]),
+        "dies_batch_set_precision": (i, [_vp, i, i, d]),
         "dies_batch_set_graph": (i, [_vp, i]),
         "dies_workspace_bytes": (i, [_vp, _P(ctypes.c_size_t)]),
         "dies_set_workspace": (i, [_vp, _vp, ctypes.c_size_t]),
@@ -232,6 +233,10 @@ def dies_set_weighting_ex(h, w: dies_weighting):
 
 def dies_batch_set_weighting(h, w: dies_weighting):
     return _check(load().dies_batch_set_weighting(h, ctypes.byref(w)))
+
+
+def dies_batch_set_precision(h, mode: int, n_batches: int = 1, fp64_radius: float = 0.0):
+    return _check(load().dies_batch_set_precision(h, int(mode), int(n_batches), float(fp64_radius)))
 
 
 def dies_set_graph(h, enable: bool):
@@ -465,7 +470,8 @@ class Batch:
     spectrum) in one persistent launch."""
 
     def __init__(self, clouds, block_size: int = 256, blocks_per_sm: int = 0, rare_batch: int = 16,
-                 inner_moves: int = 32, aggregate_atomics: int = 0, graph: bool = False):
+                 inner_moves: int = 32, aggregate_atomics: int = 0, graph: bool = False,
+                 precision: str = "mixed", n_batches: int = 1):
         c0 = clouds[0]
         n = np.array([c.n_cells for c in clouds], dtype=np.int32)
         self.offsets = np.concatenate([[0], np.cumsum(n)]).astype(np.int32)
@@ -483,6 +489,7 @@ class Batch:
         dies_batch_set_launch(self.h, block_size, blocks_per_sm, rare_batch, inner_moves, aggregate_atomics)
         dies_batch_set_graph(self.h, graph)
         dies_batch_set_weighting(self.h, weighting_of(c0))
+        dies_batch_set_precision(self.h, PREC[precision], n_batches)
 
     def set_stream(self, stream_handle: int):
         dies_batch_set_stream(self.h, stream_handle)

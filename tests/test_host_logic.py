@@ -77,3 +77,12 @@ def test_bench_reference_arm_runs_on_cpu():
     line = json.loads(out.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == "packages/s"
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_noise_profile_statistics():
+    from paper_2408_13807_gb300 import noise
+    T = np.array([[10.0, 20.0], [12.0, 20.0], [14.0, 20.0]])
+    p = noise.noise_profile(T, reference=np.array([11.0, 25.0]))
+    assert p["mean_T"] == [12.0, 20.0]
+    assert p["rel_noise"][0] == pytest.approx(2.0 / 12.0) and p["rel_noise"][1] == 0.0
+    assert p["rel_error_of_mean"] == pytest.approx([1.0 / 11.0, 0.2])
