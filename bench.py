@@ -36,9 +36,12 @@ N_PER_RUN = 100_000_000
 L2_FLUSH_BYTES = 256 << 20
 
 # Algorithmic thread-level operations per event (minimum instruction counts of
-# the method's arithmetic, derived in the design doc): boundary crossing, scattering
-# (one Philox4x32-10 block + HG + rotation), absorption (one Philox block, FP64
-# atomic, table searches, isotropic re-emission) and per-package injection/exit.
+# the method's arithmetic): boundary crossing 20 (record load, compensated
+# R^2 - p^2, square root, step, column product and compare, cell update),
+# scattering 120 (one Philox4x32-10 block of ~80 integer operations, HG
+# inversion, azimuth, rotation), absorption 150 (one Philox block, FP64
+# atomic, table searches, isotropic re-emission, two logarithms) and
+# injection + exit 120 per package.
 OPS = {"crossed": 20, "scattered": 120, "absorbed": 150, "injected": 120}
 SM_COUNT = 152
 LANES_PER_SM = 128  # 4 schedulers x 32 lanes issue per cycle
