@@ -96,6 +96,7 @@ struct Lane {
   int next_ev;   // state at lim (ST_SCATTER or ST_ABSORB)
   int exit_st;   // state on leaving the cloud (ST_ESCAPE, or ST_FFIEND for the pre-walk)
   int cinc;      // 1 if the flight's crossings count as crossings (0 in the pre-walk)
+  int lo, span;  // FFI forms: the flight leaves when its next cell falls outside [lo, lo + span)
   Real ka, ks;   // absorption / scattering coefficient per unit density at the current frequency
   Real eps;      // package energy (erg/s)
   int cell, f, st, src, model, cell_off, gbase, n, n64;
@@ -471,7 +472,7 @@ __device__ __forceinline__ void move(const TransportParams &P, Shared &S, Lane<t
         if (next >= L.n) L.st = ST_ESCAPE;
       } else {
         T.cross += L.cinc;
-        if (next >= L.n) L.st = L.exit_st;
+        if ((unsigned)(next - L.lo) >= (unsigned)L.span) L.st = L.exit_st;
       }
     }
     return;
@@ -546,6 +547,20 @@ __device__ __forceinline__ void assign(const TransportParams &P, Lane<typename R
     L.hash = 0xcbf29ce484222325ULL;
     L.nsca = L.nabs = L.ncross = 0;
   }
+}
+
+// FP32 forms: the shell holding the turning point r = p of the current
+// straight path (the largest boundary b with R_b^2 <= p^2; -1: the central
+// void), by bisection over the model's boundary squares.
+__device__ __forceinline__ int turning_shell(const TransportParams &P, const Lane<float> &L) {
+  const float *R2 = P.r2f + (L.cell_off + L.model);
+  if (L.p2 < __ldg(R2)) return -1;
+  int lo = 0, hi = L.n;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(R2 + mid) <= L.p2) lo = mid; else hi = mid - 1;
+  }
+  return lo;
 }
 
 // Start the package: frequency from the source CDF, free paths (Eq. 1),
@@ -650,9 +665,28 @@ __device__ __forceinline__ void inject(const TransportParams &P, Shared &S, Lane
     L.tau_int = u_int;  // holds u_int until the pre-walk has found tau0
     L.s0 = L.s;
     if constexpr (PREC != PREC_FP64) {
-      L.lim = __int_as_float(0x7f800000);  // the pre-walk runs to the surface
+      L.lim = __int_as_float(0x7f800000);  // the pre-walk never interacts
       L.exit_st = ST_FFIEND;
       L.cinc = 0;
+      L.lo = -1;
+      L.span = L.n + 1;  // point source: the radial path to the surface
+      L.next_ev = 0;     // 1: mirrored pre-walk
+      if (L.src == 0) {
+        // An external package's straight path is symmetric about its
+        // turning point r = p, so the pre-walk stops on entering the shell
+        // that holds the turning point and doubles the column (Sect. 2.2.3
+        // needs only the total tau0).
+        const int turn = turning_shell(P, L);
+        if (turn >= L.n - 1) {
+          // the whole chord, 2 R mu, lies in the outermost shell
+          L.acc = 2.0f * __ldg(P.rhoe + L.gbase + L.n - 1) * (-L.s);
+          L.st = ST_FFIEND;
+        } else {
+          L.lo = turn + 1;
+          L.span = L.n - turn - 1;
+          L.next_ev = 1;
+        }
+      }
     }
   } else {
     L.st = ST_NORMAL;
@@ -891,7 +925,20 @@ __device__ __forceinline__ void ffi_end(const TransportParams &P, Shared &S, Lan
                                         Tally &T) {
   using Real = typename RealOf<PREC>::T;
   const Real ke = L.ka + L.ks;  // per unit density
-  const Real tau0 = (PREC == PREC_FP64) ? L.acc : L.acc * ke;
+  Real col0 = L.acc, col_half = Real(0);
+  bool mirror = false;
+  if constexpr (PREC != PREC_FP64) {
+    // a mirrored pre-walk stopped on entering the turning shell (at s <= 0):
+    // column to the turning point = acc + rho (0 - s); the path's total twice that
+    mirror = (L.next_ev == 1) && L.cell < L.n;  // the turning shell may be the void (-1, density 0)
+    if (mirror) {
+      col_half = fmaf(__ldg(P.rhoe + L.gbase + L.cell), -L.s, L.acc);
+      col0 = 2.0f * col_half;
+    } else if (L.next_ev == 1) {
+      col0 = L.acc;  // rounding carried it through the turning shell: acc is the whole path
+    }
+  }
+  const Real tau0 = (PREC == PREC_FP64) ? L.acc : col0 * ke;
   Real q;
   if constexpr (PREC == PREC_FP64) q = -expm1(-tau0);
   else q = -expm1f(-tau0);
@@ -917,16 +964,26 @@ __device__ __forceinline__ void ffi_end(const TransportParams &P, Shared &S, Lan
     } else {
       // the forced depth as a column (ke > 0 since q > 0); kept strictly
       // below the pre-walk's column, which the replay reproduces exactly
+      // (the replay re-walks the path in FP32; the limit stays just short of
+      // the pre-walk's total so that the forced interaction happens)
       ti = -log1pf(-L.tau_int * q);
-      L.lim = fminf(__fdividef(ti, ke), L.acc * 0.99999905f);
+      L.lim = fminf(__fdividef(ti, ke), col0 * (mirror ? 0.99998474f : 0.99999905f));
       L.next_ev = (L.u_type * ke < L.ka) ? ST_ABSORB : ST_SCATTER;
       L.exit_st = ST_ESCAPE;
       L.cinc = 1;
+      L.lo = -1;
+      L.span = L.n + 1;
     }
     atomicAdd(&S.rare[CNT_FORCED], 1u);
-    L.s = L.s0;
-    L.cell = (L.src == 0) ? L.n - 1 : __ldg(&P.desc[L.model].point_cell);
-    L.acc = Real(0);
+    if (mirror && L.lim > col_half) {
+      // the forced point lies on the outbound half: replay from the turning point
+      L.s = Real(0);
+      L.acc = col_half;
+    } else {
+      L.s = L.s0;
+      L.cell = (L.src == 0) ? L.n - 1 : __ldg(&P.desc[L.model].point_cell);
+      L.acc = Real(0);
+    }
     L.st = ST_FORCED;
   }
 }
