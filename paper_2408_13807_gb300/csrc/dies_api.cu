@@ -45,7 +45,7 @@ cudaError_t launch_finalize(cudaStream_t st, int n_cells, const double *E, const
 cudaError_t launch_merge(cudaStream_t st, int n_cells, float *Eprev, float *Ecur);
 cudaError_t launch_tally(cudaStream_t st, int n_models, const ModelDesc *desc, unsigned long long n_per_source,
                          const unsigned long long *sed_q, const unsigned long long *inj_q,
-                         const unsigned long long *dir_q, double *sed, double *energies);
+                         const unsigned long long *dir_q, double *sed, double *energies, int rep);
 
 namespace {
 
@@ -194,9 +194,10 @@ struct Problem {
     L.Ecur = seg(nc * 4);
     L.T = seg(nc * 8);
     L.sed = seg(nm * kMaxFreq * 8);
-    L.sed_q = seg(nm * 2 * kMaxFreq * 8);
-    L.inj_q = seg(nm * 2 * 8);
-    L.dir_q = seg(nm * 2 * 8);
+    const size_t rp = (size_t)tally_replicas();
+    L.sed_q = seg(rp * nm * 2 * kMaxFreq * 8);
+    L.inj_q = seg(rp * nm * 2 * 8);
+    L.dir_q = seg(rp * nm * 2 * 8);
     L.freq = seg(kMaxFreq * 8);
     L.kabs = seg(kMaxFreq * 8);
     L.ksca = seg(kMaxFreq * 8);
@@ -222,6 +223,16 @@ struct Problem {
     L.seedw = seg(8);
     L.total = o;
     return L;
+  }
+
+  // Replicas of the batch tallies: enough that about 4096 model slots take
+  // the escapes of a few models (a power of two, at most 64; 1 for a single
+  // model, whose tallies live in shared memory).
+  int tally_replicas() const {
+    if (n_models <= 1) return 1;
+    int r = 1;
+    while (r < 64 && (long long)r * 2 * n_models <= 4096) r *= 2;
+    return r;
   }
 
   int source_mask_single() const { return (has_ext ? 1 : 0) | (L_point > 0.0 ? 2 : 0); }
@@ -379,6 +390,7 @@ struct Problem {
     P.sed_q = at<unsigned long long>(lay.sed_q);
     P.inj_q = at<unsigned long long>(lay.inj_q);
     P.dir_q = at<unsigned long long>(lay.dir_q);
+    P.rep = tally_replicas();
     P.E = at<double>(lay.E);
     P.Eprev = at<float>(lay.Eprev);
     P.Ecur = at<float>(lay.Ecur);
@@ -451,9 +463,10 @@ struct Problem {
     DIES_CUDA(cudaMemsetAsync(ws + lay.Eprev, 0, (size_t)n_cells * 4, st));
     DIES_CUDA(cudaMemsetAsync(ws + lay.Ecur, 0, (size_t)n_cells * 4, st));
     DIES_CUDA(cudaMemsetAsync(ws + lay.sed, 0, (size_t)n_models * kMaxFreq * 8, st));
-    DIES_CUDA(cudaMemsetAsync(ws + lay.sed_q, 0, (size_t)n_models * 2 * kMaxFreq * 8, st));
-    DIES_CUDA(cudaMemsetAsync(ws + lay.inj_q, 0, (size_t)n_models * 2 * 8, st));
-    DIES_CUDA(cudaMemsetAsync(ws + lay.dir_q, 0, (size_t)n_models * 2 * 8, st));
+    const size_t rp = (size_t)tally_replicas();
+    DIES_CUDA(cudaMemsetAsync(ws + lay.sed_q, 0, rp * n_models * 2 * kMaxFreq * 8, st));
+    DIES_CUDA(cudaMemsetAsync(ws + lay.inj_q, 0, rp * n_models * 2 * 8, st));
+    DIES_CUDA(cudaMemsetAsync(ws + lay.dir_q, 0, rp * n_models * 2 * 8, st));
     DIES_CUDA(cudaMemsetAsync(ws + lay.counters, 0, 16 * 8 + 0, st));
     DIES_CUDA(cudaMemsetAsync(ws + lay.energies, 0, 8 * 8, st));
     DIES_CUDA(cudaMemsetAsync(ws + lay.queue, 0, 2 * 8, st));
@@ -524,7 +537,7 @@ struct Problem {
     if (prec != PREC_FP64)
       DIES_CUDA(launch_tally(st, n_models, at<ModelDesc>(lay.desc), n, at<unsigned long long>(lay.sed_q),
                              at<unsigned long long>(lay.inj_q), at<unsigned long long>(lay.dir_q), at<double>(lay.sed),
-                             at<double>(lay.energies)));
+                             at<double>(lay.energies), tally_replicas()));
     DIES_CUDA(launch_finalize(st, n_cells, at<double>(lay.E), at<float>(lay.Eprev), at<float>(lay.Ecur),
                               prec == PREC_FP32, at<double>(lay.inv_mass), at<double>(lay.Lnode_d),
                               at<double>(lay.lnT), n_tnodes, at<double>(lay.T)));

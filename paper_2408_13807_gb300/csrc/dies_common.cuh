@@ -87,9 +87,12 @@ struct TransportParams {
   float *Ecur;              // FP32 form: current batch
   double *sed;              // [n_models][kMaxFreq] (FP64 form writes it directly)
   // FP32 forms: fixed-point tallies, 2^-24 package energies per unit
-  unsigned long long *sed_q;  // [n_models][2][kMaxFreq]
-  unsigned long long *inj_q;  // [n_models][2]
-  unsigned long long *dir_q;  // [n_models][2]
+  // fixed-point tallies of batches, in `rep` replicas (CTA b writes replica
+  // b % rep) so that few models do not serialise on a few addresses
+  unsigned long long *sed_q;  // [rep][n_models][2][kMaxFreq]
+  unsigned long long *inj_q;  // [rep][n_models][2]
+  unsigned long long *dir_q;  // [rep][n_models][2]
+  int rep;                    // power of two
   // per-frequency tables
   const double *kabs_d, *ksca_d, *g_d;
   const double *src_cdf_d;  // [2][kMaxFreq]

@@ -271,7 +271,8 @@ __device__ __forceinline__ void tally_sed(const TransportParams &P, Shared &S, L
   } else {
     const unsigned long long q = quanta(w);
     if (P.n_models == 1) smem_add64(&S.sed_lo[L.src][L.f], &S.sed_hi[L.src][L.f], q);
-    else atomicAdd(P.sed_q + ((size_t)L.model * 2 + L.src) * kMaxFreq + L.f, q);
+    else atomicAdd(P.sed_q + (((size_t)(blockIdx.x & (P.rep - 1)) * P.n_models + L.model) * 2 + L.src) * kMaxFreq + L.f,
+                   q);
   }
 }
 
@@ -647,7 +648,7 @@ __device__ __forceinline__ void inject(const TransportParams &P, Shared &S, Lane
   } else {
     const unsigned long long q = quanta(L.w);
     if (P.n_models == 1) smem_add64(&S.inj_lo[L.src], &S.inj_hi[L.src], q);
-    else atomicAdd(P.inj_q + (size_t)L.model * 2 + L.src, q);
+    else atomicAdd(P.inj_q + ((size_t)(blockIdx.x & (P.rep - 1)) * P.n_models + L.model) * 2 + L.src, q);
   }
   record<RECORD>(L, EV_INJECT, L.cell, L.f);
   L.w *= w_path;
@@ -948,7 +949,7 @@ __device__ __forceinline__ void ffi_end(const TransportParams &P, Shared &S, Lan
   } else {
     const unsigned long long dq = quanta(L.w * (1.0f - q));
     if (P.n_models == 1) smem_add64(&S.dir_lo[L.src], &S.dir_hi[L.src], dq);
-    else atomicAdd(P.dir_q + (size_t)L.model * 2 + L.src, dq);
+    else atomicAdd(P.dir_q + ((size_t)(blockIdx.x & (P.rep - 1)) * P.n_models + L.model) * 2 + L.src, dq);
   }
   L.w *= q;
   if (!(q > Real(0))) {
@@ -1197,15 +1198,26 @@ __global__ void __launch_bounds__(256) k_transport(const TransportParams P) {
 // (one block of 64 threads per model).
 __global__ void k_tally(const ModelDesc *desc, unsigned long long n_per_source, const unsigned long long *sed_q,
                         const unsigned long long *inj_q, const unsigned long long *dir_q, double *sed,
-                        double *energies) {
-  const int m = blockIdx.x, k = threadIdx.x;
+                        double *energies, int rep) {
+  const int m = blockIdx.x, k = threadIdx.x, nm = gridDim.x;
   const double unit = 1.0 / (double)kQuantum;
   const double e0 = desc[m].L[0] / (double)n_per_source, e1 = desc[m].L[1] / (double)n_per_source;
-  const unsigned long long *q = sed_q + (size_t)m * 2 * kMaxFreq;
-  sed[(size_t)m * kMaxFreq + k] = ((double)q[k] * e0 + (double)q[kMaxFreq + k] * e1) * unit;
+  unsigned long long s0 = 0, s1 = 0, i0 = 0, i1 = 0, d0 = 0, d1 = 0;  // integer sums over the replicas
+  for (int r = 0; r < rep; ++r) {
+    const size_t mr = (size_t)r * nm + m;
+    s0 += sed_q[mr * 2 * kMaxFreq + k];
+    s1 += sed_q[mr * 2 * kMaxFreq + kMaxFreq + k];
+    if (k == 0) {
+      i0 += inj_q[2 * mr];
+      i1 += inj_q[2 * mr + 1];
+      d0 += dir_q[2 * mr];
+      d1 += dir_q[2 * mr + 1];
+    }
+  }
+  sed[(size_t)m * kMaxFreq + k] = ((double)s0 * e0 + (double)s1 * e1) * unit;
   if (k == 0) {
-    const double inj = ((double)inj_q[2 * m] * e0 + (double)inj_q[2 * m + 1] * e1) * unit;
-    const double dir = ((double)dir_q[2 * m] * e0 + (double)dir_q[2 * m + 1] * e1) * unit;
+    const double inj = ((double)i0 * e0 + (double)i1 * e1) * unit;
+    const double dir = ((double)d0 * e0 + (double)d1 * e1) * unit;
     if (inj != 0.0) atomicAdd(energies + EN_INJECTED, inj);
     if (dir != 0.0) atomicAdd(energies + EN_DIRECT, dir);
   }
@@ -1327,8 +1339,8 @@ cudaError_t transport_occupancy(int prec, int mode, int block, int n_tnodes_pow2
 
 cudaError_t launch_tally(cudaStream_t st, int n_models, const ModelDesc *desc, unsigned long long n_per_source,
                          const unsigned long long *sed_q, const unsigned long long *inj_q,
-                         const unsigned long long *dir_q, double *sed, double *energies) {
-  k_tally<<<n_models, kMaxFreq, 0, st>>>(desc, n_per_source, sed_q, inj_q, dir_q, sed, energies);
+                         const unsigned long long *dir_q, double *sed, double *energies, int rep) {
+  k_tally<<<n_models, kMaxFreq, 0, st>>>(desc, n_per_source, sed_q, inj_q, dir_q, sed, energies, rep);
   launch_counter_add(1);
   return cudaGetLastError();
 }
