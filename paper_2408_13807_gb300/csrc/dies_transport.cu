@@ -1021,8 +1021,11 @@ __device__ __forceinline__ unsigned long long globaltimer() {
   return t;
 }
 
+// The FP32 forms are held to 48 registers (5 CTAs of 256 per SM): the
+// forced-interaction state would otherwise cost a CTA per SM, which is worth
+// more than the few spills in the rare-event path (measured).
 template <int PREC, int MODE, bool RECORD, int OPT>
-__global__ void __launch_bounds__(256) k_transport(const TransportParams P) {
+__global__ void __launch_bounds__(256, PREC == PREC_FP64 ? 1 : 5) k_transport(const TransportParams P) {
   using Real = typename RealOf<PREC>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Shared &S = *reinterpret_cast<Shared *>(smem_raw);
