@@ -26,7 +26,9 @@
  *   - direction weighting of background packages, mu = u^k_bg with weight
  *     2 k_bg mu^(2-1/k_bg) (Sect. 2.2.1, Eq. 5);
  *   - forced first interaction (Sect. 2.2.2, Eqs. 9-12), with the extinction
- *     optical depth (absorption + scattering) as the forced variable;
+ *     optical depth (absorption + scattering) as the forced variable, or
+ *     (the stronger variant named at the end of Sect. 2.2.2) the optical
+ *     depth of absorption only;
  *   - direction weighting of re-emission (Sect. 2.2.1, Eq. 6): the new
  *     direction from a Henyey-Greenstein function of parameter g_E about the
  *     reference direction (towards the centre for packages of the external
@@ -40,7 +42,7 @@
  *     the absorbing cell instead of the absorption point (the test variant
  *     of Sect. 4): r^3 uniform between the cell's inner and outer r^3, the
  *     angular position kept (irrelevant by symmetry);
- *   - free-path weighting (Sect. 2.2.3, Eq. 8): tau = -ln(u) / k with weight
+ *   - free-path weighting (Sect. 2.2.2, Eq. 8): tau = -ln(u) / k with weight
  *     e^(tau (k - 1)) / k, separately for absorption (k_A) and scattering
  *     (k_S); optionally k_A per cell, linear in log density from k_A_lo at the
  *     lowest cell density to k_A_hi at the highest;
@@ -54,7 +56,11 @@
  * B_k(T) dnu_k = E (no lookup table); the difference spectrum is the exact
  * kabs_k [B_k(T_new) - B_k(T_old)] dnu_k; the direct-escape fraction
  * e^-tau0 of a forced package is tallied in the escaping SED so that energy
- * is conserved exactly.
+ * is conserved exactly.  Forcing on the absorption depth alone: the
+ * scattering clock keeps its plain draw; only when it outlasts the whole
+ * first ray is the absorption forced inside the ray (weight 1 - e^-tau_A0,
+ * e^-tau_A0 tallied as a direct escape), otherwise the first flight is
+ * unforced -- this keeps the estimator unbiased with scattering.
  *
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror & Shaw 2011) keyed by
  * the 64-bit seed, counter (package lo, package hi, block index,
@@ -105,7 +111,7 @@ typedef struct {
   double L_point;           /* erg/s, 0 = no point source */
   const double *point_spec; /* n_freq L_nu shape, or NULL */
   double k_bg;              /* 0.5 = unweighted */
-  int32_t ffi;              /* forced first interaction */
+  int32_t ffi;              /* forced first interaction: 0 off, 1 on tau_ext, 2 on tau_A */
   double g_E;               /* re-emission direction weighting (Eq. 6); 0 = off */
   int32_t scat_w;           /* scattering direction weighting (Eq. 7) on */
   double g_S;               /* its HG parameter */
@@ -659,6 +665,24 @@ static double prewalk_tau(const orc_ctx *C, const orc_pkg *p0)
   return acc;
 }
 
+/* Absorption and scattering optical depths, summed separately, from the
+ * current point to the surface along the current direction. */
+static void prewalk_tau_split(const orc_ctx *C, const orc_pkg *p0, double *tauA0, double *tauS0)
+{
+  orc_pkg q = *p0;
+  double a = 0.0, b = 0.0;
+  while (q.cell < C->n) {
+    int next;
+    double l = boundary_distance(C, q.x, q.d, q.cell, &next);
+    a += kabs_cell(C, q.cell, q.f) * l;
+    b += ksca_cell(C, q.cell, q.f) * l;
+    move(&q, l);
+    q.cell = next;
+  }
+  *tauA0 = a;
+  *tauS0 = b;
+}
+
 static void simulate(orc_ctx *C, int s, uint64_t pkg, uint64_t seed, uint32_t *nev_out, uint64_t *hash_out)
 {
   const orc_model *M = C->M;
@@ -714,7 +738,7 @@ static void simulate(orc_ctx *C, int s, uint64_t pkg, uint64_t seed, uint32_t *n
   }
 
   /* ---- forced first interaction (Sect. 2.2.2, Eqs. 9-12) */
-  if (alive && M->ffi) {
+  if (alive && M->ffi == 1) {
     double u_int, u_type;
     draw2(&rs, &u_int, &u_type);
     double tau0 = prewalk_tau(C, &p);
@@ -757,6 +781,64 @@ static void simulate(orc_ctx *C, int s, uint64_t pkg, uint64_t seed, uint32_t *n
         p.events += 1;
         if (!do_cross(C, &p, next, l, s)) { alive = 0; break; }   /* unreachable in exact arithmetic */
       }
+    }
+  }
+
+  /* ---- forced first absorption (Sect. 2.2.2, the forced interaction on the
+   * optical depth of absorption only).  tau_S keeps its plain draw.  If it
+   * is at least the scattering depth tau_S0 of the whole first ray (the
+   * boundary wins ties), the package leaves the ray unscattered unless it is
+   * absorbed: the absorption depth is then drawn from the law conditioned on
+   * tau < tau_A0 (Eqs. 9-10 with tau_A0 for tau0), the package carries
+   * 1 - e^-tau_A0 (Eq. 12) and the rest escapes directly (tallied).  Else the
+   * flight runs unforced, with tau_A = -ln(1 - u_int). */
+  if (alive && M->ffi == 2) {
+    double u_int, u_unused;
+    draw2(&rs, &u_int, &u_unused);
+    double tauA0, tauS0;
+    prewalk_tau_split(C, &p, &tauA0, &tauS0);
+    if (p.tauS >= tauS0) {
+      double q = -expm1(-tauA0);
+      double e_direct = p.w * C->eps[s] * (1.0 - q);
+      C->sed[p.f] += e_direct;
+      C->st[ST_E_DIRECT] += e_direct;
+      C->st[ST_E_ESCAPED] += e_direct;
+      p.w *= q;
+      if (!(q > 0.0)) {
+        alive = 0;
+        C->st[ST_ESCAPED] += 1.0;
+      } else if (p.w < 1e-10) {
+        lose(C, &p, s, ST_KILL_WEIGHT);
+        alive = 0;
+      } else {
+        double tau_int = -log1p(-u_int * q);
+        if (tau_int > tauA0) tau_int = tauA0;
+        double acc = 0.0;
+        C->st[ST_FORCED] += 1.0;
+        for (;;) {
+          int next;
+          double l = boundary_distance(C, p.x, p.d, p.cell, &next);
+          double ka = kabs_cell(C, p.cell, p.f);
+          if (ka > 0.0 && acc + ka * l >= tau_int) {
+            double li = (tau_int - acc) / ka;
+            if (li > l) li = l;
+            if (li < 0.0) li = 0.0;
+            move(&p, li);
+            p.events += 1;
+            alive = do_absorb(C, &p, &rs, s);
+            if (alive && p.w < 1e-10) {
+              lose(C, &p, s, ST_KILL_WEIGHT);
+              alive = 0;
+            }
+            break;
+          }
+          acc += ka * l;
+          p.events += 1;
+          if (!do_cross(C, &p, next, l, s)) { alive = 0; break; }   /* unreachable in exact arithmetic */
+        }
+      }
+    } else {
+      p.tauA = -log1p(-u_int);
     }
   }
 
@@ -810,6 +892,7 @@ int orc_validate(const orc_model *M)
   if (!M->J_ext && !(M->L_point > 0.0)) return -6;
   if (M->L_point > 0.0 && !M->point_spec) return -6;
   if (!(M->k_bg > 0.0 && M->k_bg <= 1.0)) return -7;
+  if (M->ffi < 0 || M->ffi > 2) return -7;
   if (!(fabs(M->g_E) < 1.0) || !(fabs(M->g_S) < 1.0)) return -7;
   if (!(M->k_A > 0.0 && isfinite(M->k_A)) || !(M->k_S > 0.0 && isfinite(M->k_S))) return -7;
   if (M->kA_rho && !(M->kA_lo > 0.0 && isfinite(M->kA_lo) && M->kA_hi > 0.0 && isfinite(M->kA_hi))) return -7;
@@ -849,7 +932,7 @@ int orc_cell_mass(const orc_model *M, double *mass)
   return 0;
 }
 
-/* Absorption free-path weighting factor k_A per cell (Sect. 2.2.3): the
+/* Absorption free-path weighting factor k_A per cell (Sect. 2.2.2): the
  * constant k_A, or with density dependence linear in log density from k_A_lo
  * at the lowest positive cell density to k_A_hi at the highest; empty cells
  * and the central void take k_A_lo. */

@@ -118,7 +118,7 @@ class _Bound:
             radii=_ptr(a["radii"]), rho=_ptr(a["rho"]), length_unit_cm=float(m.length_unit_cm),
             freq=_ptr(a["freq"]), kabs=_ptr(a["kabs"]), ksca=_ptr(a["ksca"]), g=_ptr(a["g"]),
             J_ext=_ptr(a["J_ext"]), L_point=float(m.L_point), point_spec=_ptr(a["point_spec"]),
-            k_bg=float(m.k_bg), ffi=int(bool(m.ffi)),
+            k_bg=float(m.k_bg), ffi=int(m.ffi),
             g_E=float(getattr(m, "g_E", 0.0)), scat_w=int(bool(getattr(m, "scat_w", False))),
             g_S=float(getattr(m, "g_S", 0.0)), k_A=float(getattr(m, "k_A", 1.0)),
             k_S=float(getattr(m, "k_S", 1.0)), kA_rho=int(bool(getattr(m, "kA_rho", False))),

@@ -47,7 +47,9 @@ class CloudModel:
     L_point     central point-source luminosity in erg/s (0 = none).
     point_spec  float64[F] shape of the point-source L_nu (any scale) or None.
     k_bg        background-direction weighting mu = u^k_bg (0.5 = none).
-    ffi         forced first interaction.
+    ffi         forced first interaction: 0 off, 1 on the extinction optical
+                depth (Eqs. 9-12), 2 on the absorption optical depth only
+                (True / False read as 1 / 0).
     g_E         re-emission direction weighting, HG parameter (0 = none).
     scat_w      scattering direction weighting on, with HG parameter g_S.
     k_A, k_S    free-path weighting factors (1 = none); kA_rho: k_A per cell,
@@ -67,7 +69,7 @@ class CloudModel:
     L_point: float = 0.0
     point_spec: Optional[np.ndarray] = None
     k_bg: float = 0.5
-    ffi: bool = False
+    ffi: int = 0
     g_E: float = 0.0
     scat_w: bool = False
     g_S: float = 0.0
@@ -200,14 +202,14 @@ def _base(name, radii, rho, freq, length_unit_cm=0.1 * PC_CM):
 
 
 def external_cloud(n_shells: int, A_V: float, r0: float = 0.1, n_freq: int = 64,
-                   k_bg: float = 0.5, ffi: bool = False, name: Optional[str] = None) -> CloudModel:
+                   k_bg: float = 0.5, ffi: int = 0, name: Optional[str] = None) -> CloudModel:
     """Externally heated sphere, equal radial steps to R = 1, BE-like density
     normalised to the central visual extinction A_V."""
     freq = freq_grid(n_freq)
     radii = equal_radii(n_shells)
     rho = normalise_density(radii, be_like(radii, r0), A_V / AV_PER_TAU_V, kext_v())
     m = _base(name or f"ext_n{n_shells}_AV{A_V:g}", radii, rho, freq)
-    return m.replace(J_ext=isrf(freq), k_bg=float(k_bg), ffi=bool(ffi))
+    return m.replace(J_ext=isrf(freq), k_bg=float(k_bg), ffi=int(ffi))
 
 
 def point_source_cloud(n_shells: int, r_in: float, tau: float, lam_ref_um: float = LAMBDA_V_UM,
@@ -234,7 +236,7 @@ def config1() -> CloudModel:
 C2_AV = (1.0, 10.0, 100.0)
 # Direction weighting "toward the centre with exponent 2": p'(mu) ~ mu^2, i.e.
 # mu = u^(1/3) in the mu = u^k_bg family of Eq. (5).
-C2_VARIANTS = (("plain", 0.5, False), ("kbg", 1.0 / 3.0, False), ("ffi", 0.5, True))
+C2_VARIANTS = (("plain", 0.5, 0), ("kbg", 1.0 / 3.0, 0), ("ffi", 0.5, 1))
 
 
 def config2(A_V: float, variant: str = "plain") -> CloudModel:
@@ -260,7 +262,7 @@ def config5_external() -> CloudModel:
     radii = log_radii(1024, 1e-6)
     rho = normalise_density(radii, be_like(radii, 0.1), 0.1 / AV_PER_TAU_V, kext_v())
     m = _base("C5_ext_n1024_AV0.1_ffi", radii, rho, freq)
-    return m.replace(J_ext=isrf(freq), ffi=True)
+    return m.replace(J_ext=isrf(freq), ffi=1)
 
 
 def config5_internal(length_unit_cm: float = 10.0 * PC_CM) -> CloudModel:

@@ -29,7 +29,7 @@ MUTANTS = {
                            {"g": 0.6}),
     # inward flux of an isotropic field taken as J instead of pi J
     "external_flux_factor": ("L_out[0] = 4.0 * ORC_PI * ORC_PI * R * R * s;", "L_out[0] = 4.0 * ORC_PI * R * R * s;",
-                             "test_optically_thin_temperature", {}),
+                             "test_optically_thin_temperature", {"ffi": 1}),
     # re-emission from the new spectrum instead of the difference spectrum
     "no_difference_spectrum": ("pdiff[k] = bn - Bc[k];", "pdiff[k] = bn;",
                                "test_difference_spectrum_telescopes_to_final_emission", {}),
@@ -44,7 +44,7 @@ MUTANTS = {
                              "test_absorb_reemit_grey_isotropic_invariant", {}),
     # cell emission normalisation without the 4 pi
     "mass_no_4pi": ("mass[i] = 4.0 * ORC_PI * M->rho[i] * V * Lu2;", "mass[i] = M->rho[i] * V * Lu2;",
-                    "test_optically_thin_temperature", {}),
+                    "test_optically_thin_temperature", {"ffi": 1}),
     # Philox with one Weyl increment wrong
     "philox_key_bump": ("k1 += 0xBB67AE85u;", "k1 += 0xBB67AE84u;", "test_philox_known_answer_vectors", {}),
     # Eq. 7 weight inverted (sampling density over the dust density)
@@ -63,6 +63,19 @@ MUTANTS = {
     # re-emission radius uniform in r instead of in volume
     "remit_radius_linear": ("  return cbrt(a + u * (b - a));", "  return ri + u * (ro - ri);",
                             "test_shell_radius_is_uniform_in_volume", {}),
+    # forcing on the absorption depth applied when the ray is scattered
+    "ffi_abs_case_flipped": ("if (p.tauS >= tauS0) {", "if (p.tauS < tauS0) {",
+                             "test_forced_absorption_is_unbiased_with_scattering", {}),
+    # forcing on the absorption depth whatever the scattering clock says
+    "ffi_abs_scattering_ignored": ("if (p.tauS >= tauS0) {", "if (1) {",
+                                   "test_forced_absorption_is_unbiased_with_scattering", {}),
+    # Eq. 12 weight from the extinction depth while forcing an absorption
+    "ffi_abs_weight_extinction": ("double q = -expm1(-tauA0);", "double q = -expm1(-(tauA0 + tauS0));",
+                                  "test_forced_absorption_is_unbiased_with_scattering", {}),
+    # direct-escape part of the absorption forcing not tallied
+    "ffi_abs_no_direct_tally": ("      C->sed[p.f] += e_direct;\n      C->st[ST_E_DIRECT] += e_direct;\n"
+                                "      C->st[ST_E_ESCAPED] += e_direct;\n", "\n",
+                                "test_energy_conservation_ire", {}),
     # density-dependent k_A running the wrong way
     "kA_rho_reversed": ("kA[i] = M->kA_hi + (M->kA_lo - M->kA_hi) * (lmax - log(M->rho[i])) / (lmax - lmin);",
                         "kA[i] = M->kA_lo + (M->kA_hi - M->kA_lo) * (lmax - log(M->rho[i])) / (lmax - lmin);",
