@@ -128,11 +128,24 @@ int dies_set_dust(dies_model *m, const double *freq_hz, int n_freq, const double
  * At least one source is required.  Call after dies_set_dust. */
 int dies_set_sources(dies_model *m, const double *J_ext, double L_point, const double *point_spectrum);
 
+/* Forced first interaction modes (Sect. 2.2.2). */
+enum {
+  DIES_FFI_OFF = 0,
+  /* one interaction forced on the first flight with weight 1 - exp(-tau0),
+   * tau0 the extinction optical depth of the whole ray (Eqs. 9-12); the
+   * direct-escape part exp(-tau0) is tallied in the escaping SED */
+  DIES_FFI_EXTINCTION = 1,
+  /* the variant on the absorption optical depth only: a package whose plain
+   * scattering free path outlasts the whole first ray is absorbed inside it
+   * with weight 1 - exp(-tau_A0) (exp(-tau_A0) tallied as a direct escape);
+   * any other package makes an unforced first flight (unbiased with
+   * scattering) */
+  DIES_FFI_ABSORPTION = 2
+};
+
 /* Weighting (Sect. 2.2): background directions mu = u^k_bg with package
  * weight 2 k_bg mu^(2 - 1/k_bg) (Eq. 5), k_bg in (0, 1], 0.5 = unweighted;
- * forced_first_interaction != 0 forces one interaction on the first flight
- * with weight 1 - exp(-tau0) (Eqs. 9-12) and tallies the direct-escape part
- * exp(-tau0) in the escaping SED. */
+ * forced_first_interaction one of DIES_FFI_* (DIES_EINVAL otherwise). */
 int dies_set_weighting(dies_model *m, double k_bg, int forced_first_interaction);
 
 /* All weighting options of Sect. 2.2 (Table 1).  Directional weighting of
@@ -146,7 +159,7 @@ int dies_set_weighting(dies_model *m, double k_bg, int forced_first_interaction)
  * injected energy counts the source's share before any free-path weight). */
 typedef struct {
   double k_bg;                   /* Eq. 5, (0, 1], 0.5 = unweighted */
-  int forced_first_interaction;  /* Eqs. 9-12 on the extinction optical depth */
+  int forced_first_interaction;  /* DIES_FFI_*: Eqs. 9-12 on the extinction or the absorption depth */
   double g_E;                    /* Eq. 6, (-1, 1), 0 = isotropic re-emission (off) */
   int scatter_weighting;         /* Eq. 7 on (g_S = 0 is isotropic about the reference, not off) */
   double g_S;                    /* Eq. 7 parameter, (-1, 1) */

@@ -61,7 +61,7 @@ def config_class(cloud, precision: str) -> str:
     weighted = (getattr(cloud, "g_E", 0.0) != 0.0 or getattr(cloud, "scat_w", False) or
                 getattr(cloud, "k_A", 1.0) != 1.0 or getattr(cloud, "k_S", 1.0) != 1.0 or
                 getattr(cloud, "kA_rho", False))
-    return (f"{precision}|{kind}|n2^{n_bucket}|tau10^{tau_bucket}|kbg{cloud.k_bg:.3f}|ffi{int(bool(cloud.ffi))}"
+    return (f"{precision}|{kind}|n2^{n_bucket}|tau10^{tau_bucket}|kbg{cloud.k_bg:.3f}|ffi{int(cloud.ffi)}"
             + ("|w" if weighted else ""))
 
 

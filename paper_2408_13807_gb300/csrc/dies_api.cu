@@ -306,7 +306,7 @@ struct Problem {
 
   bool kA_weighting() const { return kA_rho || k_A != 1.0; }
 
-  // Absorption free-path factor per shell (Sect. 2.2.3): the constant k_A,
+  // Absorption free-path factor per shell (Sect. 2.2.2): the constant k_A,
   // or linear in log density from kA_lo at each model's lowest positive
   // shell density to kA_hi at its highest (empty shells: kA_lo).
   void kA_cells(std::vector<double> &out) const {
@@ -853,14 +853,17 @@ int dies_set_sources(dies_model *m, const double *J_ext, double L_point, const d
 int dies_set_weighting(dies_model *m, double k_bg, int ffi) {
   if (!m) return fail(DIES_EINVAL, "model is NULL");
   if (!(k_bg > 0.0 && k_bg <= 1.0)) return fail(DIES_EINVAL, "k_bg must lie in (0, 1]");
+  if (ffi < DIES_FFI_OFF || ffi > DIES_FFI_ABSORPTION) return fail(DIES_EINVAL, "unknown forced-interaction mode %d", ffi);
   m->p.k_bg = k_bg;
-  m->p.ffi = ffi ? 1 : 0;
+  m->p.ffi = ffi;
   return DIES_OK;
 }
 
 static int set_weighting_ex(Problem &p, const dies_weighting *w) {
   if (!w) return fail(DIES_EINVAL, "weighting is NULL");
   if (!(w->k_bg > 0.0 && w->k_bg <= 1.0)) return fail(DIES_EINVAL, "k_bg must lie in (0, 1]");
+  if (w->forced_first_interaction < DIES_FFI_OFF || w->forced_first_interaction > DIES_FFI_ABSORPTION)
+    return fail(DIES_EINVAL, "unknown forced-interaction mode %d", w->forced_first_interaction);
   if (!(std::fabs(w->g_E) < 1.0)) return fail(DIES_EINVAL, "g_E must lie in (-1, 1)");
   if (!(std::fabs(w->g_S) < 1.0)) return fail(DIES_EINVAL, "g_S must lie in (-1, 1)");
   if (!(w->k_A > 0.0 && std::isfinite(w->k_A)) || !(w->k_S > 0.0 && std::isfinite(w->k_S)))
@@ -869,7 +872,7 @@ static int set_weighting_ex(Problem &p, const dies_weighting *w) {
                           w->k_A_high_density > 0.0 && std::isfinite(w->k_A_high_density)))
     return fail(DIES_EINVAL, "k_A_low_density and k_A_high_density must be finite and > 0");
   p.k_bg = w->k_bg;
-  p.ffi = w->forced_first_interaction ? 1 : 0;
+  p.ffi = w->forced_first_interaction;
   p.g_E = w->g_E;
   p.scat_w = w->scatter_weighting ? 1 : 0;
   p.g_S = w->g_S;

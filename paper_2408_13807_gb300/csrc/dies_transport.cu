@@ -413,8 +413,10 @@ __device__ __forceinline__ double paths_d(const TransportParams &P, Lane<double>
 // PREWALK accumulates the extinction optical depth tau0 to the surface along
 // the first flight; FORCED replays the flight and stops where the cumulative
 // extinction reaches tau_int (Eq. 10), choosing absorption with probability
-// k_A / k_ext.  (FP64 form; the FP32 forms run both as ordinary flights of
-// the common move, see move.)
+// k_A / k_ext.  Forcing on the absorption depth (P.ffi == 2): the pre-walk
+// sums tau_A0 in acc and tau_S0 in u_type, and the forced flight runs on the
+// absorption depth alone and always absorbs.  (FP64 form; the FP32 forms run
+// both as ordinary flights of the common move, see move.)
 template <int PREC, int MODE, bool RECORD>
 __device__ __forceinline__ void move_forced(const TransportParams &P, Shared &S, Lane<double> &L, Tally &T) {
   using Real = double;
@@ -423,20 +425,25 @@ __device__ __forceinline__ void move_forced(const TransportParams &P, Shared &S,
   boundary<PREC, 0>(P, L, l, sb, next, rho);
   const Real ka = L.ka * rho, ks = L.ks * rho;
   if (L.st == ST_PREWALK) {
-    L.acc += (ka + ks) * l;
+    if (P.ffi == 2) {
+      L.acc += ka * l;
+      L.u_type += ks * l;
+    } else {
+      L.acc += (ka + ks) * l;
+    }
     L.s = sb;
     L.cell = next;
     if (next >= L.n) L.st = ST_FFIEND;
     return;
   }
   if constexpr (PREC == PREC_FP64) L.events++;
-  const Real ke = ka + ks;
+  const Real ke = (P.ffi == 2) ? ka : ka + ks;
   if (ke > Real(0) && L.acc + ke * l >= L.tau_int) {
     Real li = (L.tau_int - L.acc) / ke;
     li = li > l ? l : li;
     li = li < Real(0) ? Real(0) : li;
     L.s += li;
-    L.st = (L.u_type * ke < ka) ? ST_ABSORB : ST_SCATTER;
+    L.st = (P.ffi == 2 || L.u_type * ke < ka) ? ST_ABSORB : ST_SCATTER;
   } else {
     L.acc += ke * l;
     cross<PREC, RECORD>(P, S, L, T, sb, next);
@@ -606,7 +613,7 @@ __device__ __forceinline__ void inject(const TransportParams &P, Shared &S, Lane
     if (P.ffi) {
       const U4 c = draw<PREC>(S, L);
       u_int = u01d(c.x, c.y);
-      L.u_type = u01d(c.z, c.w);
+      L.u_type = (P.ffi == 2) ? 0.0 : u01d(c.z, c.w);  // forcing on tau_A: the pre-walk sums tau_S0 here
     }
   } else {
     set_freq<PREC>(S, L, alias_pick(S.src_alias[L.src], a.x >> 9));
@@ -639,7 +646,8 @@ __device__ __forceinline__ void inject(const TransportParams &P, Shared &S, Lane
     if (P.ffi) {
       const U4 c = draw<PREC>(S, L);
       u_int = u01f_word(c.x);
-      L.u_type = u01f_word(c.y);
+      // forcing on tau_A: u_type holds the column to the plain scattering point
+      L.u_type = (P.ffi == 2) ? -__logf(u01f_word(a.z)) * S.inv_ks_f[L.f] : u01f_word(c.y);
     }
   }
   atomicAdd(&S.rare[CNT_INJECTED], 1u);
@@ -675,7 +683,7 @@ __device__ __forceinline__ void inject(const TransportParams &P, Shared &S, Lane
       if (L.src == 0) {
         // An external package's straight path is symmetric about its
         // turning point r = p, so the pre-walk stops on entering the shell
-        // that holds the turning point and doubles the column (Sect. 2.2.3
+        // that holds the turning point and doubles the column (Sect. 2.2.2
         // needs only the total tau0).
         const int turn = turning_shell(P, L);
         if (turn >= L.n - 1) {
@@ -921,11 +929,17 @@ __device__ __forceinline__ void absorb(const TransportParams &P, Shared &S, cons
 // End of the forced-interaction pre-walk: tally the direct escape e^-tau0,
 // weight the rest by 1 - e^-tau0 (Eq. 12), draw the forced optical depth
 // (Eq. 10) and restart the first flight from the injection point.
+//
+// Forcing on the absorption depth (P.ffi == 2): only a package whose plain
+// scattering clock outlasts the whole first ray is forced, on tau_A0, and it
+// always absorbs; any other package restarts an unforced first flight with
+// tau_A = -ln(1 - u_int) (an exact split of the analog law given tau_S).
 template <int PREC, bool RECORD>
 __device__ __forceinline__ void ffi_end(const TransportParams &P, Shared &S, Lane<typename RealOf<PREC>::T> &L,
                                         Tally &T) {
   using Real = typename RealOf<PREC>::T;
-  const Real ke = L.ka + L.ks;  // per unit density
+  const bool on_abs = (P.ffi == 2);
+  const Real ke = on_abs ? L.ka : L.ka + L.ks;  // per unit density: the coefficient of the forced depth
   Real col0 = L.acc, col_half = Real(0);
   bool mirror = false;
   if constexpr (PREC != PREC_FP64) {
@@ -938,6 +952,34 @@ __device__ __forceinline__ void ffi_end(const TransportParams &P, Shared &S, Lan
     } else if (L.next_ev == 1) {
       col0 = L.acc;  // rounding carried it through the turning shell: acc is the whole path
     }
+  }
+  bool forced = true;
+  if (on_abs) {
+    if constexpr (PREC == PREC_FP64) forced = (L.tauS >= L.u_type);  // u_type: tau_S0 of the ray
+    else forced = !(L.u_type < col0);                                 // u_type: column to the scattering point
+  }
+  if (!forced) {
+    if constexpr (PREC == PREC_FP64) {
+      L.tauA = -log1p(-L.tau_int);
+    } else {
+      const float cA = -log1pf(-L.tau_int) * S.inv_ka_f[L.f];
+      L.lim = fminf(cA, L.u_type);
+      L.next_ev = (L.u_type < cA) ? ST_SCATTER : ST_ABSORB;
+      L.exit_st = ST_ESCAPE;
+      L.cinc = 1;
+      L.lo = -1;
+      L.span = L.n + 1;
+    }
+    if (mirror && L.lim > col_half) {
+      L.s = Real(0);
+      L.acc = col_half;
+    } else {
+      L.s = L.s0;
+      L.cell = (L.src == 0) ? L.n - 1 : __ldg(&P.desc[L.model].point_cell);
+      L.acc = Real(0);
+    }
+    L.st = ST_NORMAL;
+    return;
   }
   const Real tau0 = (PREC == PREC_FP64) ? L.acc : col0 * ke;
   Real q;
@@ -969,7 +1011,7 @@ __device__ __forceinline__ void ffi_end(const TransportParams &P, Shared &S, Lan
       // the pre-walk's total so that the forced interaction happens)
       ti = -log1pf(-L.tau_int * q);
       L.lim = fminf(__fdividef(ti, ke), col0 * (mirror ? 0.99998474f : 0.99999905f));
-      L.next_ev = (L.u_type * ke < L.ka) ? ST_ABSORB : ST_SCATTER;
+      L.next_ev = (on_abs || L.u_type * ke < L.ka) ? ST_ABSORB : ST_SCATTER;
       L.exit_st = ST_ESCAPE;
       L.cinc = 1;
       L.lo = -1;

@@ -28,6 +28,9 @@ DIES_ERANGE = -6
 DIES_PREC_MIXED = 0
 DIES_PREC_FP32 = 1
 DIES_PREC_FP64 = 2
+DIES_FFI_OFF = 0
+DIES_FFI_EXTINCTION = 1
+DIES_FFI_ABSORPTION = 2
 DIES_FROZEN_REEMIT = 0
 DIES_FROZEN_ABSORB_TERMINAL = 1
 DIES_MAX_FREQ = 64
@@ -86,7 +89,7 @@ class dies_weighting(ctypes.Structure):
 def weighting_of(cloud) -> dies_weighting:
     """The weighting options of a workloads.CloudModel as the C struct."""
     return dies_weighting(
-        k_bg=float(cloud.k_bg), forced_first_interaction=int(bool(cloud.ffi)), g_E=float(cloud.g_E),
+        k_bg=float(cloud.k_bg), forced_first_interaction=int(cloud.ffi), g_E=float(cloud.g_E),
         scatter_weighting=int(bool(cloud.scat_w)), g_S=float(cloud.g_S), k_A=float(cloud.k_A), k_S=float(cloud.k_S),
         k_A_density=int(bool(cloud.kA_rho)), k_A_low_density=float(cloud.kA_lo),
         k_A_high_density=float(cloud.kA_hi), reemit_uniform_in_cell=int(bool(cloud.remit_random)))
@@ -201,8 +204,9 @@ def dies_set_sources(h, J_ext, L_point: float, point_spectrum):
     return _check(load().dies_set_sources(h, _ptr(J), float(L_point), _ptr(sp)))
 
 
-def dies_set_weighting(h, k_bg: float, forced_first_interaction: bool):
-    return _check(load().dies_set_weighting(h, float(k_bg), int(bool(forced_first_interaction))))
+def dies_set_weighting(h, k_bg: float, forced_first_interaction: int):
+    """forced_first_interaction: DIES_FFI_* (True / False read as 1 / 0)."""
+    return _check(load().dies_set_weighting(h, float(k_bg), int(forced_first_interaction)))
 
 
 def dies_set_precision(h, mode: int, n_batches: int = 1, fp64_radius: float = 0.0):

@@ -44,6 +44,7 @@ def test_create_and_set_validate_inputs(lib):
         D.dies_set_dust(h, m.freq, m.kabs, m.ksca, m.g)
         D.dies_set_sources(h, m.J_ext, 0.0, None)
         D.dies_set_weighting(h, 1.0 / 3.0, True)
+        D.dies_set_weighting(h, 0.5, D.DIES_FFI_ABSORPTION)
         D.dies_set_precision(h, D.DIES_PREC_FP32, 50, 0.0)
         D.dies_set_tgrid(h, 2.7, 1500.0, 1024)
         D.dies_set_launch(h, 128, 0, 12, 4)
@@ -61,6 +62,9 @@ def test_create_and_set_validate_inputs(lib):
             lambda: D.dies_set_sources(h, -m.J_ext, 0.0, None),
             lambda: D.dies_set_weighting(h, 0.0, False),
             lambda: D.dies_set_weighting(h, 1.5, False),
+            lambda: D.dies_set_weighting(h, 0.5, 3),
+            lambda: D.dies_set_weighting(h, 0.5, -1),
+            lambda: D.dies_set_weighting_ex(h, D.weighting_of(m.replace(ffi=3))),
             lambda: D.dies_set_precision(h, 7, 1, 0.0),
             lambda: D.dies_set_precision(h, 1, 0, 0.0),
             lambda: D.dies_set_tgrid(h, 10.0, 5.0, 1024),

@@ -32,7 +32,10 @@ def D():
 FROZEN_CASES = {
     "C1_external": lambda: W.config1(),
     "kbg_third": lambda: W.external_cloud(24, 20.0, k_bg=1.0 / 3.0),
-    "ffi_thin": lambda: W.external_cloud(20, 0.3, ffi=True),
+    "ffi_thin": lambda: W.external_cloud(20, 0.3, ffi=1),
+    # forcing on the absorption depth (Sect. 2.2.2), thin and scattering-heavy
+    "ffi_abs_thin": lambda: W.external_cloud(20, 0.3, ffi=2),
+    "ffi_abs_grey_scatter": lambda: W.grey_model(6, 2.0, albedo=0.6, g=0.6, r_in=0.2).replace(ffi=2),
     "point_log_void": lambda: W.point_source_cloud(40, 1e-3, 30.0),
     "grey_void_scatter": lambda: W.grey_model(7, 3.0, albedo=0.6, g=0.7, r_in=0.2),
     "both_sources": lambda: W.external_cloud(12, 5.0).replace(L_point=W.L_SUN, point_spec=W.blackbody(W.freq_grid(), 6000.0)),
@@ -97,7 +100,8 @@ def test_ire_config1_matches_oracle_16_seeds(D, oracle, prec, agg):
 
 @pytest.mark.parametrize("prec", ["mixed", "fp64", "fp32"])
 def test_energy_conservation_and_counts(D, prec):
-    for cloud in (W.config1(), W.external_cloud(64, 30.0, k_bg=0.2), W.external_cloud(32, 0.5, ffi=True),
+    for cloud in (W.config1(), W.external_cloud(64, 30.0, k_bg=0.2), W.external_cloud(32, 0.5, ffi=1),
+                  W.external_cloud(32, 0.5, ffi=2),
                   W.point_source_cloud(64, 1e-3, 50.0)):
         m = D.Model(cloud, precision=prec, n_batches=4)
         m.run(200_000, seed=5)
@@ -334,4 +338,20 @@ def test_randomised_reemission_point_matches_oracle(D, oracle, prec):
     To = np.array([r["T"] for r in oracle.run_seeds(cloud, N, range(600, 616))])
     assert_ensembles_agree(Tg, To, 0.01, min_gated=cloud.n_cells // 2)
     st = m.stats()
+    assert st["E_escaped"] + st["E_lost"] == pytest.approx(st["E_injected"], rel=1e-6)
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp32"])
+def test_forced_absorption_matches_oracle(D, oracle, prec):
+    """Forcing on the absorption depth (Sect. 2.2.2) in the FP32 forms, with
+    the mirrored pre-walk and the unforced restart of scattered rays, against
+    the FP64 oracle with the same option."""
+    cloud = W.external_cloud(32, 0.5, ffi=2)
+    N = 1_000_000
+    m = D.Model(cloud, precision=prec, n_batches=50 if prec == "fp32" else 1)
+    Tg = np.array([m.run(N, seed=s).temperatures() for s in range(16)])
+    To = np.array([r["T"] for r in oracle.run_seeds(cloud, N, range(700, 716))])
+    assert_ensembles_agree(Tg, To, 0.01, min_gated=cloud.n_cells // 2)
+    st = m.stats()
+    assert st["status_word"] == 0
     assert st["E_escaped"] + st["E_lost"] == pytest.approx(st["E_injected"], rel=1e-6)
