@@ -75,7 +75,9 @@ CONFIGS = {
     "c1": W.config1,
     "c2": lambda: W.config2(10.0),
     "c2_kbg": lambda: W.config2(10.0, "kbg"),
+    "c2_av1": lambda: W.config2(1.0),
     "c2_ffi": lambda: W.config2(1.0, "ffi"),
+    "c2_ffi_abs": lambda: W.config2(1.0, "ffi").replace(ffi=2),
     "c3": W.config3,
     "c5e": W.config5_external,
 }

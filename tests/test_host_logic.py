@@ -49,6 +49,19 @@ def test_autotune_config_class_separates_what_matters():
     k = {autotune.config_class(m, "mixed") for m in W.config2_sweep()}
     assert len(k) == 9
     assert autotune.config_class(W.config1(), "mixed") != autotune.config_class(W.config1(), "fp32")
+    c = W.config2(1.0, "ffi")
+    assert autotune.config_class(c, "mixed") != autotune.config_class(c.replace(ffi=2), "mixed")
+
+
+def test_run_config_workloads_are_valid_models():
+    from paper_2408_13807_gb300 import run_config
+    for name, make in run_config.CONFIGS.items():
+        m = make()
+        assert m.n_cells >= 32 and np.all(np.diff(m.radii) > 0) and np.all(m.rho >= 0), name
+        assert m.n_sources >= 1
+    with pytest.raises(SystemExit) as e:
+        run_config.main(["--help"])
+    assert e.value.code == 0
 
 
 def test_autotune_uses_cache_without_gpu(tmp_path, monkeypatch):
