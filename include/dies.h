@@ -12,9 +12,10 @@
  * scattering (Eqs. 1 and 4); each absorption adds the package energy to its
  * shell, updates the shell temperature at once and re-emits the same energy
  * isotropically at a frequency drawn from the difference between the shell's
- * emission spectra at the new and old temperatures.  Optional weighting:
- * background directions mu = u^k_bg (Sect. 2.2.1, Eq. 5) and forced first
- * interaction (Sect. 2.2.2, Eqs. 9-12).
+ * emission spectra at the new and old temperatures.  Optional weighting
+ * (Sect. 2.2): background directions mu = u^k_bg (Eq. 5), directions of
+ * re-emission and scattering (Eqs. 6-7), free paths (Eq. 8) and a forced
+ * first interaction on the extinction or the absorption depth (Eqs. 9-12).
  *
  * Conventions shared by every call:
  *   - All array arguments are HOST pointers unless a name says otherwise.
@@ -91,7 +92,7 @@ typedef struct {
   double E_injected;      /* erg/s carried by injected packages (with weights) */
   double E_escaped;       /* erg/s leaving the model (SED total) */
   double E_lost;          /* erg/s of packages ended by the floor or the cap */
-  double E_direct;        /* erg/s of forced packages escaping without interaction */
+  double E_direct;        /* erg/s tallied as the direct-escape part of forced packages */
   double table_ms;        /* device time of the table build of this run (0 if cached) */
   double kernel_ms;       /* device time from the accumulator reset to the end of the temperature kernel */
   double transport_ms;    /* device time of the transport launch(es) alone */
