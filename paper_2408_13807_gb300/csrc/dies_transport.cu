@@ -290,6 +290,23 @@ __device__ __forceinline__ void lose(const TransportParams &P, Shared &S, Lane<R
   finish<RECORD>(P, L);
 }
 
+// FP32 forms: the reciprocal square root and the base-2 logarithm as the PTX
+// approximate instructions with denormal inputs flushed.  Every argument they
+// get is a normal number (d >= 1e-36 in boundary, uniforms >= 2^-24), for
+// which the flush changes nothing; it only spares the denormal handling
+// around the special-function instruction.
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+// -ln u of a uniform u in (0, 1), the free path of Eq. 1 (ln u = ln 2 log2 u)
+__device__ __forceinline__ float neg_ln_u(float u) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(u));
+  return y * -0.69314718f;
+}
+
 // ------------------------------------------------------------ geometry
 // Distance l to the boundary through which the package leaves its cell, the
 // path coordinate sb of that boundary, the cell entered there, and the
@@ -328,7 +345,7 @@ __device__ __forceinline__ void boundary(const TransportParams &P, const Lane<ty
     // signed on the way; a non-positive d (rounding at a tangent) counts as 1e-36
     const float d = fmaxf(inward ? d_in : (G.z - L.p2) + G.w, 1.0e-36f);
     next = inward ? c - 1 : c + 1;
-    sb = (inward ? -d : d) * rsqrtf(d);
+    sb = (inward ? -d : d) * rsqrt_ftz(d);
     if constexpr ((OPT & OPT_R64) != 0) {
       if ((unsigned)c < (unsigned)L.n64) {
         // optional FP64 crossing distance in the innermost shells
@@ -619,7 +636,7 @@ __device__ __forceinline__ void inject(const TransportParams &P, Shared &S, Lane
     set_freq<PREC>(S, L, alias_pick(S.src_alias[L.src], a.x >> 9));
     const float v = u01f_fine(a.y);  // 1 - u of the direction draw
     L.cell = (L.src == 0) ? L.n - 1 : __ldg(&D->point_cell);
-    w_path = set_paths(P, S, L, -__logf(u01f_word(a.z)), -__logf(u01f_word(a.w)));
+    w_path = set_paths(P, S, L, neg_ln_u(u01f_word(a.z)), neg_ln_u(u01f_word(a.w)));
     if (P.ffi) w_path = 1.0f;  // the forced flight replaces these paths
     if (L.src == 0) {
       const float Rf = __ldg(&D->Rf);
@@ -647,7 +664,7 @@ __device__ __forceinline__ void inject(const TransportParams &P, Shared &S, Lane
       const U4 c = draw<PREC>(S, L);
       u_int = u01f_word(c.x);
       // forcing on tau_A: u_type holds the column to the plain scattering point
-      L.u_type = (P.ffi == 2) ? -__logf(u01f_word(a.z)) * S.inv_ks_f[L.f] : u01f_word(c.y);
+      L.u_type = (P.ffi == 2) ? neg_ln_u(u01f_word(a.z)) * S.inv_ks_f[L.f] : u01f_word(c.y);
     }
   }
   atomicAdd(&S.rare[CNT_INJECTED], 1u);
@@ -756,7 +773,7 @@ __device__ __forceinline__ void scatter(const TransportParams &P, Shared &S, Lan
       L.s = 0.0f;
       L.p2 = 0.0f;
     }
-    L.w *= set_paths(P, S, L, -__logf(u01f_word(a.z)), -__logf(u01f_word(a.w)));
+    L.w *= set_paths(P, S, L, neg_ln_u(u01f_word(a.z)), neg_ln_u(u01f_word(a.w)));
   } else {
     const float u = u01f_word(a.x), u_phi = u01f_word(a.y);
     const int f = L.f;
@@ -790,7 +807,7 @@ __device__ __forceinline__ void scatter(const TransportParams &P, Shared &S, Lan
       L.s = 0.0f;
       L.p2 = 0.0f;
     }
-    L.w *= set_paths(P, S, L, -__logf(u01f_word(a.z)), -__logf(u01f_word(a.w)));
+    L.w *= set_paths(P, S, L, neg_ln_u(u01f_word(a.z)), neg_ln_u(u01f_word(a.w)));
   }
   T.scat++;
   if constexpr (RECORD) L.nsca++;
@@ -921,7 +938,7 @@ __device__ __forceinline__ void absorb(const TransportParams &P, Shared &S, cons
       L.s = r * (2.0f * u_mu - 1.0f);
       L.p2 = r2 * (4.0f * u_mu * (1.0f - u_mu));
     }
-    L.w *= set_paths(P, S, L, -__logf(u_ts), -__logf(u_ta));
+    L.w *= set_paths(P, S, L, neg_ln_u(u_ts), neg_ln_u(u_ta));
   }
   record<RECORD>(L, EV_ABSORB, L.cell, L.f);
 }
