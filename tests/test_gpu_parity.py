@@ -355,3 +355,15 @@ def test_forced_absorption_matches_oracle(D, oracle, prec):
     st = m.stats()
     assert st["status_word"] == 0
     assert st["E_escaped"] + st["E_lost"] == pytest.approx(st["E_injected"], rel=1e-6)
+
+
+def test_run_config_cli_runs_a_named_workload(D, capsys):
+    """The command-line runner used by the committed profiling commands."""
+    import json
+    from paper_2408_13807_gb300 import run_config
+    rc = run_config.main(["--config", "c3", "--n", "20000", "--runs", "2", "--block", "256", "--rare-batch", "12",
+                          "--inner-moves", "64", "--aggregate-atomics", "1"])
+    assert rc == 0
+    lines = [json.loads(l) for l in capsys.readouterr().out.strip().splitlines()]
+    assert len(lines) == 2 and all(l["status_word"] == 0 and l["packages_per_s"] > 0 for l in lines)
+    assert lines[0]["events_per_package"]["crossed"] > 100
