@@ -39,3 +39,17 @@ def test_seed_copies_match_the_oracle_ensemble(N):
     r = compare_ensembles(T, g["T"][0], 0.01)
     assert r["gated"].sum() >= cloud.n_cells // 2
     assert r["max_rel_gated"] <= 0.01 and r["max_z"] <= 6.0 and r["frac_beyond_3sigma"] <= 0.05, r
+
+
+@pytest.mark.parametrize("which", ["external", "internal"])
+def test_noise_grows_away_from_the_source(N, which):
+    """Sect. 4: the temperature errors grow inwards in externally heated
+    models and outwards in internally heated ones (64 GPU seeds)."""
+    cloud = W.config2(10.0) if which == "external" else W.point_source_cloud(64, 1e-2, 30.0)
+    rn = np.array(N.noise_study(cloud, [200_000], n_seeds=64)[0]["rel_noise"])
+    q = len(rn) // 4
+    inner, outer = np.median(rn[:q]), np.median(rn[-q:])
+    if which == "external":
+        assert inner > 1.5 * outer, (inner, outer)
+    else:
+        assert outer > 1.5 * inner, (inner, outer)

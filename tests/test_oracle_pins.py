@@ -467,3 +467,21 @@ def test_randomised_reemission_keeps_the_grey_invariant(oracle):
     base = oracle.run(m.replace(remit_random=False), 2_000, 8, mode="frozen", T_frozen=np.full(4, 30.0), record=True)
     other = oracle.run(m, 2_000, 8, mode="frozen", T_frozen=np.full(4, 30.0), record=True)
     assert not np.array_equal(base["hash"], other["hash"])  # the option really acts
+
+
+def test_stored_ensembles_show_the_papers_noise_pattern():
+    """Sect. 4: the errors of the temperatures grow inwards in externally
+    heated models and outwards in internally heated ones.  Checked on the
+    stored 16-seed oracle ensembles (written from the oracle alone), over
+    the shells above the 2.7 K floor."""
+    import os
+    gold = os.path.join(os.path.dirname(__file__), "golden")
+    for name, external in (("c1", True), ("c2_sweep", True), ("c5e", True), ("c3", False), ("c5i", False)):
+        g = np.load(os.path.join(gold, f"{name}_oracle.npz"))
+        for mean, se in zip(np.atleast_2d(g["mean"]), np.atleast_2d(g["se"])):
+            live = mean > 2.7 * (1 + 1e-6)
+            r = (se / mean)[live]
+            q = max(len(r) // 4, 1)
+            inner, outer = np.median(r[:q]), np.median(r[-q:])
+            # (the thinnest external clouds, A_V = 1, are nearly flat: ratio >= 1.29)
+            assert (inner > 1.2 * outer) if external else (outer > 2.0 * inner), (name, inner, outer)
