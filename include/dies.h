@@ -199,7 +199,7 @@ int dies_set_stream(dies_model *m, void *cuda_stream);
  * absorptions and package starts together once this many of its lanes wait
  * for one (or when no lane can move on); inner_moves in [1, 64]: boundary
  * crossings a lane may make between two such rare-event passes (taken in
- * steps of 4, the warp checking its parked lanes after each step);
+ * blocks of 8, rounded up, the warp checking its parked lanes after each);
  * aggregate_atomics 0 or 1 (FP32 forms): lanes of a warp absorbing in the
  * same shell in the same pass add their energies with one atomic, each lane
  * taking as its E_old the returned value plus the energies of the lower

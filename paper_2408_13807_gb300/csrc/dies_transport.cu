@@ -37,7 +37,7 @@ namespace {
 
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kCheck = 4;  // moves between two early-exit ballots of the move loop
+constexpr int kCheck = 8;  // moves between two early-exit ballots of the move loop (measured best of 2-32)
 constexpr int kMaxWarps = 8;  // warps per CTA (block size <= 256)
 
 // Lane states.  0-2: the package moves; 3: it left the cloud, its escape
@@ -1145,12 +1145,18 @@ __global__ void __launch_bounds__(256, PREC == PREC_FP64 ? 1 : 5) k_transport(co
   // All warp-wide decisions come from ballots taken by all 32 lanes; nothing
   // about the warp is carried between iterations.
   for (;;) {
-    // up to P.inner moves per lane (in steps of kCheck); after each step the
-    // warp stops early once batch_min lanes no longer move (warp-uniform loop)
+    // up to P.inner moves per lane (in blocks of kCheck, P.inner rounded up);
+    // a lane that parks skips the rest of its block (one divergent region per
+    // block, not per move), and after each block the warp stops early once
+    // batch_min lanes no longer move (warp-uniform loop)
     for (int k = 0; k < P.inner; k += kCheck) {
+      if (L.st <= ST_FORCED) {
 #pragma unroll
-      for (int j = 0; j < kCheck; ++j)
-        if (L.st <= ST_FORCED) move<PREC, MODE, RECORD, OPT>(P, S, L, T);
+        for (int j = 0; j < kCheck; ++j) {
+          move<PREC, MODE, RECORD, OPT>(P, S, L, T);
+          if (L.st > ST_FORCED) break;
+        }
+      }
       if (__popc(__ballot_sync(kFull, L.st > ST_FORCED)) >= P.batch_min) break;
     }
     const unsigned waiting = __ballot_sync(kFull, (unsigned)(L.st - ST_ESCAPE) <= (unsigned)(ST_DEAD - ST_ESCAPE));
