@@ -37,7 +37,7 @@ cudaError_t launch_frozen_cdf(cudaStream_t st, int n_cells, int F, const double 
 size_t transport_smem_bytes(int n_tnodes_pow2);
 cudaError_t launch_transport(int prec, int mode, bool record, const TransportParams &P, int grid, int block,
                              cudaStream_t st);
-cudaError_t transport_occupancy(int prec, int mode, int block, int n_tnodes_pow2, bool r64, bool ffi,
+cudaError_t transport_occupancy(int prec, int mode, int block, int n_tnodes_pow2, bool r64, bool ffi, bool batch,
                                 int *blocks_per_sm);
 cudaError_t launch_finalize(cudaStream_t st, int n_cells, const double *E, const float *Eprev, const float *Ecur,
                             int fp32, const double *inv_mass, const double *Lnode, const double *lnT, int n,
@@ -450,7 +450,7 @@ struct Problem {
     int bps = blocks_per_sm;
     int occ = 0;
     const bool r64 = (prec_ == PREC_MIXED && mode == MODE_IRE && fp64_radius > 0.0);
-    DIES_CUDA(transport_occupancy(prec_, mode, block, next_pow2(n_tnodes), r64, ffi != 0, &occ));
+    DIES_CUDA(transport_occupancy(prec_, mode, block, next_pow2(n_tnodes), r64, ffi != 0, n_models > 1, &occ));
     if (occ < 1) return fail(DIES_ECUDA, "transport kernel cannot be resident with block size %d", block);
     if (bps <= 0 || bps > occ) bps = occ;
     *grid = sm_count * bps;
@@ -1112,7 +1112,7 @@ int dies_run_frozen_static(dies_model *m, const double *T_frozen_dev, uint64_t n
   DIES_CUDA(launch_frozen_cdf(p.stream, p.n_cells, p.F, p.at<double>(p.lay.freq), p.at<double>(p.lay.kabs),
                               p.at<double>(p.lay.dnu), T_frozen_dev, cdf));
   int occ = 0;
-  DIES_CUDA(transport_occupancy(PREC_FP64, MODE_FROZEN, p.block, next_pow2(p.n_tnodes), false, false, &occ));
+  DIES_CUDA(transport_occupancy(PREC_FP64, MODE_FROZEN, p.block, next_pow2(p.n_tnodes), false, false, false, &occ));
   if (occ < 1) return fail(DIES_ECUDA, "transport kernel cannot be resident with block size %d", p.block);
   const int bps = (p.blocks_per_sm > 0 && p.blocks_per_sm < occ) ? p.blocks_per_sm : occ;
   const int mode = (flags == DIES_FROZEN_ABSORB_TERMINAL) ? MODE_FROZEN_TERMINAL : MODE_FROZEN;
