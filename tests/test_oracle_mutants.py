@@ -63,15 +63,19 @@ MUTANTS = {
     # re-emission radius uniform in r instead of in volume
     "remit_radius_linear": ("  return cbrt(a + u * (b - a));", "  return ri + u * (ro - ri);",
                             "test_shell_radius_is_uniform_in_volume", {}),
+    # forced interaction of Eqs. 9-12 choosing scattering with probability k_A / k_ext
+    "ffi_type_inverted": ("if (u_type * ke < ka) alive = do_absorb(C, &p, &rs, s);",
+                          "if (u_type * ke >= ka) alive = do_absorb(C, &p, &rs, s);",
+                          "test_forced_interaction_is_unbiased_with_scattering", {"ffi": 1, "albedo": 0.3}),
     # forcing on the absorption depth applied when the ray is scattered
     "ffi_abs_case_flipped": ("if (p.tauS >= tauS0) {", "if (p.tauS < tauS0) {",
-                             "test_forced_absorption_is_unbiased_with_scattering", {}),
+                             "test_forced_interaction_is_unbiased_with_scattering", {"ffi": 2, "albedo": 0.5}),
     # forcing on the absorption depth whatever the scattering clock says
     "ffi_abs_scattering_ignored": ("if (p.tauS >= tauS0) {", "if (1) {",
-                                   "test_forced_absorption_is_unbiased_with_scattering", {}),
+                                   "test_forced_interaction_is_unbiased_with_scattering", {"ffi": 2, "albedo": 0.5}),
     # Eq. 12 weight from the extinction depth while forcing an absorption
     "ffi_abs_weight_extinction": ("double q = -expm1(-tauA0);", "double q = -expm1(-(tauA0 + tauS0));",
-                                  "test_forced_absorption_is_unbiased_with_scattering", {}),
+                                  "test_forced_interaction_is_unbiased_with_scattering", {"ffi": 2, "albedo": 0.5}),
     # direct-escape part of the absorption forcing not tallied
     "ffi_abs_no_direct_tally": ("      C->sed[p.f] += e_direct;\n      C->st[ST_E_DIRECT] += e_direct;\n"
                                 "      C->st[ST_E_ESCAPED] += e_direct;\n", "\n",

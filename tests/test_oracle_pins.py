@@ -360,18 +360,20 @@ def test_forced_absorption_without_scattering_is_the_extinction_form(oracle):
     assert r1["stats"] == r2["stats"]
 
 
-def test_forced_absorption_is_unbiased_with_scattering(oracle):
-    """Forcing on the absorption depth (Sect. 2.2.2) in a scattering medium:
-    the expected absorption per shell equals that of analog sampling (both
-    absorb-terminal, so each shell's absorbed fraction is a plain
-    expectation)."""
-    m = W.grey_model(4, 2.0, albedo=0.5, g=0.6).replace(rho=np.array([0.3, 1.6, 0.8, 1.2]))
+@pytest.mark.parametrize("ffi,albedo", [(1, 0.3), (2, 0.5)])
+def test_forced_interaction_is_unbiased_with_scattering(oracle, ffi, albedo):
+    """Forcing on the extinction or the absorption depth (Sect. 2.2.2) in a
+    scattering medium: the expected absorption per shell equals that of
+    analog sampling (both absorb-terminal, so each shell's absorbed fraction
+    is a plain expectation).  Albedo 0.3 for the extinction form, where 0.5
+    would make the interaction type a fair coin."""
+    m = W.grey_model(4, 2.0, albedo=albedo, g=0.6).replace(rho=np.array([0.3, 1.6, 0.8, 1.2]))
     L = oracle.source_luminosity(m)[0]
     T = np.full(4, 10.0)
     runs = {f: np.array([_fractions(oracle.run(m.replace(ffi=f), 10_000, 70 + s, mode="frozen_terminal",
-                                               T_frozen=T), L) for s in range(16)]) for f in (0, 2)}
+                                               T_frozen=T), L) for s in range(16)]) for f in (0, ffi)}
     mean0, se0 = runs[0].mean(0), runs[0].std(0, ddof=1) / 4.0
-    mean2, se2 = runs[2].mean(0), runs[2].std(0, ddof=1) / 4.0
+    mean2, se2 = runs[ffi].mean(0), runs[ffi].std(0, ddof=1) / 4.0
     assert np.all(np.abs(mean2 - mean0) < 4.5 * np.hypot(se0, se2)), (mean0, mean2, se0, se2)
 
 
