@@ -157,3 +157,25 @@ def test_run_without_gpu_fails_loudly(lib):
         assert e.value.code in (D.DIES_ECUDA, D.DIES_ENOMEM)
     finally:
         D.dies_destroy_model(h)
+
+
+def test_plain_c_client_compiles_links_and_fails_cleanly_without_gpu(tmp_path):
+    """The boundary from C: tests/c_client/client.c compiles as C11 against
+    include/dies.h, links against libdies.so and, on a machine without a
+    GPU, gets a status code and a message from dies_run instead of a crash."""
+    import shutil
+    import subprocess
+    from paper_2408_13807_gb300 import build as B
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    lib_path = B.build()
+    exe = tmp_path / "client"
+    subprocess.check_call(["gcc", "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                           os.path.join(ROOT, "tests", "c_client", "client.c"), "-o", str(exe),
+                           "-L", os.path.dirname(lib_path), "-ldies", "-Wl,-rpath," + os.path.dirname(lib_path)])
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present: the run itself is covered by the GPU tests")
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "run refused" in r.stdout
