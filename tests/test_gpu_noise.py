@@ -3,7 +3,7 @@ of one cloud in a batched launch."""
 import numpy as np
 import pytest
 
-from gpu_util import compare_ensembles
+from gpu_util import check_sigma, compare_ensembles
 from paper_2408_13807_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -37,8 +37,9 @@ def test_seed_copies_match_the_oracle_ensemble(N):
     cloud = W.config1()
     T = N.seed_ensemble(cloud, int(g["n_packages"]), 64, seed=5)
     r = compare_ensembles(T, g["T"][0], 0.01)
-    assert r["gated"].sum() >= cloud.n_cells // 2
-    assert r["max_rel_gated"] <= 0.01 and r["max_z"] <= 6.0 and r["frac_beyond_3sigma"] <= 0.05, r
+    assert r["n_gated"] >= cloud.n_cells // 2 and r["n_acc"] >= 1
+    assert r["max_rel_gated"] <= 0.01, r
+    check_sigma(r)
 
 
 @pytest.mark.parametrize("which", ["external", "internal"])
