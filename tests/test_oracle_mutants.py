@@ -80,6 +80,10 @@ MUTANTS = {
     "ffi_abs_no_direct_tally": ("      C->sed[p.f] += e_direct;\n      C->st[ST_E_DIRECT] += e_direct;\n"
                                 "      C->st[ST_E_ESCAPED] += e_direct;\n", "\n",
                                 "test_energy_conservation_ire", {}),
+    # reference direction of Eqs. 6-7 with the sign flipped (outwards for the external field)
+    "reference_direction_flipped": ("ref[i] = (s == 0) ? -rhat[i] : rhat[i];", "ref[i] = (s == 0) ? rhat[i] : -rhat[i];",
+                                    "test_weighting_reference_direction_points_away_from_the_source",
+                                    {"external": True}),
     # density-dependent k_A running the wrong way
     "kA_rho_reversed": ("kA[i] = M->kA_hi + (M->kA_lo - M->kA_hi) * (lmax - log(M->rho[i])) / (lmax - lmin);",
                         "kA[i] = M->kA_lo + (M->kA_hi - M->kA_lo) * (lmax - log(M->rho[i])) / (lmax - lmin);",

@@ -429,6 +429,44 @@ def test_reemission_weighting_is_unbiased(oracle, g_E):
     assert abs(ratios.mean() - 1.0) < 4.5 * ratios.std(ddof=1) / np.sqrt(len(ratios))
 
 
+def _mean_events(oracle, m, col, N=4_000, seed=5, T=30.0):
+    ev = oracle.run(m, N, seed, mode="frozen", T_frozen=np.full(m.n_cells, T), record=True)["n_events"]
+    x = ev[:, col].astype(np.float64)
+    return x.mean(), x.std(ddof=1) / np.sqrt(N)
+
+
+@pytest.mark.parametrize("external", [True, False])
+def test_weighting_reference_direction_points_away_from_the_source(oracle, external):
+    """Sect. 2.2.1 fixes the sign of Eqs. 6-7: the cosine is measured from
+    the direction towards the centre for the external field and from the
+    outward direction for the central source, so g_E, g_S > 0 send packages
+    away from their source.  Unweighted event counts per package show the
+    sign (the unbiasedness pins above hold for either sign): an external
+    package re-emitted with g_E = 0.5 heads inwards and is absorbed more
+    often before it escapes than without weighting (measured 2.5 vs 1.4
+    absorptions per package), with g_E = -0.5 less often (1.0); a
+    point-source package the other way round.  Likewise in a pure scatterer
+    for g_S = 0.5 against g_S = -0.5 (4.7 vs 1.4 scatterings per package
+    for the external field)."""
+    rho = np.array([2.5, 0.5, 1.2, 0.8])
+    src = {} if external else {"external": False, "L_point": 1e33}
+    m = W.grey_model(4, 0.9, albedo=0.0, r_in=0.2, **src).replace(rho=rho)
+    a0, s0 = _mean_events(oracle, m, 1)
+    ap, sp = _mean_events(oracle, m.replace(g_E=0.5), 1)
+    an, sn = _mean_events(oracle, m.replace(g_E=-0.5), 1)
+    inward, outward = (ap, an) if external else (an, ap)
+    s_in, s_out = (sp, sn) if external else (sn, sp)
+    assert inward > a0 + 6.0 * np.hypot(s_in, s0), (inward, a0)
+    assert outward < a0 - 6.0 * np.hypot(s_out, s0), (outward, a0)
+    ms = W.grey_model(4, 1.5, albedo=1.0, g=0.0, r_in=0.1, **src)
+    cp, sp = _mean_events(oracle, ms.replace(scat_w=True, g_S=0.5), 0, T=10.0)
+    cn, sn = _mean_events(oracle, ms.replace(scat_w=True, g_S=-0.5), 0, T=10.0)
+    if external:
+        assert cp > cn + 6.0 * np.hypot(sp, sn), (cp, cn)
+    else:
+        assert cn > cp + 6.0 * np.hypot(sp, sn), (cp, cn)
+
+
 def test_neutral_weighting_parameters_are_the_unweighted_run(oracle):
     """g_E = 0, k_A = k_S = 1 and scattering weighting off reproduce the
     unweighted run exactly (same streams, unit weights); scattering weighting
