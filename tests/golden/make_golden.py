@@ -75,10 +75,10 @@ def main():
     if "c5e" in which:
         save("c5e", [W.config5_external()], 4_000_000, args.procs)
     if "c5i" in which:
-        save("c5i", [W.config5_internal()], 200_000, args.procs)
+        save("c5i", [W.config5_internal()], 2_000_000, args.procs)
     if "c4" in which:
         models = W.config4_models()
-        save("c4_sample", [models[i] for i in C4_SAMPLE], 200_000, args.procs)
+        save("c4_sample", [models[i] for i in C4_SAMPLE], 2_000_000, args.procs)
     if "c2" in which:
         save("c2_sweep", W.config2_sweep(), args.n_c2, args.procs)
 
