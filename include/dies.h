@@ -55,7 +55,8 @@ typedef enum {
   DIES_ECUDA = -3,    /* a CUDA runtime call failed (no device, launch error, ...) */
   DIES_ESTATE = -4,   /* call not valid in the handle's state (e.g. run before dust) */
   DIES_ETIMEOUT = -5, /* the transport kernel hit its wall-clock budget and stopped */
-  DIES_ERANGE = -6    /* a result left its table range with strict range checking on */
+  DIES_ERANGE = -6    /* a result left its representable range: an absorbed-energy counter of
+                         the all-FP32 form passed ~1e38 (use DIES_PREC_MIXED for such sources) */
 } dies_status;
 
 /* Precision forms of the transport (Sect. 2.3 discusses FP32 only). */
@@ -71,8 +72,13 @@ enum {
 
 /* flags of dies_run_frozen */
 enum {
-  DIES_FROZEN_REEMIT = 0,         /* absorption re-emits from the full cell spectrum */
-  DIES_FROZEN_ABSORB_TERMINAL = 1 /* absorption ends the package (pure-absorber tests) */
+  DIES_FROZEN_REEMIT = 0,          /* absorption re-emits from the full cell spectrum */
+  DIES_FROZEN_ABSORB_TERMINAL = 1, /* absorption ends the package (pure-absorber tests) */
+  DIES_FROZEN_FORM = 2             /* with DIES_FROZEN_ABSORB_TERMINAL only: run the pass in the
+                                      handle's precision form (dies_set_precision: the MIXED or
+                                      FP32 stepping, FP64 inner crossings, forced first
+                                      interaction) instead of the FP64 form; no per-package
+                                      records */
 };
 
 typedef struct dies_model dies_model; /* opaque; owned by the library until destroyed */
@@ -97,12 +103,18 @@ typedef struct {
   double kernel_ms;       /* device time from the accumulator reset to the end of the temperature kernel */
   double transport_ms;    /* device time of the transport launch(es) alone */
   uint32_t status_word;   /* device-side error flags: 0 = none, 1 = time budget reached, 8 = flight
-                             watchdog tripped, 16 = a package left unfinished */
+                             watchdog tripped, 16 = a package left unfinished, 32 = FP32
+                             counter out of range (DIES_ERANGE) */
   uint32_t launches;      /* kernels launched by this run */
   uint32_t diag[16];      /* diag[0] = 1: state of the first package ended by the flight
                              watchdog (state, cell, freq, n, s, p^2, tauA, tauS (FP32
                              forms: column travelled, column limit), kA, kS, w as
                              float bits, package, model) */
+  double upload_ms;       /* device time of the input uploads that open the table build
+                             (part of table_ms; 0 if cached).  Together with table_ms and
+                             kernel_ms: the split of a run into upload, table build and
+                             transport + temperatures that Sect. 3.1 reports as total vs
+                             kernel time */
 } dies_stats;
 
 /* ------------------------------------------------------------ one model */
@@ -209,6 +221,43 @@ int dies_set_stream(dies_model *m, void *cuda_stream);
 int dies_set_launch(dies_model *m, int block_size, int blocks_per_sm, int rare_batch, int inner_moves,
                     int aggregate_atomics);
 
+/* Re-emission table layouts of the FP32 forms (dies_launch.reemit_table). */
+enum {
+  DIES_TABLE_ALIAS = 0, /* one alias-table row per T interval: one probe and one compare */
+  DIES_TABLE_CDF = 1    /* one FP32 CDF row per T interval: binary search of six probes */
+};
+
+/* The full launch configuration, all knobs of the autotuner (no counterpart
+ * in the paper; Sect. 2.3 runs one work item per package).  The first five
+ * fields are those of dies_set_launch, with the same ranges; then
+ *   refill_divisor       in [0, 4096]: a warp takes about 1/refill_divisor of
+ *                        its share of the launch per trip to the device work
+ *                        counter (32 to 1024 packages, a multiple of 32, so 1
+ *                        to 32 packages per lane); 0 = 64.  Relative to the
+ *                        launch, so one value serves every package count;
+ *   reemit_table         DIES_TABLE_ALIAS or DIES_TABLE_CDF (FP32 forms; the
+ *                        FP64 form searches FP64 CDF rows);
+ *   packages_per_thread  1 (or 0) or 2: with 2 (FP32 forms without forced
+ *                        first interaction; other runs ignore it) each lane
+ *                        owns two slots of a per-warp pool of packages in
+ *                        shared memory besides the package in its registers:
+ *                        a stopped package waits there for its event while
+ *                        the lane moves another, and events run in passes of
+ *                        one kind.
+ * Both sample the same discrete distributions (to within 2^-23 per bin);
+ * results do not depend on the configuration beyond FP32 rounding. */
+typedef struct dies_launch {
+  int block_size;
+  int blocks_per_sm;
+  int rare_batch;
+  int inner_moves;
+  int aggregate_atomics;
+  int refill_divisor;
+  int reemit_table;
+  int packages_per_thread;
+} dies_launch;
+int dies_set_launch_ex(dies_model *m, const dies_launch *launch);
+
 /* Wall-clock budget of one transport launch in seconds (default 120).  A
  * launch that reaches it stops early and the run returns DIES_ETIMEOUT. */
 int dies_set_time_budget(dies_model *m, double seconds);
@@ -261,7 +310,16 @@ int dies_get_stats(dies_model *m, dies_stats *out);
  * Uses the Philox stream layout of the FP64 form.  Optional per-package
  * outputs (NULL to skip), package j of active source s at row s*n + j:
  * n_events_out[rows*3] = (scatterings, absorptions, crossings) and
- * path_hash_out[rows] = 64-bit FNV-1a hash of the event sequence. */
+ * path_hash_out[rows] = 64-bit FNV-1a hash of the event sequence.
+ * With flags = DIES_FROZEN_ABSORB_TERMINAL | DIES_FROZEN_FORM the pass runs
+ * the handle's own precision form instead (the stepping, sampling and
+ * forced-interaction code of dies_run, Sect. 2.1 and Eq. 4, with each
+ * absorption ending its package): a pure absorber's per-shell absorbed
+ * energy then has a closed form (impact-parameter quadrature for the
+ * external field, radial for the point source) that pins the FP32 geometry.
+ * Absorbed energies are tallied in FP64 in every form; T_frozen is unused
+ * by the physics of this mode but still required; records must be NULL
+ * (else DIES_EINVAL). */
 int dies_run_frozen(dies_model *m, const double *T_frozen, uint64_t n_packages, uint64_t seed, int flags,
                     uint32_t *n_events_out, uint64_t *path_hash_out);
 
@@ -271,11 +329,20 @@ void dies_destroy_model(dies_model *m);
  * counterpart: this entry point serves callers that cannot call cudaMalloc
  * (code running while a stream is being captured, plug-ins whose host
  * application owns all device memory, allocators that forbid side
- * allocations).  It computes exactly what dies_run_frozen computes, but every
- * input and output is a caller-owned DEVICE pointer and the pass's scratch
- * (per-shell re-emission CDFs, work counter, event counters) lives in one
- * fixed array inside the library, DIES_STATIC_SCRATCH_BYTES bytes on every
- * GPU that loads it, kept until the process exits.
+ * allocations).  It computes the absorbed energies, the escaping SED, the
+ * per-package event counts and the path hashes that dies_run_frozen
+ * computes, but every input and output is a caller-owned DEVICE pointer and
+ * the pass's scratch (per-shell re-emission CDFs, work counter, event
+ * counters, status word, SED partials) lives in one fixed array inside the
+ * library, DIES_STATIC_SCRATCH_BYTES bytes on every GPU that loads it, kept
+ * until the process exits.  The handle's temperatures, absorbed energies and
+ * SED (dies_get_temperatures / _absorbed / _escaping_sed) keep the values of
+ * its last dies_run.  To learn whether the pass completed, call
+ * dies_get_stats on the handle afterwards (it waits for the stream): it
+ * returns DIES_ETIMEOUT when the kernel stopped at the handle's time budget
+ * (dies_set_time_budget) and fills the counters and energies of the pass;
+ * it reads them from the shared scratch, so call it before the next static
+ * pass on any handle.
  *   T_frozen_dev  [n_shells] shell temperatures (> 0), device memory
  *   E_abs_dev     [n_shells] out: absorbed energy per shell (erg/s)
  *   sed_dev       [n_freq]   out: escaping luminosity per bin (erg/s)
@@ -310,6 +377,7 @@ int dies_batch_set_sources(dies_batch *b, const double *J_ext, double L_point, c
 int dies_batch_set_stream(dies_batch *b, void *cuda_stream);
 int dies_batch_set_launch(dies_batch *b, int block_size, int blocks_per_sm, int rare_batch, int inner_moves,
                           int aggregate_atomics);
+int dies_batch_set_launch_ex(dies_batch *b, const dies_launch *launch);
 /* Weighting for all models of the batch (as dies_set_weighting_ex; with
  * k_A_density the density range is each model's own). */
 int dies_batch_set_weighting(dies_batch *b, const dies_weighting *w);

@@ -14,10 +14,22 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/dies.h"
 #include "dies_common.cuh"
 
 namespace dies {
+
+// NVTX range over a host-side phase of a call (upload and table build,
+// enqueue of the transport, wait and read-back), for timeline profilers;
+// without a profiler attached the push and pop cost a few nanoseconds.
+struct Range {
+  explicit Range(const char *name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range &) = delete;
+  Range &operator=(const Range &) = delete;
+};
 
 static std::atomic<unsigned long long> g_launches{0};
 void launch_counter_add(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
@@ -26,8 +38,8 @@ cudaError_t launch_freq_tables(cudaStream_t st, int F, const double *nu, const d
                                double *dnu, double *src_cdf_d, uint32_t *src_alias, double *src_sum);
 cudaError_t launch_node_tables(cudaStream_t st, int F, int n, int n_pow2, double T_min, double T_max,
                                const double *nu, const double *kabs, const double *dnu, double *Lnode_d,
-                               float *Lnode_f, double *lnT, uint32_t *dalias, double *dcdf_d, uint16_t *nguide,
-                               int *nmeta);
+                               float *Lnode_f, double *lnT, uint32_t *dalias, double *dcdf_d, float *dcdf_f,
+                               uint16_t *nguide, int *nmeta);
 cudaError_t launch_geometry(cudaStream_t st, int n_models, ModelDesc *desc, int n_cells_total, int n_bnd,
                             const double *radii, const double *rho, double length_unit_cm, const double *src_sum,
                             double L_point, double *r2d, float *r2f, double *rhod, float *rhof, double *inv_mass,
@@ -38,7 +50,7 @@ size_t transport_smem_bytes(int n_tnodes_pow2);
 cudaError_t launch_transport(int prec, int mode, bool record, const TransportParams &P, int grid, int block,
                              cudaStream_t st);
 cudaError_t transport_occupancy(int prec, int mode, int block, int n_tnodes_pow2, bool r64, bool ffi, bool batch,
-                                int *blocks_per_sm);
+                                bool pool, int *blocks_per_sm);
 cudaError_t launch_finalize(cudaStream_t st, int n_cells, const double *E, const float *Eprev, const float *Ecur,
                             int fp32, const double *inv_mass, const double *Lnode, const double *lnT, int n,
                             double *T_out);
@@ -86,7 +98,7 @@ struct Layout {
   size_t desc, radii, rho_in, r2d, r2f, rhod, rhof, inv_mass, inv_massf, kA_d, kA_f, geo, rhoe, E, Eprev, Ecur, T, sed;
   size_t sed_q, inj_q, dir_q;
   size_t freq, kabs, ksca, g, J, spec, dnu, src_cdf_d, src_alias, src_sum;
-  size_t Lnode_d, Lnode_f, lnT, dalias, dcdf_d, nguide, nmeta;
+  size_t Lnode_d, Lnode_f, lnT, dalias, dcdf_d, dcdf_f, nguide, nmeta;
   size_t counters, energies, queue, status, diag, seedw;
   size_t total;
 };
@@ -116,6 +128,9 @@ struct Problem {
   int n_tnodes = 1024;
   cudaStream_t stream = nullptr;
   int block = 256, blocks_per_sm = 0, rare_batch = 16, inner = 32, agg = 0;
+  int pkgs_per_thread = 1;  // 2: a second package per lane in per-warp shared-memory pools (FP32 forms, no FFI)
+  int refill_div = 0;  // a warp takes ~1/refill_div of its share of the launch per trip to the work counter (0 = 64)
+  int remit_table = DIES_TABLE_ALIAS;
   double time_budget_s = 120.0;
   // device
   unsigned char *ws = nullptr;
@@ -124,13 +139,20 @@ struct Problem {
   Layout lay{};
   bool tables_valid = false;
   int sm_count = 0;
-  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  // run timing: 0 start, 5 uploads done, 1 tables built, 2/3 around the transport, 4 end
+  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   bool events_ready = false;
   bool table_built_this_run = false;
   bool has_result = false;
   bool stats_pending = false;
+  bool e_in_fp32_counters = false;  // the last run kept absorbed energies in the FP32 form's two counters
   unsigned long long launches_at_start = 0;
   dies_stats stats{};
+  // a dies_run_frozen_static pass whose counters, status and SED still sit
+  // in the library's static scratch (device addresses of those words)
+  bool static_pending = false;
+  const void *static_counters = nullptr, *static_energies = nullptr, *static_status = nullptr,
+             *static_diag = nullptr, *static_sed = nullptr;
   // graph replay of the per-run device work (dies_set_graph)
   bool use_graph = false;
   cudaStream_t cap_stream = nullptr;
@@ -213,6 +235,7 @@ struct Problem {
     L.lnT = seg(np2 * 8);
     L.dalias = seg(nt * kMaxFreq * 4);
     L.dcdf_d = seg(nt * kMaxFreq * 8);
+    L.dcdf_f = seg(nt * kMaxFreq * 4);
     L.nguide = seg(kGuide * 2);
     L.nmeta = seg(2 * 4);
     L.counters = seg(16 * 8);
@@ -334,6 +357,7 @@ struct Problem {
   }
 
   int build_tables() {
+    Range r("dies: upload + table build");
     fill_desc();
     int rc;
     if ((rc = upload(lay.desc, desc.data(), desc.size() * sizeof(ModelDesc)))) return rc;
@@ -358,13 +382,15 @@ struct Problem {
     const size_t offs[6] = {lay.freq, lay.kabs, lay.ksca, lay.g, lay.J, lay.spec};
     for (int i = 0; i < 6; ++i)
       if ((rc = upload(offs[i], pad.data() + i * kMaxFreq, kMaxFreq * 8))) return rc;
+    DIES_CUDA(cudaEventRecord(ev[5], stream));
     DIES_CUDA(launch_freq_tables(stream, F, at<double>(lay.freq), has_ext ? at<double>(lay.J) : nullptr,
                                  (L_point > 0.0) ? at<double>(lay.spec) : nullptr, at<double>(lay.dnu),
                                  at<double>(lay.src_cdf_d), at<uint32_t>(lay.src_alias), at<double>(lay.src_sum)));
     DIES_CUDA(launch_node_tables(stream, F, n_tnodes, next_pow2(n_tnodes), T_min, T_max, at<double>(lay.freq),
                                  at<double>(lay.kabs), at<double>(lay.dnu), at<double>(lay.Lnode_d),
                                  at<float>(lay.Lnode_f), at<double>(lay.lnT), at<uint32_t>(lay.dalias),
-                                 at<double>(lay.dcdf_d), at<uint16_t>(lay.nguide), at<int>(lay.nmeta)));
+                                 at<double>(lay.dcdf_d), at<float>(lay.dcdf_f), at<uint16_t>(lay.nguide),
+                                 at<int>(lay.nmeta)));
     DIES_CUDA(launch_geometry(stream, n_models, at<ModelDesc>(lay.desc), n_cells, n_cells + n_models,
                               at<double>(lay.radii), at<double>(lay.rho_in), length_unit_cm, at<double>(lay.src_sum),
                               L_point, at<double>(lay.r2d), at<float>(lay.r2f), at<double>(lay.rhod),
@@ -406,6 +432,10 @@ struct Problem {
     P.nguide = at<uint16_t>(lay.nguide);
     P.nmeta = at<int>(lay.nmeta);
     P.dcdf_d = at<double>(lay.dcdf_d);
+    P.dcdf_f = at<float>(lay.dcdf_f);
+    P.remit_cdf = remit_table;
+    P.refill_div = (unsigned)refill_div;
+    P.pool = (pkgs_per_thread == 2 && mode == MODE_IRE) ? 1 : 0;
     P.n_tnodes = n_tnodes;
     P.n_tnodes_pow2 = next_pow2(n_tnodes);
     P.n_per_source = n;
@@ -424,6 +454,7 @@ struct Problem {
     P.max_events = 100000000ULL;
     P.time_budget_ns = (unsigned long long)(time_budget_s * 1e9);
     P.inv_n = (float)(1.0 / (double)n);
+    P.inv_nd = 1.0 / (double)n;
     P.k_bg_f = (float)k_bg;
     P.g_E = g_E;
     P.g_S = g_S;
@@ -449,8 +480,9 @@ struct Problem {
   int grid_for(int prec_, int mode, int *grid) {
     int bps = blocks_per_sm;
     int occ = 0;
-    const bool r64 = (prec_ == PREC_MIXED && mode == MODE_IRE && fp64_radius > 0.0);
-    DIES_CUDA(transport_occupancy(prec_, mode, block, next_pow2(n_tnodes), r64, ffi != 0, n_models > 1, &occ));
+    const bool r64 = (prec_ == PREC_MIXED && fp64_radius > 0.0);
+    DIES_CUDA(transport_occupancy(prec_, mode, block, next_pow2(n_tnodes), r64, ffi != 0, n_models > 1,
+                                  pkgs_per_thread == 2, &occ));
     if (occ < 1) return fail(DIES_ECUDA, "transport kernel cannot be resident with block size %d", block);
     if (bps <= 0 || bps > occ) bps = occ;
     *grid = sm_count * bps;
@@ -505,6 +537,8 @@ struct Problem {
     DIES_CUDA(cudaEventRecord(ev[4], stream));
     has_result = true;
     stats_pending = true;
+    static_pending = false;
+    e_in_fp32_counters = (prec == PREC_FP32);
     return DIES_OK;
   }
 
@@ -513,6 +547,7 @@ struct Problem {
   // seed_dev set (graph capture) the kernels read the seed from there and
   // the timing events are recorded as graph nodes.
   int enqueue_body(cudaStream_t st, uint64_t n, uint64_t seed, int grid, const unsigned long long *seed_dev) {
+    Range r("dies: enqueue transport + temperatures");
     int rc;
     const unsigned rec_flags = seed_dev ? cudaEventRecordExternal : cudaEventRecordDefault;
     if ((rc = reset_accumulators_on(st))) return rc;
@@ -602,21 +637,30 @@ struct Problem {
     return DIES_OK;
   }
 
-  // Wait for the stream and collect the counters of the last run.
+  // Wait for the stream and collect the counters of the last run (of the
+  // last static frozen pass if that came last: its words sit in the static
+  // scratch, and only host stack memory receives them).
   int collect() {
     if (!has_result) return fail(DIES_ESTATE, "no run has completed on this handle");
+    Range r("dies: wait + read-back");
     DIES_CUDA(cudaStreamSynchronize(stream));
-    if (!stats_pending) return (stats.status_word & STATUS_TIMEOUT) ? DIES_ETIMEOUT : DIES_OK;
+    if (!stats_pending) {
+      if (stats.status_word & STATUS_TIMEOUT) return DIES_ETIMEOUT;
+      return (stats.status_word & STATUS_RANGE) ? DIES_ERANGE : DIES_OK;
+    }
+    const bool st = static_pending;
     unsigned long long cnt[16];
     double en[8];
     uint32_t status = 0;
-    std::vector<double> sed((size_t)n_models * kMaxFreq);
-    DIES_CUDA(cudaMemcpy(cnt, ws + lay.counters, sizeof cnt, cudaMemcpyDeviceToHost));
-    DIES_CUDA(cudaMemcpy(en, ws + lay.energies, sizeof en, cudaMemcpyDeviceToHost));
-    DIES_CUDA(cudaMemcpy(&status, ws + lay.status, 4, cudaMemcpyDeviceToHost));
+    double sed_stat[kMaxFreq];
+    std::vector<double> sed(st ? 0 : (size_t)n_models * kMaxFreq);
+    DIES_CUDA(cudaMemcpy(cnt, st ? static_counters : ws + lay.counters, sizeof cnt, cudaMemcpyDeviceToHost));
+    DIES_CUDA(cudaMemcpy(en, st ? static_energies : ws + lay.energies, sizeof en, cudaMemcpyDeviceToHost));
+    DIES_CUDA(cudaMemcpy(&status, st ? static_status : ws + lay.status, 4, cudaMemcpyDeviceToHost));
     uint32_t diag[16];
-    DIES_CUDA(cudaMemcpy(diag, ws + lay.diag, sizeof diag, cudaMemcpyDeviceToHost));
-    DIES_CUDA(cudaMemcpy(sed.data(), ws + lay.sed, sed.size() * 8, cudaMemcpyDeviceToHost));
+    DIES_CUDA(cudaMemcpy(diag, st ? static_diag : ws + lay.diag, sizeof diag, cudaMemcpyDeviceToHost));
+    if (st) DIES_CUDA(cudaMemcpy(sed_stat, static_sed, sizeof sed_stat, cudaMemcpyDeviceToHost));
+    else DIES_CUDA(cudaMemcpy(sed.data(), ws + lay.sed, sed.size() * 8, cudaMemcpyDeviceToHost));
     dies_stats s{};
     s.injected = cnt[CNT_INJECTED];
     s.escaped = cnt[CNT_ESCAPED];
@@ -631,22 +675,34 @@ struct Problem {
     s.E_lost = en[EN_LOST];
     s.E_direct = en[EN_DIRECT];
     double esc = 0.0;
-    for (double v : sed) esc += v;
+    if (st) {
+      for (int k = 0; k < kMaxFreq; ++k) esc += sed_stat[k];
+    } else {
+      for (double v : sed) esc += v;
+    }
     s.E_escaped = esc;
     float ms = 0.0f;
-    if (cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess) s.table_ms = table_built_this_run ? ms : 0.0;
-    if (cudaEventElapsedTime(&ms, ev[1], ev[4]) == cudaSuccess) s.kernel_ms = ms;
-    if (cudaEventElapsedTime(&ms, ev[2], ev[3]) == cudaSuccess) s.transport_ms = ms;
+    if (!st) {  // the static pass records no timing events
+      if (cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess) s.table_ms = table_built_this_run ? ms : 0.0;
+      if (table_built_this_run && cudaEventElapsedTime(&ms, ev[0], ev[5]) == cudaSuccess) s.upload_ms = ms;
+      if (cudaEventElapsedTime(&ms, ev[1], ev[4]) == cudaSuccess) s.kernel_ms = ms;
+      if (cudaEventElapsedTime(&ms, ev[2], ev[3]) == cudaSuccess) s.transport_ms = ms;
+    }
     s.status_word = status;
     for (int i = 0; i < 16; ++i) s.diag[i] = diag[i];
     s.launches = (uint32_t)(g_launches.load() - launches_at_start);
     stats = s;
     stats_pending = false;
+    static_pending = false;
     if (status & STATUS_TIMEOUT) return fail(DIES_ETIMEOUT, "transport kernel stopped at its time budget");
+    if (status & STATUS_RANGE)
+      return fail(DIES_ERANGE, "an absorbed-energy counter of the all-FP32 form left the FP32 range "
+                               "(luminosity above ~1e38 erg/s): use DIES_PREC_MIXED");
     return DIES_OK;
   }
 
   int frozen(const double *T_frozen, uint64_t n, uint64_t seed, int flags, uint32_t *ev_out, uint64_t *hash_out) {
+    Range r("dies: frozen pass");
     int rc;
     if ((rc = check_ready())) return rc;
     if (n == 0) return fail(DIES_EINVAL, "n_packages must be >= 1");
@@ -654,8 +710,16 @@ struct Problem {
     for (int i = 0; i < n_cells; ++i)
       if (!(std::isfinite(T_frozen[i]) && T_frozen[i] > 0.0))
         return fail(DIES_EINVAL, "T_frozen[%d] must be finite and > 0", i);
-    if (flags != DIES_FROZEN_REEMIT && flags != DIES_FROZEN_ABSORB_TERMINAL)
+    const bool in_form = (flags & DIES_FROZEN_FORM) != 0;
+    const int base = flags & ~DIES_FROZEN_FORM;
+    if (base != DIES_FROZEN_REEMIT && base != DIES_FROZEN_ABSORB_TERMINAL)
       return fail(DIES_EINVAL, "unknown frozen flags %d", flags);
+    if (in_form && base != DIES_FROZEN_ABSORB_TERMINAL)
+      return fail(DIES_EINVAL, "DIES_FROZEN_FORM needs DIES_FROZEN_ABSORB_TERMINAL");
+    if (in_form && (ev_out || hash_out))
+      return fail(DIES_EINVAL, "per-package records exist only in the FP64 form (n_events_out and path_hash_out must be NULL)");
+    // the precision form of the pass: the handle's with DIES_FROZEN_FORM, else FP64
+    const int fprec = in_form ? prec : PREC_FP64;
     if ((rc = ensure_device())) return rc;
     launches_at_start = g_launches.load();
     DIES_CUDA(cudaEventRecord(ev[0], stream));
@@ -690,20 +754,29 @@ struct Problem {
                                  dT, dcdf)))
         break;
       if ((rc = reset_accumulators())) break;
+      const int mode = (base == DIES_FROZEN_ABSORB_TERMINAL) ? MODE_FROZEN_TERMINAL : MODE_FROZEN;
       int grid;
-      if ((rc = grid_for(PREC_FP64, MODE_FROZEN, &grid))) break;
+      if ((rc = grid_for(fprec, mode, &grid))) break;
       if ((e = cudaEventRecord(ev[2], stream))) break;
-      const int mode = (flags == DIES_FROZEN_ABSORB_TERMINAL) ? MODE_FROZEN_TERMINAL : MODE_FROZEN;
       TransportParams P = params(mode, n, seed);
       P.cell_cdf = dcdf;
       P.rec_events = dev;
       P.rec_hash = dhash;
-      if ((e = launch_transport(PREC_FP64, mode, ev_out || hash_out, P, grid, block, stream))) break;
+      if (fprec != PREC_MIXED) P.r64 = 0;
+      if ((e = launch_transport(fprec, mode, ev_out || hash_out, P, grid, block, stream))) break;
       if ((e = cudaEventRecord(ev[3], stream))) break;
+      // the FP32 forms keep their escape and injection tallies in fixed point
+      if (fprec != PREC_FP64 &&
+          (e = launch_tally(stream, n_models, at<ModelDesc>(lay.desc), n, at<unsigned long long>(lay.sed_q),
+                            at<unsigned long long>(lay.inj_q), at<unsigned long long>(lay.dir_q), at<double>(lay.sed),
+                            at<double>(lay.energies), tally_replicas())))
+        break;
       if ((e = cudaMemcpyAsync(ws + lay.T, dT, (size_t)n_cells * 8, cudaMemcpyDeviceToDevice, stream))) break;
       if ((e = cudaEventRecord(ev[4], stream))) break;
       has_result = true;
       stats_pending = true;
+      static_pending = false;
+      e_in_fp32_counters = false;  // every frozen pass tallies in the FP64 accumulator
       if ((rc = collect())) break;
       if (ev_out && (e = cudaMemcpy(ev_out, dev, rows * 3 * 4, cudaMemcpyDeviceToHost))) break;
       if (hash_out && (e = cudaMemcpy(hash_out, dhash, rows * 8, cudaMemcpyDeviceToHost))) break;
@@ -717,7 +790,7 @@ struct Problem {
     if (!out) return fail(DIES_EINVAL, "output pointer is NULL");
     if (n != n_cells) return fail(DIES_EINVAL, "expected %d shells, got %d", n_cells, n);
     int rc = collect();
-    if (rc && rc != DIES_ETIMEOUT) return rc;
+    if (rc && rc != DIES_ETIMEOUT && rc != DIES_ERANGE) return rc;
     DIES_CUDA(cudaMemcpy(out, ws + off, (size_t)n * 8, cudaMemcpyDeviceToHost));
     return rc;
   }
@@ -726,7 +799,7 @@ struct Problem {
     if (!out) return fail(DIES_EINVAL, "output pointer is NULL");
     if (n != n_models * F) return fail(DIES_EINVAL, "expected %d values, got %d", n_models * F, n);
     int rc = collect();
-    if (rc && rc != DIES_ETIMEOUT) return rc;
+    if (rc && rc != DIES_ETIMEOUT && rc != DIES_ERANGE) return rc;
     std::vector<double> tmp((size_t)n_models * kMaxFreq);
     DIES_CUDA(cudaMemcpy(tmp.data(), ws + lay.sed, tmp.size() * 8, cudaMemcpyDeviceToHost));
     for (int m = 0; m < n_models; ++m)
@@ -931,12 +1004,18 @@ int dies_set_stream(dies_model *m, void *s) {
   return DIES_OK;
 }
 
-static int set_launch(Problem &p, int block, int bps, int rare_batch, int inner, int agg) {
+static int check_launch(int block, int bps, int rare_batch, int inner, int agg) {
   if (block < 64 || block > 256 || block % 32) return fail(DIES_EINVAL, "block_size must be a multiple of 32 in [64, 256]");
   if (bps < 0) return fail(DIES_EINVAL, "blocks_per_sm must be >= 0");
   if (rare_batch < 1 || rare_batch > 32) return fail(DIES_EINVAL, "rare_batch must be in [1, 32]");
   if (inner < 1 || inner > 64) return fail(DIES_EINVAL, "inner_moves must be in [1, 64]");
   if (agg != 0 && agg != 1) return fail(DIES_EINVAL, "aggregate_atomics must be 0 or 1");
+  return DIES_OK;
+}
+
+static int set_launch(Problem &p, int block, int bps, int rare_batch, int inner, int agg) {
+  int rc = check_launch(block, bps, rare_batch, inner, agg);
+  if (rc) return rc;
   p.block = block;
   p.blocks_per_sm = bps;
   p.rare_batch = rare_batch;
@@ -949,6 +1028,27 @@ int dies_set_launch(dies_model *m, int block_size, int blocks_per_sm, int rare_b
                     int aggregate_atomics) {
   if (!m) return fail(DIES_EINVAL, "model is NULL");
   return set_launch(m->p, block_size, blocks_per_sm, rare_batch, inner_moves, aggregate_atomics);
+}
+
+static int set_launch_ex(Problem &p, const dies_launch *l) {
+  if (!l) return fail(DIES_EINVAL, "launch is NULL");
+  if (l->refill_divisor < 0 || l->refill_divisor > 4096)
+    return fail(DIES_EINVAL, "refill_divisor must be in [0, 4096]");
+  if (l->packages_per_thread < 0 || l->packages_per_thread > 2)
+    return fail(DIES_EINVAL, "packages_per_thread must be 0, 1 or 2");
+  if (l->reemit_table != DIES_TABLE_ALIAS && l->reemit_table != DIES_TABLE_CDF)
+    return fail(DIES_EINVAL, "reemit_table must be DIES_TABLE_ALIAS or DIES_TABLE_CDF");
+  int rc = set_launch(p, l->block_size, l->blocks_per_sm, l->rare_batch, l->inner_moves, l->aggregate_atomics);
+  if (rc) return rc;
+  p.refill_div = l->refill_divisor;
+  p.pkgs_per_thread = l->packages_per_thread == 2 ? 2 : 1;
+  p.remit_table = l->reemit_table;
+  return DIES_OK;
+}
+
+int dies_set_launch_ex(dies_model *m, const dies_launch *launch) {
+  if (!m) return fail(DIES_EINVAL, "model is NULL");
+  return set_launch_ex(m->p, launch);
 }
 
 int dies_set_time_budget(dies_model *m, double seconds) {
@@ -1005,12 +1105,12 @@ int dies_get_temperatures(dies_model *m, double *T, int n) {
 int dies_get_absorbed(dies_model *m, double *E, int n) {
   if (!m) return fail(DIES_EINVAL, "model is NULL");
   Problem &p = m->p;
-  if (p.prec == DIES_PREC_FP32 && p.has_result) {
+  if (p.e_in_fp32_counters && p.has_result) {
     // FP32 form: the absorbed energy is the sum of the two FP32 counters
     if (!E) return fail(DIES_EINVAL, "output pointer is NULL");
     if (n != p.n_cells) return fail(DIES_EINVAL, "expected %d shells, got %d", p.n_cells, n);
     int rc = p.collect();
-    if (rc && rc != DIES_ETIMEOUT) return rc;
+    if (rc && rc != DIES_ETIMEOUT && rc != DIES_ERANGE) return rc;
     std::vector<float> a(n), b(n);
     DIES_CUDA(cudaMemcpy(a.data(), p.ws + p.lay.Eprev, (size_t)n * 4, cudaMemcpyDeviceToHost));
     DIES_CUDA(cudaMemcpy(b.data(), p.ws + p.lay.Ecur, (size_t)n * 4, cudaMemcpyDeviceToHost));
@@ -1028,7 +1128,7 @@ int dies_get_escaping_sed(dies_model *m, double *L, int n) {
 int dies_get_stats(dies_model *m, dies_stats *out) {
   if (!m || !out) return fail(DIES_EINVAL, "NULL argument");
   int rc = m->p.collect();
-  if (rc && rc != DIES_ETIMEOUT) return rc;
+  if (rc && rc != DIES_ETIMEOUT && rc != DIES_ERANGE) return rc;
   *out = m->p.stats;
   return rc;
 }
@@ -1045,7 +1145,7 @@ void dies_destroy_model(dies_model *m) { delete m; }
 
 // ------------------------------------------------ frozen pass, no allocation
 // Scratch of dies_run_frozen_static: the per-shell re-emission CDF rows, then
-// the work counter, event counters, energy sums and status word.  Host code
+// the work counter, event counters, energy sums, status word and escaping SED.  Host code
 // must not use the symbol as an address; it looks the device address up once
 // per device below.
 namespace {
@@ -1055,7 +1155,8 @@ constexpr size_t kStaticEnergies = kStaticCdfBytes + 128;   // 8 x double
 constexpr size_t kStaticQueue = kStaticCdfBytes + 192;      // 2 x u64
 constexpr size_t kStaticStatus = kStaticCdfBytes + 208;     // u32
 constexpr size_t kStaticDiag = kStaticCdfBytes + 256;       // 16 x u32
-constexpr size_t kStaticZeroBytes = 320;                    // counters .. diag
+constexpr size_t kStaticSed = kStaticCdfBytes + 320;        // 64 x double: the escaping SED
+constexpr size_t kStaticZeroBytes = 320 + 64 * 8;           // counters .. SED
 static_assert(kStaticCdfBytes + kStaticZeroBytes <= DIES_STATIC_SCRATCH_BYTES, "static scratch too small");
 }  // namespace
 
@@ -1063,8 +1164,9 @@ static __device__ __align__(256) unsigned char g_static_scratch[DIES_STATIC_SCRA
 
 namespace {
 constexpr int kMaxDevices = 64;
-unsigned char *g_static_addr[kMaxDevices];
-std::atomic<int> g_static_ready[kMaxDevices];
+// per device: the scratch array's device address once looked up (null before);
+// threads racing on the first lookup store the same value
+std::atomic<unsigned char *> g_static_addr[kMaxDevices];
 
 // Device address of the scratch array on the current device (looked up on the
 // first call per device).
@@ -1073,15 +1175,16 @@ int static_scratch(unsigned char **out) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(DIES_ECUDA, "cudaGetDevice failed: %s", cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return fail(DIES_ECUDA, "device index %d out of range", dev);
-  if (g_static_ready[dev].load(std::memory_order_acquire) == 0) {
+  unsigned char *a = g_static_addr[dev].load(std::memory_order_acquire);
+  if (a == nullptr) {
     void *p = nullptr;
     e = cudaGetSymbolAddress(&p, g_static_scratch);
     if (e != cudaSuccess || p == nullptr)
       return fail(DIES_ECUDA, "cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(e));
-    g_static_addr[dev] = (unsigned char *)p;
-    g_static_ready[dev].store(1, std::memory_order_release);
+    a = static_cast<unsigned char *>(p);
+    g_static_addr[dev].store(a, std::memory_order_release);
   }
-  *out = g_static_addr[dev];
+  *out = a;
   return DIES_OK;
 }
 }  // namespace
@@ -1105,20 +1208,21 @@ int dies_run_frozen_static(dies_model *m, const double *T_frozen_dev, uint64_t n
   unsigned char *scr = nullptr;
   int rc = static_scratch(&scr);
   if (rc) return rc;
+  const unsigned long long launches0 = dies::g_launches.load();
   DIES_CUDA(cudaMemsetAsync(scr + kStaticCounters, 0, kStaticZeroBytes, p.stream));
   DIES_CUDA(cudaMemsetAsync(E_abs_dev, 0, (size_t)p.n_cells * 8, p.stream));
-  DIES_CUDA(cudaMemsetAsync(sed_dev, 0, (size_t)p.F * 8, p.stream));
   double *cdf = reinterpret_cast<double *>(scr);
   DIES_CUDA(launch_frozen_cdf(p.stream, p.n_cells, p.F, p.at<double>(p.lay.freq), p.at<double>(p.lay.kabs),
                               p.at<double>(p.lay.dnu), T_frozen_dev, cdf));
   int occ = 0;
-  DIES_CUDA(transport_occupancy(PREC_FP64, MODE_FROZEN, p.block, next_pow2(p.n_tnodes), false, false, false, &occ));
+  DIES_CUDA(transport_occupancy(PREC_FP64, MODE_FROZEN, p.block, next_pow2(p.n_tnodes), false, false, false, false,
+                                &occ));
   if (occ < 1) return fail(DIES_ECUDA, "transport kernel cannot be resident with block size %d", p.block);
   const int bps = (p.blocks_per_sm > 0 && p.blocks_per_sm < occ) ? p.blocks_per_sm : occ;
   const int mode = (flags == DIES_FROZEN_ABSORB_TERMINAL) ? MODE_FROZEN_TERMINAL : MODE_FROZEN;
   TransportParams P = p.params(mode, n, seed);
   P.E = E_abs_dev;
-  P.sed = sed_dev;
+  P.sed = reinterpret_cast<double *>(scr + kStaticSed);  // copied to sed_dev below
   P.cell_cdf = cdf;
   P.rec_events = n_events_dev;
   P.rec_hash = reinterpret_cast<unsigned long long *>(path_hash_dev);
@@ -1129,6 +1233,17 @@ int dies_run_frozen_static(dies_model *m, const double *T_frozen_dev, uint64_t n
   P.diag = reinterpret_cast<uint32_t *>(scr + kStaticDiag);
   const bool record = n_events_dev || path_hash_dev;
   DIES_CUDA(launch_transport(PREC_FP64, mode, record, P, p.sm_count * bps, p.block, p.stream));
+  DIES_CUDA(cudaMemcpyAsync(sed_dev, scr + kStaticSed, (size_t)p.F * 8, cudaMemcpyDeviceToDevice, p.stream));
+  // dies_get_stats on this handle reads the pass's status and counters from the scratch
+  p.launches_at_start = launches0;
+  p.static_counters = scr + kStaticCounters;
+  p.static_energies = scr + kStaticEnergies;
+  p.static_status = scr + kStaticStatus;
+  p.static_diag = scr + kStaticDiag;
+  p.static_sed = scr + kStaticSed;
+  p.has_result = true;
+  p.stats_pending = true;
+  p.static_pending = true;
   return DIES_OK;
 }
 
@@ -1188,6 +1303,11 @@ int dies_batch_set_launch(dies_batch *b, int block_size, int blocks_per_sm, int 
   return set_launch(b->p, block_size, blocks_per_sm, rare_batch, inner_moves, aggregate_atomics);
 }
 
+int dies_batch_set_launch_ex(dies_batch *b, const dies_launch *launch) {
+  if (!b) return fail(DIES_EINVAL, "batch is NULL");
+  return set_launch_ex(b->p, launch);
+}
+
 int dies_batch_set_weighting(dies_batch *b, const dies_weighting *w) {
   if (!b) return fail(DIES_EINVAL, "batch is NULL");
   return set_weighting_ex(b->p, w);
@@ -1224,7 +1344,7 @@ int dies_batch_get_escaping_sed(dies_batch *b, double *L, int n) {
 int dies_batch_get_stats(dies_batch *b, dies_stats *out) {
   if (!b || !out) return fail(DIES_EINVAL, "NULL argument");
   int rc = b->p.collect();
-  if (rc && rc != DIES_ETIMEOUT) return rc;
+  if (rc && rc != DIES_ETIMEOUT && rc != DIES_ERANGE) return rc;
   *out = b->p.stats;
   return rc;
 }

@@ -45,6 +45,7 @@ enum : uint32_t {
   STATUS_BAD_FREQ = 4u,
   STATUS_STUCK = 8u,   // a warp ran kFlightLimit moves without a rare event; its moving lanes were ended
   STATUS_ABANDONED = 16u,  // a package was still in flight when its lane left the work loop
+  STATUS_RANGE = 32u,      // all-FP32 form: an absorbed-energy counter left the FP32 range
 };
 
 // Consecutive loop iterations a warp may run without any lane finishing a
@@ -63,7 +64,7 @@ struct alignas(16) ModelDesc {
   double R;        // outer radius (length units)
   double L[2];     // source luminosities (erg/s), written by the table build
   unsigned long long pkg_off;  // first source slot of this model (slots x packages = work items)
-  float Lf[2];     // the luminosities as float (package energies of the FP32 forms)
+  float Lf[2];     // the luminosities as float (unused by the transport: package energies come from L)
   float Rf;        // outer radius as float
   float pad1;
 };
@@ -104,6 +105,7 @@ struct TransportParams {
   const uint16_t *nguide;   // FP32 forms: [kGuide] first node of each bucket of float(Lambda) bits
   const int *nmeta;         // {bits of Lambda_0, bucket shift}
   const double *dcdf_d;
+  const float *dcdf_f;      // FP32 forms with remit_cdf: the re-emission CDF rows in FP32
   int n_tnodes;
   int n_tnodes_pow2;        // smallest power of two >= n_tnodes
   // frozen pass
@@ -137,14 +139,18 @@ struct TransportParams {
   int mode;
   unsigned long long max_events;
   unsigned long long time_budget_ns;
-  float inv_n;      // 1 / n_per_source (FP32 package energies)
+  float inv_n;      // 1 / n_per_source
+  double inv_nd;    // 1 / n_per_source in FP64 (package energy L / N, formed once per package)
   float k_bg_f;     // k_bg as float (FP32 forms)
   int kbg_plain;    // k_bg == 1/2: no weighting
   int r64;          // MIXED form: some model has FP64 crossing distances in its inner shells
   int batch_min;    // lanes that must wait for a rare event before a warp runs them together
   int inner;        // moves per lane between two warp-collective sections (>= 1)
-  unsigned chunk;   // work items a warp takes from the counter at a time (multiple of 32, >= 32)
+  unsigned chunk;   // work items a warp takes from the counter at a time (multiple of 32, >= 32; set at launch)
+  unsigned refill_div;  // the chunk is about 1/refill_div of a warp's share of the launch (0 = 64)
   int agg;          // FP32 forms: warp-aggregated absorption atomics (lanes sharing a cell add once)
+  int remit_cdf;    // FP32 forms: re-emission bin by binary search of CDF rows instead of alias rows
+  int pool;         // FP32 forms without forced interaction: two packages per thread (per-warp pools)
 };
 
 // Alias-table entries (FP32 forms): bits 6..31 the 26-bit acceptance

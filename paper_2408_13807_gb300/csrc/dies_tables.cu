@@ -122,7 +122,7 @@ __global__ void k_freq_tables(int F, const double *nu, const double *J, const do
 // Blocks j >= n pad the search tables with +inf up to a power of two.
 __global__ void k_node_tables(int F, int n, double T_min, double T_max, const double *nu, const double *kabs,
                               const double *dnu, double *Lnode_d, float *Lnode_f, double *lnT, uint32_t *dalias,
-                              double *dcdf_d) {
+                              double *dcdf_d, float *dcdf_f) {
   __shared__ double sh[2];
   __shared__ double total;
   __shared__ double wsh[kMaxFreq];
@@ -158,6 +158,7 @@ __global__ void k_node_tables(int F, int n, double T_min, double T_max, const do
   double v = (tot > 0.0) ? c / tot : (double)(k + 1) / F;
   if (k >= F - 1) v = 1.0;
   dcdf_d[(size_t)j * kMaxFreq + k] = v;
+  dcdf_f[(size_t)j * kMaxFreq + k] = (float)v;  // FP32 forms with CDF rows (a launch option)
   wsh[k] = (k < F) ? d : 0.0;
   __syncthreads();
   if (k == 0) build_alias(wsh, F, dalias + (size_t)j * kMaxFreq);
@@ -278,10 +279,10 @@ cudaError_t launch_freq_tables(cudaStream_t st, int F, const double *nu, const d
 
 cudaError_t launch_node_tables(cudaStream_t st, int F, int n, int n_pow2, double T_min, double T_max,
                                const double *nu, const double *kabs, const double *dnu, double *Lnode_d,
-                               float *Lnode_f, double *lnT, uint32_t *dalias, double *dcdf_d, uint16_t *nguide,
-                               int *nmeta) {
+                               float *Lnode_f, double *lnT, uint32_t *dalias, double *dcdf_d, float *dcdf_f,
+                               uint16_t *nguide, int *nmeta) {
   k_node_tables<<<n_pow2, kMaxFreq, 0, st>>>(F, n, T_min, T_max, nu, kabs, dnu, Lnode_d, Lnode_f, lnT, dalias,
-                                             dcdf_d);
+                                             dcdf_d, dcdf_f);
   k_node_guide<<<1, kGuide, 0, st>>>(n, Lnode_f, nguide, nmeta);
   launch_counter_add(2);
   return cudaGetLastError();

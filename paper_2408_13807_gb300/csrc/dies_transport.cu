@@ -88,6 +88,12 @@ struct Shared {
   unsigned long long wq_next[kMaxWarps], wq_end[kMaxWarps];
 };
 
+// Byte offset of the per-warp package pools (pool variant) in a CTA's
+// dynamic shared memory: after the Shared block and the node table.
+__host__ __device__ constexpr size_t pool_offset(int n_tnodes_pow2) {
+  return (sizeof(Shared) + sizeof(float) * (size_t)n_tnodes_pow2 + 15) & ~(size_t)15;
+}
+
 template <class Real>
 struct Lane {
   Real p2, s, tauA, tauS, w, acc, tau_int, s0, u_type;
@@ -186,6 +192,20 @@ __device__ __forceinline__ int node_count_guided(const Shared &S, const float *L
   while (j < n && L[j] <= e) ++j;
   return j;
 }
+// The same count, also returning the first node above e (+inf past the table)
+// that the scan has loaded anyway.
+__device__ __forceinline__ int node_count_guided_hi(const Shared &S, const float *L, int n, float e, float &hi) {
+  const int d = __float_as_int(e) - S.g_b0;
+  const int b = d < 0 ? 0 : min(d >> S.g_sh, kGuide - 1);
+  int j = S.nguide[b];
+  float v = (j < n) ? L[j] : __int_as_float(0x7f800000);
+  while (v <= e) {
+    ++j;
+    v = (j < n) ? L[j] : __int_as_float(0x7f800000);
+  }
+  hi = v;
+  return j;
+}
 
 // ------------------------------------------- weighted sampling (Sect. 2.2)
 // Henyey-Greenstein cosine by inversion of its CDF (Eq. 6 form; |g| < 1e-6
@@ -230,6 +250,17 @@ __device__ __forceinline__ int node_count_f(const float *L, int pow2, float e) {
 __device__ __forceinline__ int node_count_d(const double *Ld, int n, int j, double e) {
   while (j < n && __ldg(Ld + j) <= e) ++j;
   while (j > 0 && __ldg(Ld + j - 1) > e) --j;
+  return j;
+}
+
+// The same exact count for e >= 0 with the comparisons on the integer pipes:
+// non-negative finite doubles order like their bit patterns.  The float
+// estimate j (from the float table) is at most one node off, because adjacent
+// nodes differ by far more than a float's rounding.
+__device__ __forceinline__ int node_count_bits(const double *Ld, int n, int j, double e) {
+  const long long eb = __double_as_longlong(e);
+  if (j < n && __double_as_longlong(__ldg(Ld + j)) <= eb) return j + 1;
+  if (j > 0 && __double_as_longlong(__ldg(Ld + j - 1)) > eb) return j - 1;
   return j;
 }
 
@@ -579,7 +610,9 @@ __device__ __forceinline__ void assign(const TransportParams &P, Lane<typename R
   L.n = __ldg(&D->n_cells);
   L.n64 = __ldg(&D->n_fp64);
   if constexpr (PREC == PREC_FP64) L.eps = __ldg(&D->L[L.src]) / (double)P.n_per_source;
-  else L.eps = __ldg(&D->Lf[L.src]) * P.inv_n;
+  // FP32 forms: the package energy L / N rounded once to float (formed in
+  // FP64: a luminosity above the float range still gives a float energy)
+  else L.eps = __double2float_rn(__ldg(&D->L[L.src]) * P.inv_nd);
   L.pkg_lo = (uint32_t)pkg;
   L.pkg_hi = (uint32_t)(pkg >> 32);
   L.blk = 0;
@@ -841,7 +874,10 @@ __device__ __forceinline__ void absorb(const TransportParams &P, Shared &S, cons
   T.abs++;
   if constexpr (RECORD) L.nabs++;
   if constexpr (MODE == MODE_FROZEN_TERMINAL) {
-    atomicAdd(P.E + gc, (double)L.w * (double)L.eps);
+    // the package energy in FP64 in every form (a test mode: the tally must
+    // match the FP64 injected energy, not the float package energy)
+    if constexpr (PREC == PREC_FP64) atomicAdd(P.E + gc, L.w * L.eps);
+    else atomicAdd(P.E + gc, (double)L.w * (__ldg(&P.desc[L.model].L[L.src]) * P.inv_nd));
     record<RECORD>(L, EV_ABSORB, L.cell, L.f);
     finish<RECORD>(P, L);
     return;
@@ -897,8 +933,10 @@ __device__ __forceinline__ void absorb(const TransportParams &P, Shared &S, cons
     const float u_ts = u01f_word(a.w);
     const float u_ta = u01f((a.x & 0x1ffu) | ((a.y & 0x1ffu) << 9) | ((a.z & 0x1fu) << 18));
     const float dEf = L.w * L.eps;
-    const float im = __ldg(P.inv_massf + gc);
-    float eo;
+    // E_old: MIXED from the FP64 accumulator (old_d, plus pre_d of this lane's
+    // group predecessors), as a float in old_f; FP32 form from its two counters
+    double old_d = 0.0;
+    float old_f = 0.0f, pre_lane = 0.0f;
     if (P.agg) {
       // Lanes of this warp absorbing in the same cell add their energies
       // with one atomic; each lane's E_old is the group's old value plus the
@@ -914,26 +952,62 @@ __device__ __forceinline__ void absorb(const TransportParams &P, Shared &S, cons
         tot += v;
         if (below & (1u << j)) pre += v;
       }
-      float old = 0.0f;
       if constexpr (PREC == PREC_MIXED) {
-        if (lane == lead) old = d2f_nonneg(atomicAdd(P.E + gc, f2d_nonneg(tot)));
+        double old = 0.0;
+        if (lane == lead) old = atomicAdd(P.E + gc, f2d_nonneg(tot));
+        old_d = __shfl_sync(grp, old, lead);
+        old_f = d2f_nonneg(old_d) + pre;
+        pre_lane = pre;
       } else {
+        float old = 0.0f;
         if (lane == lead) old = __ldg(P.Eprev + gc) + atomicAdd(P.Ecur + gc, tot);
+        old_f = __shfl_sync(grp, old, lead) + pre;
       }
-      eo = (__shfl_sync(grp, old, lead) + pre) * im;
     } else if constexpr (PREC == PREC_MIXED) {
-      // FP64 accumulator; its old value gives e_old, the lookup is FP32
-      eo = d2f_nonneg(atomicAdd(P.E + gc, f2d_nonneg(dEf))) * im;
+      old_d = atomicAdd(P.E + gc, f2d_nonneg(dEf));
+      old_f = d2f_nonneg(old_d);
     } else {
       // FP32 form: two FP32 counters, E = E_prev (frozen in this batch) + E_cur
-      eo = (__ldg(P.Eprev + gc) + atomicAdd(P.Ecur + gc, dEf)) * im;
+      old_f = __ldg(P.Eprev + gc) + atomicAdd(P.Ecur + gc, dEf);
     }
-    const float de = dEf * im;
-    const float es = fmaf(u_e, de, eo);
-    const int j = node_count_guided(S, sLnode, P.n_tnodes, es);
-    if (eo + de > sLnode[P.n_tnodes - 1]) atomicAdd(&S.rare[CNT_CLAMP_HI], 1u);
+    if constexpr (PREC == PREC_FP32) {
+      if (!(old_f < 1.0e38f)) atomicOr(P.status, STATUS_RANGE);  // the run then reports DIES_ERANGE
+    }
+    int j;
+    float en;  // e_new (table units), for the clamp counter
+    if constexpr (PREC == PREC_MIXED) {
+      // The row is the node interval holding e* = (E_old + u_e dE) / mass.
+      // When e_new stays below the node above e_old by more than float
+      // rounding (2^-20 relative), the interval of e_old holds e* for every
+      // u_e, and the float energies decide it.  Otherwise (an absorption whose
+      // [e_old, e_new] reaches a node: ~1e-4 of them in a well-filled cell)
+      // e* is formed in FP64 and searched exactly against the FP64 nodes: in
+      // a cell holding more than ~2^24 package energies dE is below one float
+      // ulp of E_old, where an FP32 e* would always take the interval of e_old.
+      const float im = __ldg(P.inv_massf + gc);
+      const float eo = old_f * im;
+      en = fmaf(dEf, im, eo);
+      float hi;
+      j = node_count_guided_hi(S, sLnode, P.n_tnodes, eo, hi);
+      if (en >= hi * (1.0f - 0x1p-20f)) {
+        const double od = old_d + f2d_nonneg(pre_lane);
+        const double es_d = fma(f2d_nonneg(u_e), f2d_nonneg(dEf), od) * __ldg(P.inv_mass + gc);
+        j = node_count_bits(P.Lnode_d, P.n_tnodes, node_count_guided(S, sLnode, P.n_tnodes, d2f_nonneg(es_d)),
+                            es_d);
+      }
+    } else {
+      const float im = __ldg(P.inv_massf + gc);
+      const float eo = old_f * im, de = dEf * im;
+      j = node_count_guided(S, sLnode, P.n_tnodes, fmaf(u_e, de, eo));
+      en = eo + de;
+    }
+    if (en > sLnode[P.n_tnodes - 1]) atomicAdd(&S.rare[CNT_CLAMP_HI], 1u);
     const int row = min(j, P.n_tnodes - 1);
-    set_freq<PREC>(S, L, alias_pick_ldg(P.dalias + ((size_t)row << kFreqShift), a.y >> 9));
+    // re-emission bin from the row of the interval holding e* (a launch option:
+    // one probe of an alias row, or a binary search of an FP32 CDF row)
+    const int f_new = P.remit_cdf ? cdf_pick_ldg(P.dcdf_f + ((size_t)row << kFreqShift), u01f_word(a.y))
+                                  : alias_pick_ldg(P.dalias + ((size_t)row << kFreqShift), a.y >> 9);
+    set_freq<PREC>(S, L, f_new);
     float r2 = L.p2 + L.s * L.s;
     float r = sqrtf(r2);
     if (P.remit_random) {
@@ -1101,16 +1175,47 @@ __device__ __forceinline__ unsigned long long globaltimer() {
   return t;
 }
 
-// The FP32 forms are held to 48 registers (5 CTAs of 256 per SM): the
-// forced-interaction state would otherwise cost a CTA per SM, which is worth
-// more than the few spills in the rare-event path (measured).
-template <int PREC, int MODE, bool RECORD, int OPT>
-__global__ void __launch_bounds__(256, PREC == PREC_FP64 ? 1 : 5) k_transport(const TransportParams P) {
-  using Real = typename RealOf<PREC>::T;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Shared &S = *reinterpret_cast<Shared *>(smem_raw);
-  float *sLnode = reinterpret_cast<float *>(smem_raw + sizeof(Shared));
+// Refill the finished lanes (ST_DEAD) of the warp from the warp's chunk of
+// work items: a full-warp collective in which lane 0 alone touches the
+// warp's cursor and takes a new chunk from the device counter when this one
+// runs out.  A lane beyond the launch's work ends in ST_DONE.
+template <int PREC, bool RECORD>
+__device__ __forceinline__ void refill(const TransportParams &P, Shared &S, Lane<typename RealOf<PREC>::T> &L) {
+  const int lane = threadIdx.x & 31;
+  const unsigned dead = __ballot_sync(kFull, L.st == ST_DEAD);
+  if (dead == 0u) return;
+  const unsigned c = __popc(dead);
+  unsigned long long b1 = 0, b2 = 0;
+  unsigned n1 = 0;
+  if (lane == 0) {
+    // P.chunk >= 32 >= c, so one new chunk always covers the shortfall
+    const int w = threadIdx.x >> 5;
+    const unsigned long long nx = S.wq_next[w];
+    n1 = (unsigned)min((unsigned long long)c, S.wq_end[w] - nx);
+    b1 = nx;
+    if (n1 < c) {
+      b2 = atomicAdd(P.queue, (unsigned long long)P.chunk);
+      S.wq_next[w] = b2 + (c - n1);
+      S.wq_end[w] = b2 + P.chunk;
+    } else {
+      S.wq_next[w] = nx + n1;
+    }
+  }
+  b1 = __shfl_sync(kFull, b1, 0);
+  b2 = __shfl_sync(kFull, b2, 0);
+  n1 = __shfl_sync(kFull, n1, 0);
+  if (L.st == ST_DEAD) {
+    const unsigned r = __popc(dead & ((1u << lane) - 1u));
+    const unsigned long long g = (r < n1) ? b1 + r : b2 + (r - n1);
+    if (g < P.total) assign<PREC, RECORD>(P, L, g);
+    else L.st = ST_DONE;
+  }
+}
 
+// Per-CTA set-up shared by the transport kernels: per-frequency coefficients,
+// HG constants, source tables and the node table into shared memory, tallies
+// and work cursors zeroed, the Philox key read (the caller synchronises).
+__device__ __forceinline__ void stage_tables(const TransportParams &P, Shared &S, float *sLnode) {
   for (int k = threadIdx.x; k < kMaxFreq; k += blockDim.x) {
     const bool in = k < P.F;
     const double ka = in ? P.kabs_d[k] : 0.0, ks = in ? P.ksca_d[k] : 0.0, g = in ? P.g_d[k] : 0.0;
@@ -1149,6 +1254,48 @@ __global__ void __launch_bounds__(256, PREC == PREC_FP64 ? 1 : 5) k_transport(co
     S.key[0] = (uint32_t)seed;
     S.key[1] = (uint32_t)(seed >> 32);
   }
+}
+
+// End of a CTA's work: per-lane event counters and the CTA's shared-memory
+// tallies into the device counters (no warp collectives).
+template <int PREC>
+__device__ __forceinline__ void flush_tallies(const TransportParams &P, Shared &S, const Tally &T) {
+  if (T.cross) atomicAdd(&S.rare[CNT_CROSS], T.cross);
+  if (T.scat) atomicAdd(&S.rare[CNT_SCATTER], T.scat);
+  if (T.abs) atomicAdd(&S.rare[CNT_ABSORB], T.abs);
+  if constexpr (PREC == PREC_FP64) {
+    if (T.e_inj != 0.0) atomicAdd(P.energies + EN_INJECTED, T.e_inj);
+    if (T.e_direct != 0.0) atomicAdd(P.energies + EN_DIRECT, T.e_direct);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < CNT_COUNT; i += blockDim.x)
+    if (S.rare[i]) atomicAdd(P.counters + i, (unsigned long long)S.rare[i]);
+  if (PREC != PREC_FP64 && P.n_models == 1) {
+    auto pair = [](unsigned int lo, unsigned int hi) { return ((unsigned long long)hi << 32) | lo; };
+    for (int i = threadIdx.x; i < 2 * kMaxFreq; i += blockDim.x) {
+      const unsigned long long v = pair(S.sed_lo[i >> 6][i & 63], S.sed_hi[i >> 6][i & 63]);
+      if (v) atomicAdd(P.sed_q + i, v);
+    }
+    if (threadIdx.x < 2) {
+      const unsigned long long vi = pair(S.inj_lo[threadIdx.x], S.inj_hi[threadIdx.x]);
+      const unsigned long long vd = pair(S.dir_lo[threadIdx.x], S.dir_hi[threadIdx.x]);
+      if (vi) atomicAdd(P.inj_q + threadIdx.x, vi);
+      if (vd) atomicAdd(P.dir_q + threadIdx.x, vd);
+    }
+  }
+}
+
+// The FP32 forms are held to 48 registers (5 CTAs of 256 per SM): the
+// forced-interaction state would otherwise cost a CTA per SM, which is worth
+// more than the few spills in the rare-event path (measured).
+template <int PREC, int MODE, bool RECORD, int OPT>
+__global__ void __launch_bounds__(256, PREC == PREC_FP64 ? 1 : 5) k_transport(const TransportParams P) {
+  using Real = typename RealOf<PREC>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Shared &S = *reinterpret_cast<Shared *>(smem_raw);
+  float *sLnode = reinterpret_cast<float *>(smem_raw + sizeof(Shared));
+
+  stage_tables(P, S, sLnode);
   __syncthreads();
 
   Tally T;
@@ -1214,38 +1361,8 @@ __global__ void __launch_bounds__(256, PREC == PREC_FP64 ? 1 : 5) k_transport(co
     }
     idle = 0;
     if (L.st == ST_ESCAPE) escape<PREC, RECORD>(P, S, L);
-    // refill the finished lanes from the warp's chunk of work items (a
-    // full-warp collective: lane 0 alone touches the warp's cursor and takes
-    // a new chunk from the device counter when this one runs out)
-    const unsigned dead = __ballot_sync(kFull, L.st == ST_DEAD);
-    if (dead != 0u) {
-      const unsigned c = __popc(dead);
-      unsigned long long b1 = 0, b2 = 0;
-      unsigned n1 = 0;
-      if (lane == 0) {
-        // P.chunk >= 32 >= c, so one new chunk always covers the shortfall
-        const int w = threadIdx.x >> 5;
-        const unsigned long long nx = S.wq_next[w];
-        n1 = (unsigned)min((unsigned long long)c, S.wq_end[w] - nx);
-        b1 = nx;
-        if (n1 < c) {
-          b2 = atomicAdd(P.queue, (unsigned long long)P.chunk);
-          S.wq_next[w] = b2 + (c - n1);
-          S.wq_end[w] = b2 + P.chunk;
-        } else {
-          S.wq_next[w] = nx + n1;
-        }
-      }
-      b1 = __shfl_sync(kFull, b1, 0);
-      b2 = __shfl_sync(kFull, b2, 0);
-      n1 = __shfl_sync(kFull, n1, 0);
-      if (L.st == ST_DEAD) {
-        const unsigned r = __popc(dead & lanes_below);
-        const unsigned long long g = (r < n1) ? b1 + r : b2 + (r - n1);
-        if (g < P.total) assign<PREC, RECORD>(P, L, g);
-        else L.st = ST_DONE;
-      }
-    }
+    // refill the finished lanes from the warp's chunk of work items
+    refill<PREC, RECORD>(P, S, L);
     if ((unsigned)(L.st - ST_SCATTER) <= (unsigned)(ST_FFIEND - ST_SCATTER)) rare<PREC, MODE, RECORD, OPT>(P, S, sLnode, L, T);
     if ((++sections & 31u) == 0 && L.st != ST_DONE && (globaltimer() - t0) > P.time_budget_ns) {
       // time budget reached: this lane gives up its package and its share of the work
@@ -1256,31 +1373,257 @@ __global__ void __launch_bounds__(256, PREC == PREC_FP64 ? 1 : 5) k_transport(co
   }
   if (!timed_out && L.st != ST_DONE) atomicOr(P.status, STATUS_ABANDONED);
 
-  // per-lane counters through shared / global atomics (no warp collectives
-  // after the work loop)
-  if (T.cross) atomicAdd(&S.rare[CNT_CROSS], T.cross);
-  if (T.scat) atomicAdd(&S.rare[CNT_SCATTER], T.scat);
-  if (T.abs) atomicAdd(&S.rare[CNT_ABSORB], T.abs);
-  if constexpr (PREC == PREC_FP64) {
-    if (T.e_inj != 0.0) atomicAdd(P.energies + EN_INJECTED, T.e_inj);
-    if (T.e_direct != 0.0) atomicAdd(P.energies + EN_DIRECT, T.e_direct);
+  flush_tallies<PREC>(P, S, T);
+}
+
+// ------------------------------------------ two packages per thread (pool)
+// An option of the FP32 forms without forced first interaction (launch knob
+// packages_per_thread = 2).  Besides the package in its registers, every
+// lane owns two slots of a per-warp pool of 64 packages in shared memory.
+// A lane whose package stops for a scattering, an absorption or a start
+// leaves it in an empty slot and takes a package that is ready to move, so
+// the lanes of the warp keep crossing boundaries; the waiting events are
+// then run in passes of ONE kind, with as many lanes as the pool holds
+// events of that kind (the kind the warp can serve most of), instead of the
+// few lanes of each kind that happen to stop together.  Slot bookkeeping is
+// warp-synchronous: lane l keeps the kind of slots l and l + 32 in registers
+// (the State of the stored package, or kEmpty), and every assignment of
+// lanes to slots is derived from ballots by all 32 lanes.  No wait depends
+// on another warp.
+constexpr int kPool = 64;   // package slots per warp
+constexpr int kEmpty = 15;  // kind of an empty slot (else: the State of its package)
+
+__device__ __forceinline__ bool is_event(int st) {
+  return (unsigned)(st - ST_SCATTER) <= (unsigned)(ST_INJECT - ST_SCATTER);
+}
+
+// The state a package carries between events (FP32 forms, no forced
+// interaction) as four float4 in structure-of-arrays order: slot i of group
+// g at pool[g * kPool + i], so a warp's accesses to distinct slots do not
+// share banks more than the 128-bit access pattern requires.
+__device__ __forceinline__ void pool_put(float4 *pool, int slot, const Lane<float> &L) {
+  const uint32_t meta =
+      ((uint32_t)L.f & 63u) | ((uint32_t)L.src << 8) | ((uint32_t)L.st << 12) | ((uint32_t)L.next_ev << 16);
+  pool[slot] = make_float4(L.p2, L.s, L.w, L.acc);
+  pool[kPool + slot] = make_float4(L.lim, L.eps, __int_as_float(L.cell), __uint_as_float(meta));
+  pool[2 * kPool + slot] =
+      make_float4(__int_as_float(L.model), __int_as_float(L.gbase), __int_as_float(L.n), __int_as_float(L.n64));
+  pool[3 * kPool + slot] =
+      make_float4(__uint_as_float(L.events), __uint_as_float(L.blk), __uint_as_float(L.pkg_lo), __uint_as_float(L.pkg_hi));
+}
+
+__device__ __forceinline__ void pool_get(const float4 *pool, int slot, const Shared &S, Lane<float> &L) {
+  const float4 a = pool[slot], b = pool[kPool + slot], c = pool[2 * kPool + slot], d = pool[3 * kPool + slot];
+  L.p2 = a.x;
+  L.s = a.y;
+  L.w = a.z;
+  L.acc = a.w;
+  L.lim = b.x;
+  L.eps = b.y;
+  L.cell = __float_as_int(b.z);
+  const uint32_t meta = __float_as_uint(b.w);
+  L.f = (int)(meta & 63u);
+  L.src = (int)((meta >> 8) & 15u);
+  L.st = (int)((meta >> 12) & 15u);
+  L.next_ev = (int)(meta >> 16);
+  L.model = __float_as_int(c.x);
+  L.gbase = __float_as_int(c.y);
+  L.n = __float_as_int(c.z);
+  L.n64 = __float_as_int(c.w);
+  L.cell_off = L.gbase - L.model - 1;
+  L.events = __float_as_uint(d.x);
+  L.blk = __float_as_uint(d.y);
+  L.pkg_lo = __float_as_uint(d.z);
+  L.pkg_hi = __float_as_uint(d.w);
+  L.ka = S.kabs_f[L.f];
+  L.ks = S.ksca_f[L.f];
+}
+
+// slot of the r-th (from 0) set bit of the 64-bit slot mask (lo: slots 0-31)
+__device__ __forceinline__ int nth_slot(unsigned lo, unsigned hi, int r) {
+  const int nl = __popc(lo);
+  return r < nl ? (int)__fns(lo, 0, r + 1) : 32 + (int)__fns(hi, 0, r - nl + 1);
+}
+
+// Slot-kind bookkeeping of an assignment: the first n set slots of (lo, hi)
+// go, in order, to the first n lanes of src; each such slot takes the value
+// val of its lane.  Called by all 32 lanes; lane l updates slots l, l + 32.
+__device__ __forceinline__ void set_kinds(unsigned lo, unsigned hi, unsigned src, int n, int val, int &k0,
+                                          int &k1) {
+  const int lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1u;
+  const int r0 = __popc(lo & below), r1 = __popc(lo) + __popc(hi & below);
+  const bool a0 = ((lo >> lane) & 1u) && r0 < n, a1 = ((hi >> lane) & 1u) && r1 < n;
+  const int v0 = __shfl_sync(kFull, val, a0 ? (int)__fns(src, 0, r0 + 1) : lane);
+  const int v1 = __shfl_sync(kFull, val, a1 ? (int)__fns(src, 0, r1 + 1) : lane);
+  if (a0) k0 = v0;
+  if (a1) k1 = v1;
+}
+__device__ __forceinline__ void clear_kinds(unsigned lo, unsigned hi, int n, int &k0, int &k1) {
+  const int lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1u;
+  if (((lo >> lane) & 1u) && __popc(lo & below) < n) k0 = kEmpty;
+  if (((hi >> lane) & 1u) && __popc(lo) + __popc(hi & below) < n) k1 = kEmpty;
+}
+
+// After a block of moves: escapes tallied, stopped packages left in empty
+// slots, idle lanes given ready packages, finished lanes new work.
+template <int PREC, int OPT>
+__device__ __forceinline__ void pool_exchange(const TransportParams &P, Shared &S, float4 *pool, Lane<float> &L,
+                                              int &k0, int &k1) {
+  const int lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1u;
+  if (L.st == ST_ESCAPE) escape<PREC, false>(P, S, L);
+  const unsigned evl = __ballot_sync(kFull, is_event(L.st));
+  if (evl != 0u) {
+    const unsigned elo = __ballot_sync(kFull, k0 == kEmpty), ehi = __ballot_sync(kFull, k1 == kEmpty);
+    const int n = min(__popc(evl), __popc(elo) + __popc(ehi));
+    if (n > 0) {
+      set_kinds(elo, ehi, evl, n, L.st, k0, k1);
+      if ((evl >> lane) & 1u) {
+        const int r = __popc(evl & below);
+        if (r < n) {
+          pool_put(pool, nth_slot(elo, ehi, r), L);
+          L.st = ST_DEAD;
+        }
+      }
+    }
   }
+  const unsigned idl = __ballot_sync(kFull, L.st == ST_DEAD || L.st == ST_DONE);
+  if (idl != 0u) {
+    const unsigned rlo = __ballot_sync(kFull, k0 == ST_NORMAL), rhi = __ballot_sync(kFull, k1 == ST_NORMAL);
+    const int n = min(__popc(idl), __popc(rlo) + __popc(rhi));
+    if (n > 0) {
+      if ((idl >> lane) & 1u) {
+        const int r = __popc(idl & below);
+        if (r < n) pool_get(pool, nth_slot(rlo, rhi, r), S, L);
+      }
+      clear_kinds(rlo, rhi, n, k0, k1);
+    }
+  }
+  refill<PREC, false>(P, S, L);
+  __syncwarp();
+}
+
+// One pass of a single event kind: the kind of which the warp can serve the
+// most events now (those its lanes hold, plus those in slots that free or
+// displaced lanes can take).  Other lanes' packages are moved into empty
+// slots when the free lanes are too few.
+template <int PREC, int OPT>
+__device__ __forceinline__ void pool_pass(const TransportParams &P, Shared &S, const float *sLnode, float4 *pool,
+                                          Lane<float> &L, Tally &T, int &k0, int &k1) {
+  const int lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1u;
+  if (L.st == ST_ESCAPE) escape<PREC, false>(P, S, L);  // (an exchange always comes first; kept for safety)
+  const unsigned fre = __ballot_sync(kFull, L.st == ST_DEAD || L.st == ST_DONE);
+  const unsigned elo = __ballot_sync(kFull, k0 == kEmpty), ehi = __ballot_sync(kFull, k1 == kEmpty);
+  const int room = __popc(fre) + __popc(elo) + __popc(ehi);
+  int kind = -1, best = 0;
+  unsigned el = 0u, slo = 0u, shi = 0u;
+#pragma unroll
+  for (int e = ST_SCATTER; e <= ST_INJECT; ++e) {
+    const unsigned l = __ballot_sync(kFull, L.st == e);
+    const unsigned a = __ballot_sync(kFull, k0 == e), b = __ballot_sync(kFull, k1 == e);
+    const int served = __popc(l) + min(__popc(a) + __popc(b), min(room, 32 - __popc(l)));
+    if (served > best) {
+      best = served;
+      kind = e;
+      el = l;
+      slo = a;
+      shi = b;
+    }
+  }
+  if (kind < 0) return;
+  const int want = min(__popc(slo) + __popc(shi), 32 - __popc(el));
+  const unsigned oth = ~(el | fre);
+  const int ndisp = min(max(want - __popc(fre), 0), min(__popc(oth), __popc(elo) + __popc(ehi)));
+  if (ndisp > 0) {
+    set_kinds(elo, ehi, oth, ndisp, L.st, k0, k1);
+    if ((oth >> lane) & 1u) {
+      const int r = __popc(oth & below);
+      if (r < ndisp) {
+        pool_put(pool, nth_slot(elo, ehi, r), L);
+        L.st = ST_DEAD;
+      }
+    }
+  }
+  const unsigned fr2 = __ballot_sync(kFull, L.st == ST_DEAD || L.st == ST_DONE);
+  const int nload = min(want, __popc(fr2));
+  if (nload > 0) {
+    if ((fr2 >> lane) & 1u) {
+      const int r = __popc(fr2 & below);
+      if (r < nload) pool_get(pool, nth_slot(slo, shi, r), S, L);
+    }
+    clear_kinds(slo, shi, nload, k0, k1);
+  }
+  __syncwarp();
+  if (L.st == kind) rare<PREC, MODE_IRE, false, OPT>(P, S, sLnode, L, T);
+  __syncwarp();
+}
+
+template <int PREC, int OPT>
+__global__ void __launch_bounds__(256, 4) k_transport_pool(const TransportParams P) {
+  static_assert(PREC != PREC_FP64 && (OPT & OPT_NOFFI) != 0, "pool variant: FP32 forms without forced interaction");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Shared &S = *reinterpret_cast<Shared *>(smem_raw);
+  float *sLnode = reinterpret_cast<float *>(smem_raw + sizeof(Shared));
+  float4 *pool = reinterpret_cast<float4 *>(smem_raw + pool_offset(P.n_tnodes_pow2)) + (threadIdx.x >> 5) * (4 * kPool);
+  stage_tables(P, S, sLnode);
   __syncthreads();
-  for (int i = threadIdx.x; i < CNT_COUNT; i += blockDim.x)
-    if (S.rare[i]) atomicAdd(P.counters + i, (unsigned long long)S.rare[i]);
-  if (PREC != PREC_FP64 && P.n_models == 1) {
-    auto pair = [](unsigned int lo, unsigned int hi) { return ((unsigned long long)hi << 32) | lo; };
-    for (int i = threadIdx.x; i < 2 * kMaxFreq; i += blockDim.x) {
-      const unsigned long long v = pair(S.sed_lo[i >> 6][i & 63], S.sed_hi[i >> 6][i & 63]);
-      if (v) atomicAdd(P.sed_q + i, v);
+
+  Tally T;
+  T.cross = T.scat = T.abs = 0;
+  T.e_inj = T.e_direct = 0.0;
+  Lane<float> L;
+  L.st = ST_DEAD;
+  int k0 = kEmpty, k1 = kEmpty;
+  const unsigned long long t0 = globaltimer();
+  unsigned quiet = 0, sections = 0;
+  bool timed_out = false;
+  for (;;) {
+    bool pass = false;
+    for (int k = 0; k < P.inner; k += kCheck) {
+      const bool was_moving = L.st <= ST_FORCED;
+      if (was_moving) {
+#pragma unroll
+        for (int j = 0; j < kCheck; ++j) {
+          move<PREC, MODE_IRE, false, OPT>(P, S, L, T);
+          if (L.st > ST_FORCED) break;
+        }
+      }
+      // the flight watchdog counts blocks in which moving lanes moved but none stopped
+      if (__ballot_sync(kFull, was_moving && L.st > ST_FORCED) != 0u) quiet = 0;
+      else if (__ballot_sync(kFull, was_moving) != 0u) ++quiet;
+      if (__ballot_sync(kFull, L.st > ST_FORCED) == 0u) continue;
+      pool_exchange<PREC, OPT>(P, S, pool, L, k0, k1);
+      const int empty = __popc(__ballot_sync(kFull, k0 == kEmpty)) + __popc(__ballot_sync(kFull, k1 == kEmpty));
+      const int moving = __popc(__ballot_sync(kFull, L.st <= ST_FORCED));
+      if (empty < P.batch_min || moving <= 32 - P.batch_min) {
+        pass = true;
+        break;
+      }
     }
-    if (threadIdx.x < 2) {
-      const unsigned long long vi = pair(S.inj_lo[threadIdx.x], S.inj_hi[threadIdx.x]);
-      const unsigned long long vd = pair(S.dir_lo[threadIdx.x], S.dir_hi[threadIdx.x]);
-      if (vi) atomicAdd(P.inj_q + threadIdx.x, vi);
-      if (vd) atomicAdd(P.dir_q + threadIdx.x, vd);
+    if (__ballot_sync(kFull, L.st != ST_DONE) == 0u && __ballot_sync(kFull, k0 != kEmpty || k1 != kEmpty) == 0u)
+      break;
+    if (pass || __ballot_sync(kFull, L.st <= ST_FORCED) == 0u) pool_pass<PREC, OPT>(P, S, sLnode, pool, L, T, k0, k1);
+    if (quiet >= kFlightLimit) {
+      // watchdog: kFlightLimit blocks of moves without a stop; end the moving packages as lost
+      if (L.st <= ST_FORCED) {
+        lose<false>(P, S, L, CNT_KILL_CAP);
+        atomicOr(P.status, STATUS_STUCK);
+      }
+      quiet = 0;
+    }
+    if ((++sections & 31u) == 0 && (globaltimer() - t0) > P.time_budget_ns) {
+      // time budget reached: this warp gives up its packages and its share of the work
+      atomicOr(P.status, STATUS_TIMEOUT);
+      L.st = ST_DONE;
+      k0 = k1 = kEmpty;
+      timed_out = true;
     }
   }
+  if (!timed_out && L.st != ST_DONE) atomicOr(P.status, STATUS_ABANDONED);
+  flush_tallies<PREC>(P, S, T);
 }
 
 // FP32 forms: convert the fixed-point tallies of every model to energies
@@ -1348,12 +1691,13 @@ __global__ void k_merge_batches(int n_cells, float *Eprev, float *Ecur) {
   }
 }
 
-// Work chunk of a warp: about 1/64 of a warp's share of the launch, so that
-// the last chunks (at most kChunkMax / 32 packages per lane) end close together.
+// Work chunk of a warp: about 1/divisor of a warp's share of the launch
+// (default 1/64), so that the last chunks (at most kChunkMax / 32 packages
+// per lane) end close together while the device work counter sees few atomics.
 constexpr unsigned long long kChunkMin = 32, kChunkMax = 1024;
-unsigned chunk_size(unsigned long long total, int grid, int block) {
+unsigned chunk_size(unsigned long long total, int grid, int block, unsigned divisor) {
   const unsigned long long warps = (unsigned long long)grid * (unsigned long long)(block / 32);
-  unsigned long long c = total / (warps * 64ull + 1ull);
+  unsigned long long c = total / (warps * (unsigned long long)(divisor ? divisor : 64u) + 1ull);
   c = c < kChunkMin ? kChunkMin : (c > kChunkMax ? kChunkMax : c);
   return (unsigned)(c & ~31ull);
 }
@@ -1364,10 +1708,30 @@ cudaError_t launch_one(const TransportParams &P, int grid, int block, size_t sme
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   TransportParams Q = P;
-  Q.chunk = chunk_size(P.total, grid, block);
+  Q.chunk = chunk_size(P.total, grid, block, P.refill_div);
   kern<<<grid, block, smem, st>>>(Q);
   launch_counter_add(1);
   return cudaGetLastError();
+}
+
+template <int PREC, int OPT>
+cudaError_t launch_pool(const TransportParams &P, int grid, int block, size_t smem, cudaStream_t st) {
+  auto kern = k_transport_pool<PREC, OPT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  TransportParams Q = P;
+  Q.chunk = chunk_size(P.total, grid, block, P.refill_div);
+  kern<<<grid, block, smem, st>>>(Q);
+  launch_counter_add(1);
+  return cudaGetLastError();
+}
+
+template <int PREC, int OPT>
+cudaError_t occupancy_pool(int block, size_t smem, int *blocks_per_sm) {
+  auto kern = k_transport_pool<PREC, OPT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kern, block, smem);
 }
 
 template <int PREC, int MODE, bool RECORD, int OPT = 0>
@@ -1382,10 +1746,30 @@ cudaError_t occupancy_one(int block, size_t smem, int *blocks_per_sm) {
 
 size_t transport_smem_bytes(int n_tnodes_pow2) { return sizeof(Shared) + sizeof(float) * (size_t)n_tnodes_pow2; }
 
-// prec: PREC_*, mode: MODE_*; the frozen modes exist in the FP64 form only.
+// the pool variant: the per-warp package pools after the tables (16-byte aligned)
+size_t transport_smem_bytes_pool(int n_tnodes_pow2, int block) {
+  return pool_offset(n_tnodes_pow2) + (size_t)(block / 32) * 4 * kPool * sizeof(float4);
+}
+
+// prec: PREC_*, mode: MODE_*.  The re-emitting frozen mode exists in the
+// FP64 form only; the absorb-terminal mode also in the FP32 forms (single
+// model, no per-package records), for the pure-absorber closed forms.
 cudaError_t launch_transport(int prec, int mode, bool record, const TransportParams &P, int grid, int block,
                              cudaStream_t st) {
   const size_t smem = transport_smem_bytes(P.n_tnodes_pow2);
+  if (mode == MODE_FROZEN_TERMINAL && prec != PREC_FP64) {
+    if (record || P.n_models != 1) return cudaErrorInvalidValue;
+    constexpr int TM = MODE_FROZEN_TERMINAL;
+    if (prec == PREC_MIXED) {
+      if (P.ffi)
+        return P.r64 ? launch_one<PREC_MIXED, TM, false, OPT_R64>(P, grid, block, smem, st)
+                     : launch_one<PREC_MIXED, TM, false, 0>(P, grid, block, smem, st);
+      return P.r64 ? launch_one<PREC_MIXED, TM, false, OPT_R64 | OPT_NOFFI>(P, grid, block, smem, st)
+                   : launch_one<PREC_MIXED, TM, false, OPT_NOFFI>(P, grid, block, smem, st);
+    }
+    return P.ffi ? launch_one<PREC_FP32, TM, false, 0>(P, grid, block, smem, st)
+                 : launch_one<PREC_FP32, TM, false, OPT_NOFFI>(P, grid, block, smem, st);
+  }
   if (mode != MODE_IRE) {
     if (prec != PREC_FP64) return cudaErrorInvalidValue;
     if (mode == MODE_FROZEN)
@@ -1395,6 +1779,18 @@ cudaError_t launch_transport(int prec, int mode, bool record, const TransportPar
                   : launch_one<PREC_FP64, MODE_FROZEN_TERMINAL, false>(P, grid, block, smem, st);
   }
   const bool batch = P.n_models > 1 && !P.r64;  // batches run their own variants (grouped tallies)
+  if (P.pool && !P.ffi && prec != PREC_FP64) {
+    // two packages per thread: the pool variants (no forced interaction)
+    const size_t sp = transport_smem_bytes_pool(P.n_tnodes_pow2, block);
+    constexpr int NF = OPT_NOFFI;
+    if (prec == PREC_MIXED) {
+      if (batch) return launch_pool<PREC_MIXED, NF | OPT_BATCH>(P, grid, block, sp, st);
+      return P.r64 ? launch_pool<PREC_MIXED, NF | OPT_R64>(P, grid, block, sp, st)
+                   : launch_pool<PREC_MIXED, NF>(P, grid, block, sp, st);
+    }
+    return batch ? launch_pool<PREC_FP32, NF | OPT_BATCH>(P, grid, block, sp, st)
+                 : launch_pool<PREC_FP32, NF>(P, grid, block, sp, st);
+  }
   switch (prec) {
     case PREC_MIXED:
       if (batch)
@@ -1416,8 +1812,32 @@ cudaError_t launch_transport(int prec, int mode, bool record, const TransportPar
 }
 
 cudaError_t transport_occupancy(int prec, int mode, int block, int n_tnodes_pow2, bool r64, bool ffi, bool batch,
-                                int *blocks_per_sm) {
+                                bool pool, int *blocks_per_sm) {
   const size_t smem = transport_smem_bytes(n_tnodes_pow2);
+  if (pool && mode == MODE_IRE && !ffi && prec != PREC_FP64) {
+    const size_t sp = transport_smem_bytes_pool(n_tnodes_pow2, block);
+    constexpr int NF = OPT_NOFFI;
+    const bool b = batch && !r64;
+    if (prec == PREC_MIXED) {
+      if (b) return occupancy_pool<PREC_MIXED, NF | OPT_BATCH>(block, sp, blocks_per_sm);
+      return r64 ? occupancy_pool<PREC_MIXED, NF | OPT_R64>(block, sp, blocks_per_sm)
+                 : occupancy_pool<PREC_MIXED, NF>(block, sp, blocks_per_sm);
+    }
+    return b ? occupancy_pool<PREC_FP32, NF | OPT_BATCH>(block, sp, blocks_per_sm)
+             : occupancy_pool<PREC_FP32, NF>(block, sp, blocks_per_sm);
+  }
+  if (mode == MODE_FROZEN_TERMINAL && prec != PREC_FP64) {
+    constexpr int TM = MODE_FROZEN_TERMINAL;
+    if (prec == PREC_MIXED) {
+      if (ffi)
+        return r64 ? occupancy_one<PREC_MIXED, TM, false, OPT_R64>(block, smem, blocks_per_sm)
+                   : occupancy_one<PREC_MIXED, TM, false, 0>(block, smem, blocks_per_sm);
+      return r64 ? occupancy_one<PREC_MIXED, TM, false, OPT_R64 | OPT_NOFFI>(block, smem, blocks_per_sm)
+                 : occupancy_one<PREC_MIXED, TM, false, OPT_NOFFI>(block, smem, blocks_per_sm);
+    }
+    return ffi ? occupancy_one<PREC_FP32, TM, false, 0>(block, smem, blocks_per_sm)
+               : occupancy_one<PREC_FP32, TM, false, OPT_NOFFI>(block, smem, blocks_per_sm);
+  }
   if (mode != MODE_IRE) return occupancy_one<PREC_FP64, MODE_FROZEN, true>(block, smem, blocks_per_sm);
   if (batch && !r64 && prec == PREC_MIXED)
     return ffi ? occupancy_one<PREC_MIXED, MODE_IRE, false, OPT_BATCH>(block, smem, blocks_per_sm)

@@ -33,7 +33,10 @@ DIES_FFI_EXTINCTION = 1
 DIES_FFI_ABSORPTION = 2
 DIES_FROZEN_REEMIT = 0
 DIES_FROZEN_ABSORB_TERMINAL = 1
+DIES_FROZEN_FORM = 2
 DIES_MAX_FREQ = 64
+DIES_TABLE_ALIAS = 0
+DIES_TABLE_CDF = 1
 
 PREC = {"mixed": DIES_PREC_MIXED, "fp32": DIES_PREC_FP32, "fp64": DIES_PREC_FP64}
 
@@ -50,7 +53,7 @@ EXPORTS = (
     "dies_run_batch", "dies_run_batch_async", "dies_batch_get_temperatures", "dies_batch_get_escaping_sed",
     "dies_batch_get_stats", "dies_destroy_batch", "dies_last_error", "dies_launch_count", "dies_version",
     "dies_measure_peaks",
-    "dies_run_frozen_static",
+    "dies_run_frozen_static", "dies_set_launch_ex", "dies_batch_set_launch_ex",
 )
 
 
@@ -69,6 +72,7 @@ class dies_stats(ctypes.Structure):
         ("E_direct", ctypes.c_double), ("table_ms", ctypes.c_double), ("kernel_ms", ctypes.c_double),
         ("transport_ms", ctypes.c_double),
         ("status_word", ctypes.c_uint32), ("launches", ctypes.c_uint32), ("diag", ctypes.c_uint32 * 16),
+        ("upload_ms", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -153,6 +157,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "dies_batch_set_sources": (i, [_vp, _dp, d, _dp]),
         "dies_batch_set_stream": (i, [_vp, _vp]),
         "dies_batch_set_launch": (i, [_vp, i, i, i, i, i]),
+        "dies_set_launch_ex": (i, [_vp, _vp]),
+        "dies_batch_set_launch_ex": (i, [_vp, _vp]),
         "dies_run_batch": (i, [_vp, u64, u64]),
         "dies_run_batch_async": (i, [_vp, u64, u64]),
         "dies_batch_get_temperatures": (i, [_vp, _dp, i]),
@@ -225,6 +231,20 @@ def dies_set_launch(h, block_size: int, blocks_per_sm: int = 0, rare_batch: int 
                     aggregate_atomics: int = 0):
     return _check(load().dies_set_launch(h, int(block_size), int(blocks_per_sm), int(rare_batch), int(inner_moves),
                                          int(aggregate_atomics)))
+
+
+class dies_launch(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int) for k in ("block_size", "blocks_per_sm", "rare_batch", "inner_moves",
+                                             "aggregate_atomics", "refill_divisor", "reemit_table",
+                                             "packages_per_thread")]
+
+
+def dies_set_launch_ex(h, **kw):
+    return _check(load().dies_set_launch_ex(h, ctypes.byref(dies_launch(**kw))))
+
+
+def dies_batch_set_launch_ex(h, **kw):
+    return _check(load().dies_batch_set_launch_ex(h, ctypes.byref(dies_launch(**kw))))
 
 
 def dies_set_time_budget(h, seconds: float):
@@ -413,7 +433,8 @@ class Model:
     def __init__(self, cloud, precision: str = "mixed", n_batches: int = 1, fp64_radius: float = 0.0,
                  tgrid=(2.7, 1500.0, 1024), torch_memory: bool = True, device: int = 0, block_size: int = 256,
                  blocks_per_sm: int = 0, rare_batch: int = 16, inner_moves: int = 32, aggregate_atomics: int = 0,
-                 graph: bool = False):
+                 graph: bool = False, refill_divisor: int = 0, reemit_table: int = DIES_TABLE_ALIAS,
+                 packages_per_thread: int = 1):
         self.cloud = cloud
         self.h = dies_create_model(cloud.radii, cloud.rho, cloud.length_unit_cm)
         self.n_cells = cloud.n_cells
@@ -424,7 +445,10 @@ class Model:
         dies_set_weighting_ex(self.h, weighting_of(cloud))
         dies_set_precision(self.h, PREC[precision], n_batches, fp64_radius)
         dies_set_tgrid(self.h, *tgrid)
-        dies_set_launch(self.h, block_size, blocks_per_sm, rare_batch, inner_moves, aggregate_atomics)
+        dies_set_launch_ex(self.h, block_size=block_size, blocks_per_sm=blocks_per_sm, rare_batch=rare_batch,
+                           inner_moves=inner_moves, aggregate_atomics=aggregate_atomics,
+                           refill_divisor=refill_divisor, reemit_table=reemit_table,
+                                 packages_per_thread=packages_per_thread)
         dies_set_graph(self.h, graph)
         if torch_memory:
             stream, self._ws = _torch_stream_and_workspace(dies_workspace_bytes(self.h), device)
@@ -456,6 +480,13 @@ class Model:
         flags = DIES_FROZEN_ABSORB_TERMINAL if terminal else DIES_FROZEN_REEMIT
         return dies_run_frozen(self.h, T_frozen, n_packages, seed, flags, rows, record)
 
+    def run_terminal_in_form(self, n_packages: int, seed: int = 0):
+        """Absorb-terminal pass in this handle's precision form (pure-absorber
+        closed forms); read the result with absorbed() / sed() / stats()."""
+        T = np.full(self.n_cells, 10.0)
+        dies_run_frozen(self.h, T, n_packages, seed, DIES_FROZEN_ABSORB_TERMINAL | DIES_FROZEN_FORM, 0, False)
+        return self
+
     def close(self):
         dies_destroy_model(self.h)
         self.h = None
@@ -475,7 +506,8 @@ class Batch:
 
     def __init__(self, clouds, block_size: int = 256, blocks_per_sm: int = 0, rare_batch: int = 16,
                  inner_moves: int = 32, aggregate_atomics: int = 0, graph: bool = False,
-                 precision: str = "mixed", n_batches: int = 1):
+                 precision: str = "mixed", n_batches: int = 1, refill_divisor: int = 0,
+                 reemit_table: int = DIES_TABLE_ALIAS, packages_per_thread: int = 1):
         c0 = clouds[0]
         n = np.array([c.n_cells for c in clouds], dtype=np.int32)
         self.offsets = np.concatenate([[0], np.cumsum(n)]).astype(np.int32)
@@ -490,7 +522,10 @@ class Batch:
         J = next((c.J_ext for c in clouds if c.J_ext is not None), None)
         pt = next((c for c in clouds if c.L_point > 0), None)
         dies_batch_set_sources(self.h, J, pt.L_point if pt else 0.0, pt.point_spec if pt else None)
-        dies_batch_set_launch(self.h, block_size, blocks_per_sm, rare_batch, inner_moves, aggregate_atomics)
+        dies_batch_set_launch_ex(self.h, block_size=block_size, blocks_per_sm=blocks_per_sm, rare_batch=rare_batch,
+                                 inner_moves=inner_moves, aggregate_atomics=aggregate_atomics,
+                                 refill_divisor=refill_divisor, reemit_table=reemit_table,
+                                 packages_per_thread=packages_per_thread)
         dies_batch_set_graph(self.h, graph)
         dies_batch_set_weighting(self.h, weighting_of(c0))
         dies_batch_set_precision(self.h, PREC[precision], n_batches)

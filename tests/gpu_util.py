@@ -112,11 +112,14 @@ def check_sigma(r, alpha: float = ALPHA):
         f"largest |t| = {r['max_z']:.2f} over {r['n_gated']} shells: family-wise p = {r['p_familywise']:.2e}")
 
 
-def assert_ensembles_agree(Tg, To, rel_gate=0.01, min_gated=1, min_acc=1, alpha=ALPHA):
+def assert_ensembles_agree(Tg, To, rel_gate=0.01, min_gated=1, min_acc=None, alpha=ALPHA):
     """Acceptance: at least min_gated shells inside the 3-sigma gate and
-    min_acc inside the accuracy gate; every acc_gated shell agrees to better
-    than rel_gate; the gated shells pass both multiplicity-corrected sigma
-    criteria (see the module docstring)."""
+    min_acc (default min_gated / 2) inside the accuracy gate, so that the
+    1 % criterion covers a stated share of every run; every acc_gated shell
+    agrees to better than rel_gate; the gated shells pass both
+    multiplicity-corrected sigma criteria (see the module docstring)."""
+    if min_acc is None:
+        min_acc = max(1, min_gated // 2)
     r = compare_ensembles(Tg, To, rel_gate, alpha=alpha)
     assert r["n_gated"] >= min_gated, f"too few shells inside the sigma gate: {r['n_gated']} < {min_gated}"
     assert r["n_acc"] >= min_acc, f"too few shells inside the accuracy gate: {r['n_acc']} < {min_acc}"
@@ -141,3 +144,25 @@ def pooled_sigma_check(results, alpha=ALPHA):
          "p_familywise": float(p_fw), "max_z": float(zs.max()) if n else 0.0}
     check_sigma(r, alpha)
     return r
+
+
+def check_against_expectation(obs: np.ndarray, expect: np.ndarray, var: np.ndarray, alpha: float = ALPHA,
+                              min_expect: float = 0.0):
+    """Observed values against exact expectations with known variances
+    (Gaussian regime): over the entries with expect > min_expect, the count
+    beyond 3 sigma must stay within its binomial (1 - alpha) quantile and the
+    largest |z| within the Sidak bound.  Returns the z values."""
+    from scipy import stats
+    obs, expect, var = (np.asarray(a, np.float64) for a in (obs, expect, var))
+    use = expect > min_expect
+    z = (obs[use] - expect[use]) / np.sqrt(var[use])
+    n = int(use.sum())
+    assert n > 0, "no entry above the expectation threshold"
+    q3 = 2.0 * stats.norm.sf(3.0)
+    k3 = int(np.sum(np.abs(z) > 3.0))
+    k_max = int(stats.binom.ppf(1.0 - alpha, n, q3))
+    assert k3 <= k_max, f"{k3} of {n} entries beyond 3 sigma (chance allows {k_max})"
+    p_min = float(2.0 * stats.norm.sf(np.abs(z).max()))
+    p_fw = n * p_min if p_min < 1e-12 else 1.0 - (1.0 - p_min) ** n
+    assert p_fw >= alpha, f"largest |z| = {np.abs(z).max():.2f} over {n} entries (family-wise p = {p_fw:.2e})"
+    return z

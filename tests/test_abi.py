@@ -179,3 +179,21 @@ def test_plain_c_client_compiles_links_and_fails_cleanly_without_gpu(tmp_path):
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "run refused" in r.stdout
+
+
+def test_frozen_flags_are_validated_on_the_host(lib):
+    """DIES_FROZEN_FORM (the absorb-terminal pass in the handle's precision
+    form) needs DIES_FROZEN_ABSORB_TERMINAL and takes no per-package records;
+    unknown flags are refused.  Checked before any device work."""
+    m = W.external_cloud(4, 1.0)
+    h = D.dies_create_model(m.radii, m.rho, m.length_unit_cm)
+    try:
+        D.dies_set_dust(h, m.freq, m.kabs, m.ksca, m.g)
+        D.dies_set_sources(h, m.J_ext, 0.0, None)
+        T = np.full(4, 10.0)
+        for flags, rows in ((D.DIES_FROZEN_FORM, 0), (D.DIES_FROZEN_ABSORB_TERMINAL | D.DIES_FROZEN_FORM, 5), (8, 0)):
+            with pytest.raises(D.DiesError) as e:
+                D.dies_run_frozen(h, T, 5, 0, flags, rows, rows > 0)
+            assert e.value.code == D.DIES_EINVAL, flags
+    finally:
+        D.dies_destroy_model(h)

@@ -53,16 +53,16 @@ def test_c2_sweep_full_size(D, i):
     g = golden("c2_sweep")
     assert str(g["names"][i]) == cloud.name
     Tg = ensemble(D, cloud, 100_000_000)
-    r = assert_ensembles_agree(Tg, g["T"][i], 0.01, min_gated=cloud.n_cells // 2)
-    print(f"{cloud.name}: gated {r['gated'].sum()}/{cloud.n_cells}, max rel {r['max_rel_gated']:.4f}, "
-          f"max z {r['max_z']:.2f}")
+    r = assert_ensembles_agree(Tg, g["T"][i], 0.01, min_gated=cloud.n_cells // 2, min_acc=3 * cloud.n_cells // 4)
+    print(f"{cloud.name}: gated {r['n_gated']}/{cloud.n_cells}, accuracy gate {r['n_acc']}, max rel "
+          f"{r['max_rel_gated']:.4f}, beyond 3 sigma {r['k3']} (limit {r['k3_limit']}), max z {r['max_z']:.2f}")
 
 
 def test_c3_point_source_mixed_and_fp32(D):
     cloud = W.config3()
     g = golden("c3")
     Tm = ensemble(D, cloud, 100_000_000)
-    r = assert_ensembles_agree(Tm, g["T"][0], 0.01, min_gated=cloud.n_cells // 2)
+    r = assert_ensembles_agree(Tm, g["T"][0], 0.01, min_gated=cloud.n_cells // 2, min_acc=100)
     # The all-FP32 form keeps absorbed energies in FP32 counters (Sect. 2.3): equal
     # increments into a large FP32 counter round systematically, so its error
     # against the FP64 oracle is reported and held to the 1 % gate only; the
@@ -71,7 +71,7 @@ def test_c3_point_source_mixed_and_fp32(D):
     rf = compare_ensembles(Tf, g["T"][0])
     T1 = ensemble(D, cloud, 100_000_000, seeds=range(8), precision="fp32", n_batches=1)
     r1 = compare_ensembles(T1, g["T"][0])
-    assert rf["acc_gated"].sum() >= 20 and rf["max_rel_gated"] <= 0.01, rf
+    assert rf["n_acc"] >= 100 and rf["max_rel_gated"] <= 0.01, rf
     inner50 = float(np.abs(rf["d"][:8] / g["mean"][0][:8]).max())
     inner1 = float(np.abs(r1["d"][:8] / g["mean"][0][:8]).max())
     assert inner1 > inner50, (inner1, inner50)
@@ -84,19 +84,20 @@ def test_c5_external_thin_ffi(D):
     cloud = W.config5_external()
     g = golden("c5e")
     Tg = ensemble(D, cloud, 1_000_000_000)
-    r = assert_ensembles_agree(Tg, g["T"][0], 0.01, min_gated=100)
+    r = assert_ensembles_agree(Tg, g["T"][0], 0.01, min_gated=120, min_acc=80)
     T64 = ensemble(D, cloud, 200_000_000, fp64_radius=1e-3)
-    r64 = assert_ensembles_agree(T64, g["T"][0], 0.01, min_gated=100)
-    print(f"C5 external: gated {r['gated'].sum()}, max rel {r['max_rel_gated']:.4f}; "
-          f"FP64 inner crossings gated {r64['gated'].sum()}, max rel {r64['max_rel_gated']:.4f}")
+    r64 = assert_ensembles_agree(T64, g["T"][0], 0.01, min_gated=120, min_acc=80)
+    print(f"C5 external: gated {r['n_gated']}, accuracy gate {r['n_acc']}, max rel {r['max_rel_gated']:.4f}, "
+          f"max z {r['max_z']:.2f}; FP64 inner crossings gated {r64['n_gated']}, max rel {r64['max_rel_gated']:.4f}")
 
 
 def test_c5_internal_thick(D):
     cloud = W.config5_internal()
     g = golden("c5i")
-    Tg = ensemble(D, cloud, 100_000_000)
-    r = assert_ensembles_agree(Tg, g["T"][0], 0.01, min_gated=20)
-    print(f"C5 internal: gated {r['gated'].sum()}, max rel {r['max_rel_gated']:.4f}, max z {r['max_z']:.2f}")
+    Tg = ensemble(D, cloud, 1_000_000_000)
+    r = assert_ensembles_agree(Tg, g["T"][0], 0.01, min_gated=200, min_acc=150)
+    print(f"C5 internal (1e9 packages): gated {r['n_gated']}, accuracy gate {r['n_acc']}, max rel "
+          f"{r['max_rel_gated']:.4f}, beyond 3 sigma {r['k3']} (limit {r['k3_limit']}), max z {r['max_z']:.2f}")
 
 
 def test_c4_batch_4096_models(D):
@@ -126,7 +127,7 @@ def test_c4_batch_4096_models(D):
         rel.append(r["rel"][r["acc_gated"]])
     rel = np.concatenate(rel)
     pooled = pooled_sigma_check(rs)
-    assert pooled["n_gated"] >= 200 and len(rel) >= 100, (pooled["n_gated"], len(rel))
+    assert pooled["n_gated"] >= 1200 and len(rel) >= 500, (pooled["n_gated"], len(rel))
     assert rel.max() <= 0.01, rel.max()
     print(f"C4 batch: {pooled['n_gated']} gated shells in {len(sample)} sampled models, {len(rel)} in the "
           f"accuracy gate, max rel {rel.max():.4f}, beyond 3 sigma {pooled['k3']} (limit {pooled['k3_limit']}), "

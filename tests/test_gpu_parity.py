@@ -390,3 +390,79 @@ def test_table_temperature_inversion_matches_root_solve(D, oracle):
     print(f"table inversion: {inside.sum()} shells, max rel {rel.max():.2e}")
     assert rel.max() < 1e-4, rel.max()
     assert np.all(Tg[~inside] == pytest.approx(Tr[~inside], rel=1e-6))
+
+
+def test_luminous_source_beyond_the_float_range(D):
+    """A source of 1e40 erg/s (above the float range, 3.4e38): the mixed
+    form forms each package energy L / N in FP64 and stays finite and
+    conservative; the all-FP32 form's energy counters cannot hold such
+    energies, and its run reports DIES_ERANGE (flag 32) instead of returning
+    infinite temperatures."""
+    import ctypes
+    cloud = W.point_source_cloud(32, 1e-2, 10.0, L=1e40, length_unit_cm=100.0 * W.PC_CM)
+    m = D.Model(cloud, precision="mixed").run(1_000_000, seed=3)
+    st = m.stats()
+    T = m.temperatures()
+    assert st["status_word"] == 0 and np.all(np.isfinite(T)) and np.all(np.isfinite(m.absorbed()))
+    assert st["E_injected"] == pytest.approx(1e40, rel=1e-12)
+    assert st["E_escaped"] + st["E_lost"] == pytest.approx(st["E_injected"], rel=1e-9)
+    m.close()
+    f = D.Model(cloud, precision="fp32", n_batches=4)
+    with pytest.raises(D.DiesError) as ei:
+        f.run(1_000_000, seed=3)
+    assert ei.value.code == D.DIES_ERANGE
+    raw = D.dies_stats()
+    assert D.load().dies_get_stats(f.h, ctypes.byref(raw)) == D.DIES_ERANGE
+    assert raw.status_word & 32
+    f.close()
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp32"])
+@pytest.mark.parametrize("case", ["C1", "point", "kbg"])
+def test_two_packages_per_thread_match_the_oracle(D, oracle, prec, case):
+    """The pool variant of the FP32 forms (a second package per lane in a
+    per-warp shared-memory pool, events run in passes of one kind) against
+    the FP64 oracle over 16 seeds; every package of every run finishes and
+    energy is conserved."""
+    cloud = {"C1": W.config1, "point": lambda: W.point_source_cloud(48, 1e-2, 30.0),
+             "kbg": lambda: W.external_cloud(40, 20.0, k_bg=1.0 / 3.0)}[case]()
+    N = 1_000_000
+    m = D.Model(cloud, precision=prec, n_batches=50 if prec == "fp32" else 1, packages_per_thread=2)
+    Tg = []
+    for s in range(16):
+        st = m.run(N, seed=s).stats()
+        assert st["status_word"] == 0 and st["injected"] == N, st["status_word"]
+        assert st["escaped"] + st["killed_weight"] + st["killed_cap"] == N and st["killed_cap"] == 0
+        assert st["E_escaped"] + st["E_lost"] == pytest.approx(st["E_injected"], rel=1e-9)
+        Tg.append(m.temperatures())
+    m.close()
+    To = np.array([r["T"] for r in oracle.run_seeds(cloud, N, range(800, 816))])
+    r = assert_ensembles_agree(np.array(Tg), To, 0.01, min_gated=cloud.n_cells // 2)
+    print(f"pool {prec} {case}: gated {r['n_gated']}, max rel {r['max_rel_gated']:.4f}, max z {r['max_z']:.2f}")
+
+
+def test_two_packages_per_thread_in_a_batch_and_at_the_time_budget(D):
+    """The pool variant in a parameter-study batch (per-model tallies grouped
+    per warp) conserves energy and starts every package of every model; with
+    a 2 ms time budget it stops early (flag 1) and the handle stays usable."""
+    import ctypes
+    clouds = W.config4_models(32, seed=7)
+    b = D.Batch(clouds, packages_per_thread=2)
+    for s in range(3):
+        st = b.run(100_000, seed=s).stats()
+        assert st["status_word"] == 0 and st["injected"] == 100_000 * len(clouds)
+        assert st["escaped"] + st["killed_weight"] + st["killed_cap"] == st["injected"]
+        assert st["E_escaped"] + st["E_lost"] == pytest.approx(st["E_injected"], rel=1e-9)
+        assert np.all(np.isfinite(b.temperatures()))
+    b.close()
+    m = D.Model(W.config5_internal(), precision="mixed", packages_per_thread=2)
+    D.dies_set_time_budget(m.h, 2e-3)
+    with pytest.raises(D.DiesError) as ei:
+        m.run(200_000_000, seed=1)
+    assert ei.value.code == D.DIES_ETIMEOUT
+    raw = D.dies_stats()
+    assert D.load().dies_get_stats(m.h, ctypes.byref(raw)) == D.DIES_ETIMEOUT and raw.status_word & 1
+    D.dies_set_time_budget(m.h, 120.0)
+    st = m.run(200_000, seed=2).stats()
+    assert st["status_word"] == 0 and st["injected"] == 200_000
+    m.close()

@@ -81,3 +81,36 @@ def test_static_frozen_pass_rejects_what_it_cannot_hold(env):
         assert e.value.code == D.DIES_ESTATE
     finally:
         D.dies_destroy_model(h)
+
+
+def test_static_pass_reports_a_stop_at_the_time_budget(env):
+    """The static pass only enqueues; dies_get_stats afterwards waits for it
+    and reads its status and counters from the library's scratch array (no
+    allocation), so a pass stopped by the handle's time budget reports
+    DIES_ETIMEOUT with device flag 1 and partial counts, and the next pass
+    that completes reports DIES_OK with every package accounted for."""
+    import ctypes
+    torch, D = env
+    cloud = W.config5_internal()  # optically thick: thousands of events per package
+    n, F = cloud.n_cells, cloud.n_freq
+    m = D.Model(cloud, precision="fp64")
+    m.run(1000, seed=0)
+    dev = torch.device("cuda", 0)
+    Td = torch.full((n,), 40.0, dtype=torch.float64, device=dev)
+    E = torch.empty(n, dtype=torch.float64, device=dev)
+    sed = torch.empty(F, dtype=torch.float64, device=dev)
+    D.dies_set_time_budget(m.h, 2e-3)
+    N = 50_000_000
+    D.dies_run_frozen_static(m.h, Td.data_ptr(), N, 1, D.DIES_FROZEN_REEMIT, E.data_ptr(), sed.data_ptr())
+    raw = D.dies_stats()
+    assert D.load().dies_get_stats(m.h, ctypes.byref(raw)) == D.DIES_ETIMEOUT
+    st = raw.as_dict()
+    assert st["status_word"] & 1 and 0 < st["injected"] < N
+    D.dies_set_time_budget(m.h, 120.0)
+    D.dies_run_frozen_static(m.h, Td.data_ptr(), 2_000, 2, D.DIES_FROZEN_REEMIT, E.data_ptr(), sed.data_ptr())
+    st = m.stats()
+    assert st["status_word"] == 0 and st["injected"] == 2_000
+    assert st["escaped"] + st["killed_weight"] + st["killed_cap"] == 2_000
+    assert st["E_escaped"] + st["E_lost"] == pytest.approx(st["E_injected"], rel=1e-9)
+    assert st["E_escaped"] == pytest.approx(float(sed.sum().item()), rel=1e-12)
+    m.close()
