@@ -1,10 +1,17 @@
-"""Launch-shape autotuner for the IRE transport kernel.
+"""Launch autotuner for the IRE transport kernel.
 
-For a cloud model (or a batch of models) it times short runs over a small
-grid of (block size, CTAs per SM, rare_batch, inner moves, aggregated
-absorption atomics) and keeps the fastest.  Results
-are cached per "config class" (precision, weighting, source kind, shell-count
-and optical-depth buckets) in ``tune_cache.json`` next to this file; a class
+For a cloud model (or a batch of models) it times short runs and keeps the
+fastest configuration, in stages: a grid over (packages per thread: one in
+registers, or a second in the warp's shared-memory pool; block size, CTAs
+per SM, rare_batch, inner moves, aggregated absorption atomics), then the share of
+the launch a warp claims per trip to the device work counter (1/16 to 1/256),
+then the layout of the re-emission table (alias rows or FP32 CDF rows).
+Every candidate computes the same distributions; only the speed differs.
+The FP64-crossing threshold of the mixed form is an accuracy setting, not a
+speed one, so it is set by a rule on each model's shell geometry
+(``fp64_radius_for``) and recorded beside the tuned knobs.  Results are
+cached per "config class" (precision, weighting, source kind, shell-count and
+optical-depth buckets) in ``tune_cache.json`` next to this file; a class
 missing from the cache is tuned on the spot (on the GPU, through the same C
 ABI as the runs it tunes).
 """
@@ -24,8 +31,40 @@ GRID_RARE = (12, 16, 24)
 GRID_INNER = (32, 64)
 GRID_AGG = (0, 1)
 GRID_BPS = (0,)
-KEYS = ("block_size", "blocks_per_sm", "rare_batch", "inner_moves", "aggregate_atomics")
-DEFAULT = {"block_size": 256, "blocks_per_sm": 0, "rare_batch": 16, "inner_moves": 32, "aggregate_atomics": 0}
+GRID_REFILL = (16, 32, 64, 128, 256)   # refills per warp share of a launch (chunk = share / this)
+GRID_TABLE = (D.DIES_TABLE_ALIAS, D.DIES_TABLE_CDF)
+GRID_PPT = (1, 2)   # packages per thread: registers only, or a second one in the warp's shared-memory pool
+KEYS = ("block_size", "blocks_per_sm", "rare_batch", "inner_moves", "aggregate_atomics", "refill_divisor",
+        "reemit_table", "packages_per_thread")
+DEFAULT = {"block_size": 256, "blocks_per_sm": 0, "rare_batch": 16, "inner_moves": 32, "aggregate_atomics": 0,
+           "refill_divisor": 64, "reemit_table": D.DIES_TABLE_ALIAS, "packages_per_thread": 1}
+
+# FP64 crossing distances where FP32 would lose more than this relative
+# accuracy on a crossing (see fp64_radius_for): a path-length error of 1e-4
+# in a cell shifts its absorbed energy by ~1e-4 and its temperature by
+# ~2e-5, far inside the 1 % acceptance
+FP64_TOL = 1e-4
+
+
+def fp64_radius_for(cloud, tol: float = FP64_TOL) -> float:
+    """FP64-crossing threshold (a fraction of the outer radius) for the mixed
+    form: cells whose FP32 crossing distance may be off by more than ``tol``.
+
+    The FP32 geometry forms R_b^2 - p^2 from a float p^2 and a float-pair
+    R_b^2: the rounding of p^2, 2^-24 p^2, is relative to a crossing's
+    R_b^2 - p^2 ~ 2 r dr for a ray grazing a cell of thickness dr at radius
+    r, so the crossing distance sqrt(R_b^2 - p^2) is off by about
+    2^-25 r / dr (and a step, the difference of two path coordinates of size
+    ~r, likewise).  The threshold covers every cell, from the centre out, up
+    to the outermost one where that exceeds ``tol``; 0 when no cell does
+    (every benchmark geometry: at most r / dr = 256, an error of 8e-6)."""
+    import numpy as np
+    r = np.asarray(cloud.radii, dtype=np.float64)
+    dr = np.diff(r)
+    bad = np.nonzero(2.0 ** -25 * r[1:] / np.maximum(dr, 1e-300) > tol)[0]
+    if bad.size == 0:
+        return 0.0
+    return float(r[bad.max() + 1] / r[-1]) * (1.0 + 1e-12)
 
 _lock = threading.Lock()
 _cache: Optional[Dict[str, dict]] = None
@@ -65,8 +104,16 @@ def config_class(cloud, precision: str) -> str:
             + ("|w" if weighted else ""))
 
 
-def _time_model(cloud, precision: str, shape: dict, n: int, reps: int = 2) -> float:
-    m = D.Model(cloud, precision=precision, **shape)
+# Tuning sizes: the package counts the benchmark runs use (the best shape
+# depends on them: work refills, the launch's tail), three timed runs each.
+TUNE_N = {"mixed": 100_000_000, "fp32": 100_000_000, "fp64": 20_000_000}
+TUNE_N_BATCH = 200_000
+TUNE_REPS = 3
+
+
+def _time_model(cloud, precision: str, shape: dict, n: int, reps: int = TUNE_REPS) -> float:
+    m = D.Model(cloud, precision=precision, fp64_radius=fp64_radius_for(cloud) if precision == "mixed" else 0.0,
+                **shape)
     try:
         m.run(min(n, 200_000), seed=7)  # tables + warm-up
         best = float("inf")
@@ -84,27 +131,59 @@ def _cached(c: Dict[str, dict], key: str) -> Optional[dict]:
     return {k: int(e[k]) for k in KEYS} if e is not None and all(k in e for k in KEYS) else None
 
 
-def tune(cloud, precision: str = "mixed", n: int = 20_000_000, blocks: Iterable[int] = GRID_BLOCK,
-         rare: Iterable[int] = GRID_RARE, bps: Iterable[int] = GRID_BPS,
-         inner: Iterable[int] = GRID_INNER, agg: Iterable[int] = GRID_AGG) -> Tuple[dict, dict]:
-    """Time every shape of the grid on ``cloud``; return (best shape, timings)."""
+def _stages(timer, fp64: bool, blocks, rare, bps, inner, agg, refill, tables, ppt=GRID_PPT, pool_ok=True):
+    """Coordinate search: packages per thread (one, or two with the shared-
+    memory pool) crossed with the shape grid, then the refill divisor, then
+    the table layout; returns (best, timings).  ``pool_ok`` is False where
+    the pool variant does not exist (FP64 form, forced first interaction)."""
     times = {}
-    if precision == "fp64":
-        agg = (0,)  # the FP64 form has no aggregated path
-    for b in blocks:
-        for k in bps:
-            for r in rare:
-                for i in inner:
-                    for a in agg:
-                        shape = {"block_size": b, "blocks_per_sm": k, "rare_batch": r, "inner_moves": i,
-                                 "aggregate_atomics": a}
-                        times[f"{b}/{k}/{r}/{i}/{a}"] = _time_model(cloud, precision, shape, n)
-    key = min(times, key=times.get)
-    best = dict(zip(KEYS, (int(x) for x in key.split("/"))))
-    return dict(best, ms=times[key], n=n), times
+
+    def key(sh):
+        return "/".join(str(sh[k]) for k in KEYS)
+
+    def try_shape(sh):
+        k = key(sh)
+        if k not in times:
+            times[k] = timer(sh)
+        return times[k]
+
+    if fp64:
+        agg, tables = (0,), (D.DIES_TABLE_ALIAS,)  # no aggregated path, FP64 CDF rows only
+    if fp64 or not pool_ok:
+        ppt = (1,)
+    base = dict(DEFAULT)
+    for q in ppt:
+        for b in blocks:
+            for k in bps:
+                for r in rare:
+                    for i in inner:
+                        for a in agg:
+                            try_shape(dict(base, block_size=b, blocks_per_sm=k, rare_batch=r, inner_moves=i,
+                                           aggregate_atomics=a, packages_per_thread=q))
+    best = dict(zip(KEYS, (int(x) for x in min(times, key=times.get).split("/"))))
+    for p in refill:
+        try_shape(dict(best, refill_divisor=p))
+    best = dict(zip(KEYS, (int(x) for x in min(times, key=times.get).split("/"))))
+    for t in tables:
+        try_shape(dict(best, reemit_table=t))
+    k = min(times, key=times.get)
+    return dict(zip(KEYS, (int(x) for x in k.split("/")))), times
 
 
-def best_launch(cloud, precision: str = "mixed", allow_tuning: bool = True, n: int = 20_000_000) -> dict:
+def tune(cloud, precision: str = "mixed", n: Optional[int] = None, blocks: Iterable[int] = GRID_BLOCK,
+         rare: Iterable[int] = GRID_RARE, bps: Iterable[int] = GRID_BPS,
+         inner: Iterable[int] = GRID_INNER, agg: Iterable[int] = GRID_AGG, ppt: Iterable[int] = GRID_REFILL,
+         tables: Iterable[int] = GRID_TABLE) -> Tuple[dict, dict]:
+    """Tune every knob on ``cloud``; return (best configuration, timings)."""
+    n = n or TUNE_N[precision]
+    best, times = _stages(lambda sh: _time_model(cloud, precision, sh, n), precision == "fp64", blocks, rare, bps,
+                          inner, agg, ppt, tables, pool_ok=not cloud.ffi)
+    return dict(best, ms=times["/".join(str(best[k]) for k in KEYS)], n=n,
+                fp64_radius=fp64_radius_for(cloud) if precision == "mixed" else 0.0,
+                candidates=len(times)), times
+
+
+def best_launch(cloud, precision: str = "mixed", allow_tuning: bool = True, n: Optional[int] = None) -> dict:
     """Cached best launch shape for the config class of ``cloud``; tuned and
     cached on first use when ``allow_tuning`` (needs a GPU)."""
     key = config_class(cloud, precision)
@@ -121,7 +200,7 @@ def best_launch(cloud, precision: str = "mixed", allow_tuning: bool = True, n: i
     return {k: best[k] for k in KEYS}
 
 
-def best_batch_launch(clouds, allow_tuning: bool = True, n_per_model: int = 20_000) -> dict:
+def best_batch_launch(clouds, allow_tuning: bool = True, n_per_model: int = TUNE_N_BATCH) -> dict:
     """Best launch shape for a parameter-study batch (timed on the batch itself)."""
     key = f"batch|{len(clouds)}|n_avg{int(sum(c.n_cells for c in clouds) / len(clouds))}"
     with _lock:
@@ -130,25 +209,60 @@ def best_batch_launch(clouds, allow_tuning: bool = True, n_per_model: int = 20_0
         return hit
     if not allow_tuning:
         return dict(DEFAULT)
-    times = {}
-    for b in GRID_BLOCK:
-        for r in GRID_RARE:
-            for i in GRID_INNER:
-                for a in GRID_AGG:
-                    bt = D.Batch(clouds, block_size=b, rare_batch=r, inner_moves=i, aggregate_atomics=a)
-                    try:
-                        bt.run(2_000, seed=3)
-                        best = float("inf")
-                        for rep in range(2):
-                            bt.run(n_per_model, seed=5 + rep)
-                            best = min(best, bt.stats()["transport_ms"])
-                        times[(b, r, i, a)] = best
-                    finally:
-                        bt.close()
-    (b, r, i, a) = min(times, key=times.get)
-    rec = {"block_size": b, "blocks_per_sm": 0, "rare_batch": r, "inner_moves": i, "aggregate_atomics": a,
-           "ms": times[(b, r, i, a)], "n": n_per_model}
+
+    def timer(sh):
+        bt = D.Batch(clouds, **sh)
+        try:
+            bt.run(2_000, seed=3)
+            best = float("inf")
+            for rep in range(TUNE_REPS):
+                bt.run(n_per_model, seed=5 + rep)
+                best = min(best, bt.stats()["transport_ms"])
+            return best
+        finally:
+            bt.close()
+
+    best, times = _stages(timer, False, GRID_BLOCK, GRID_RARE, GRID_BPS, GRID_INNER, GRID_AGG, GRID_REFILL, GRID_TABLE,
+                          pool_ok=not clouds[0].ffi)
+    rec = dict(best, ms=times["/".join(str(best[k]) for k in KEYS)], n=n_per_model, candidates=len(times),
+               fp64_radius=0.0)
     with _lock:
         _load()[key] = rec
         _save()
     return {k: rec[k] for k in KEYS}
+
+
+def benchmark_classes():
+    """(cloud or batch, precision) of every configuration the benchmark and
+    the full-size tests run, for retuning the cache in one go."""
+    from . import workloads as W
+    singles = [(c, "mixed") for c in W.config2_sweep()]
+    singles += [(W.config1(), "mixed"), (W.config1(), "fp64"), (W.config2(10.0), "fp64"), (W.config3(), "mixed"),
+                (W.config3(), "fp32"), (W.config5_external(), "mixed"), (W.config5_internal(), "mixed")]
+    return singles, W.config4_models()
+
+
+def main(argv=None) -> int:
+    """Retune the cache entries of the benchmark configurations (on the GPU)."""
+    import argparse
+    ap = argparse.ArgumentParser(description=main.__doc__)
+    ap.add_argument("--force", action="store_true", help="retune classes that are already cached")
+    args = ap.parse_args(argv)
+    singles, batch = benchmark_classes()
+    for cloud, prec in singles:
+        key = config_class(cloud, prec)
+        if args.force:
+            with _lock:
+                _load().pop(key, None)
+        shape = best_launch(cloud, prec)
+        print(json.dumps({"class": key, **shape, "fp64_radius": fp64_radius_for(cloud) if prec == "mixed" else 0.0}),
+              flush=True)
+    if args.force:
+        with _lock:
+            _load().pop(f"batch|{len(batch)}|n_avg{int(sum(c.n_cells for c in batch) / len(batch))}", None)
+    print(json.dumps({"class": "batch", **best_batch_launch(batch)}), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

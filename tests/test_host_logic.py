@@ -69,14 +69,14 @@ def test_autotune_uses_cache_without_gpu(tmp_path, monkeypatch):
     m = W.config1()
     key = autotune.config_class(m, "mixed")
     old = autotune.config_class(W.config3(), "mixed")
-    cache.write_text(json.dumps({key: {"block_size": 128, "blocks_per_sm": 0, "rare_batch": 12, "inner_moves": 16,
-                                       "aggregate_atomics": 1, "ms": 1.0},
-                                 old: {"block_size": 128, "blocks_per_sm": 0, "rare_batch": 12, "ms": 1.0}}))
+    full = {"block_size": 128, "blocks_per_sm": 0, "rare_batch": 12, "inner_moves": 16, "aggregate_atomics": 1,
+            "refill_divisor": 128, "reemit_table": 1, "packages_per_thread": 2}
+    cache.write_text(json.dumps({key: dict(full, ms=1.0),
+                                 old: {"block_size": 128, "blocks_per_sm": 0, "rare_batch": 12, "inner_moves": 16,
+                                       "aggregate_atomics": 1, "ms": 1.0}}))
     monkeypatch.setattr(autotune, "CACHE_PATH", str(cache))
     monkeypatch.setattr(autotune, "_cache", None)
-    assert autotune.best_launch(m, "mixed", allow_tuning=False) == {"block_size": 128, "blocks_per_sm": 0,
-                                                                    "rare_batch": 12, "inner_moves": 16,
-                                                                    "aggregate_atomics": 1}
+    assert autotune.best_launch(m, "mixed", allow_tuning=False) == full
     # an entry without every knob counts as missing
     assert autotune.best_launch(W.config3(), "mixed", allow_tuning=False) == autotune.DEFAULT
     assert autotune.best_launch(W.config5_internal(), "mixed", allow_tuning=False) == autotune.DEFAULT
@@ -99,3 +99,38 @@ def test_noise_profile_statistics():
     assert p["mean_T"] == [12.0, 20.0]
     assert p["rel_noise"][0] == pytest.approx(2.0 / 12.0) and p["rel_noise"][1] == 0.0
     assert p["rel_error_of_mean"] == pytest.approx([1.0 / 11.0, 0.2])
+
+
+def test_autotune_search_stages_cover_every_knob():
+    """The tuner's coordinate search (with a synthetic timer: fastest at
+    block 128, rare 24, inner 64, aggregation on, refill divisor 32, CDF
+    rows) visits the shape grid, then packages per thread, then the table
+    layout, and returns the optimum of each stage."""
+    def timer(sh):
+        return (abs(sh["block_size"] - 128) + abs(sh["rare_batch"] - 24) + abs(sh["inner_moves"] - 64) +
+                (1 - sh["aggregate_atomics"]) + abs(sh["refill_divisor"] - 32) + (1 - sh["reemit_table"]))
+    def timer2(sh):  # the pool variant wins by a margin
+        return timer(sh) - (0.5 if sh["packages_per_thread"] == 2 else 0.0)
+    best, times = autotune._stages(timer2, False, autotune.GRID_BLOCK, autotune.GRID_RARE, autotune.GRID_BPS,
+                                   autotune.GRID_INNER, autotune.GRID_AGG, autotune.GRID_REFILL, autotune.GRID_TABLE)
+    assert best == {"block_size": 128, "blocks_per_sm": 0, "rare_batch": 24, "inner_moves": 64,
+                    "aggregate_atomics": 1, "refill_divisor": 32, "reemit_table": 1, "packages_per_thread": 2}
+    n_grid = len(autotune.GRID_BLOCK) * len(autotune.GRID_RARE) * len(autotune.GRID_INNER) * len(autotune.GRID_AGG)
+    assert len(times) == 2 * n_grid + len(autotune.GRID_REFILL) - 1 + len(autotune.GRID_TABLE) - 1
+    best1, _ = autotune._stages(timer2, False, (128,), (24,), (0,), (64,), (0, 1), (32,), (0, 1), pool_ok=False)
+    assert best1["packages_per_thread"] == 1  # forced first interaction: no pool variant
+    best64, _ = autotune._stages(timer2, True, (128,), (24,), (0,), (64,), (0, 1), (32,), (0, 1))
+    assert best64["aggregate_atomics"] == 0 and best64["reemit_table"] == 0  # no such paths in the FP64 form
+    assert best64["packages_per_thread"] == 1
+
+
+def test_fp64_threshold_rule_covers_thin_cells_only():
+    """The mixed form's FP64-crossing threshold: 0 for every benchmark
+    geometry (FP32 crossings accurate to < 1e-5 there), and for a model with
+    cells 1e-8 thick at r = 1e-3 it reaches out to cover them."""
+    for c in (W.config1(), W.config3(), W.config5_external(), W.config5_internal(), *W.config4_models(8)):
+        assert autotune.fp64_radius_for(c) == 0.0, c.name
+    r = np.concatenate([[0.0], 1e-3 * (1.0 + 1e-8 * np.arange(1, 4)), np.linspace(0.1, 1.0, 28)])
+    m = W.config1().replace(radii=r, rho=np.ones(len(r) - 1))
+    thr = autotune.fp64_radius_for(m)
+    assert r[3] < thr * r[-1] < r[4]
