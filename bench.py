@@ -35,14 +35,18 @@ UNIT = "packages/s"
 N_PER_RUN = 100_000_000
 L2_FLUSH_BYTES = 256 << 20
 
-# Algorithmic thread-level operations per event (minimum instruction counts of
-# the method's arithmetic): boundary crossing 20 (record load, compensated
-# R^2 - p^2, square root, step, column product and compare, cell update),
-# scattering 120 (one Philox4x32-10 block of ~80 integer operations, HG
-# inversion, azimuth, rotation), absorption 150 (one Philox block, FP64
-# atomic, table searches, isotropic re-emission, two logarithms) and
-# injection + exit 120 per package.
-OPS = {"crossed": 20, "scattered": 120, "absorbed": 150, "injected": 120}
+# Algorithmic thread-level operations per event, the roofline numerator.
+# OPS: the method's own arithmetic without the random-number generator:
+# boundary crossing 15 (one square root, ~12 FP32 operations, two table
+# loads), scattering 25 (two logarithms for the free paths, HG inversion with
+# one division and one square root, one sine/cosine, ~20 operations of the
+# rotation), absorption 25 (one FP64 atomic read-modify-write, a table search
+# of up to 16 probes, two logarithms, one sine/cosine) and injection + exit
+# 20 per package (source sampling, direction, two logarithms, the SED add).
+# OPS_RNG adds one Philox4x32-10 block (~80 integer operations) per event and
+# two per injection, and counts the crossing at 20 with its cell update.
+OPS = {"crossed": 15, "scattered": 25, "absorbed": 25, "injected": 20}
+OPS_RNG = {"crossed": 20, "scattered": 120, "absorbed": 150, "injected": 120}
 SM_COUNT = 152
 LANES_PER_SM = 128  # 4 schedulers x 32 lanes issue per cycle
 
@@ -228,7 +232,8 @@ def traffic_from_profile():
 
 def accuracy_vs_oracle(T_runs):
     """Largest relative deviation of the step-averaged GPU temperatures from
-    the stored oracle means, on shells where the oracle's 3-sigma is < 1 %."""
+    the stored oracle means, on shells where the oracle's 6 sigma is < 1 %
+    (the accuracy gate of the parity tests)."""
     p = os.path.join(ROOT, "tests", "golden", "c2_sweep_oracle.npz")
     if not os.path.exists(p) or not T_runs:
         return None
@@ -236,7 +241,7 @@ def accuracy_vs_oracle(T_runs):
     worst = 0.0
     for i, T in enumerate(T_runs):
         mo, so = g["mean"][i], g["se"][i]
-        gate = 3.0 * so <= 0.01 * mo
+        gate = 6.0 * so <= 0.01 * mo  # the accuracy gate of the tests (noise cannot reach 1 %)
         if gate.any():
             worst = max(worst, float(np.max(np.abs(np.mean(T, axis=0)[gate] / mo[gate] - 1.0))))
     return worst
@@ -292,7 +297,7 @@ def measure_batch(D, autotune, n_per_model: int, reps: int = 2):
 def measure_precision_forms(D, autotune):
     """The all-FP32 form (with and without the batches of Sect. 2.3) and the
     FP64 form, each with its largest temperature error against the stored
-    FP64-oracle means (shells where the oracle's 3-sigma is below 1 %)."""
+    FP64-oracle means (shells where the oracle's 6 sigma is below 1 %)."""
     from paper_2408_13807_gb300 import workloads as W
     out = {}
     mean, se = golden_mean("c3")
@@ -306,24 +311,59 @@ def measure_precision_forms(D, autotune):
         m.close()
         rec = {"packages_per_s": 1e8 / (st["transport_ms"] * 1e-3)}
         if mean is not None:
-            gate = 3 * se[0] <= 0.01 * mean[0]
+            gate = 6 * se[0] <= 0.01 * mean[0]
             d = T / mean[0] - 1.0
             rec["max_rel_T_error"] = float(np.max(np.abs(d[gate])))
             rec["mean_rel_T_error_inner8"] = float(np.mean(d[:8]))
         out[label] = rec
-    c1 = W.config1()
-    m = D.Model(c1, precision="fp64", **autotune.best_launch(c1, "fp64"))
-    m.run(100_000, seed=1)
-    m.run(10_000_000, seed=2)
-    out["fp64_form_C1"] = {"packages_per_s": 1e7 / (m.stats()["transport_ms"] * 1e-3)}
-    m.close()
-    m = D.Model(c1, precision="mixed", **autotune.best_launch(c1, "mixed"))
-    m.run(100_000, seed=1)
-    m.run(10_000_000, seed=2)
-    out["mixed_form_C1"] = {"packages_per_s": 1e7 / (m.stats()["transport_ms"] * 1e-3)}
-    m.close()
+    # the plain single-model FP64-geometry form against the mixed form, on one
+    # run of the headline sweep (C2, A_V = 10, plain) and on C1
+    for label, cloud, n_f64, n_mix in (("C2_AV10_plain", W.config2(10.0), 20_000_000, 100_000_000),
+                                       ("C1", W.config1(), 10_000_000, 10_000_000)):
+        rec = {}
+        for prec, nn in (("fp64", n_f64), ("mixed", n_mix)):
+            m = D.Model(cloud, precision=prec, **autotune.best_launch(cloud, prec))
+            m.run(100_000, seed=1)
+            m.run(nn, seed=2)
+            rec[f"{prec}_packages_per_s"] = nn / (m.stats()["transport_ms"] * 1e-3)
+            m.close()
+        rec["mixed_over_fp64"] = rec["mixed_packages_per_s"] / rec["fp64_packages_per_s"]
+        rec["packages"] = {"fp64": n_f64, "mixed": n_mix}
+        out[f"fp64_vs_mixed_{label}"] = rec
     out["workload"] = ("C3 point source, 256 log shells, tau_V = 100, 1e8 packages, one seed, error vs the "
-                       "oracle's 16-seed mean; C1 32 shells A_V = 10, 1e7 packages")
+                       "oracle's 16-seed mean; the plain FP64-geometry form against the mixed form on C2 "
+                       "(A_V = 10 plain, 2e7 / 1e8 packages) and C1 (1e7 packages)")
+    return out
+
+
+def measure_c5(D, autotune, n: int = 1_000_000_000):
+    """The extreme-dynamic-range configurations at their full size: 1024 log
+    shells 1e-6..1, the thin external cloud with forced first interaction and
+    the thick internally heated envelope, each 1e9 packages, one seed, with
+    the largest temperature error against the stored oracle means (shells
+    where the oracle's 6 sigma is below 1 %, the tests' accuracy gate)."""
+    from paper_2408_13807_gb300 import workloads as W
+    out = {}
+    for label, cloud, gold in (("C5_external_AV0.1_ffi", W.config5_external(), "c5e"),
+                               ("C5_internal_tau1000", W.config5_internal(), "c5i")):
+        m = D.Model(cloud, precision="mixed", **autotune.best_launch(cloud, "mixed"))
+        m.run(1_000_000, seed=1)
+        m.run(n, seed=2)
+        st = m.stats()
+        T = m.temperatures()
+        m.close()
+        if st["status_word"] != 0:
+            raise RuntimeError(f"device status {st['status_word']} in {label}")
+        sec = st["transport_ms"] * 1e-3
+        rec = {"packages": n, "packages_per_s": n / sec, "transport_ms": st["transport_ms"],
+               "events_per_package": {k: st[k] / n for k in ("crossed", "scattered", "absorbed")},
+               "absorptions_per_s": st["absorbed"] / sec}
+        mean, se = golden_mean(gold)
+        if mean is not None:
+            gate = (6 * se[0] <= 0.01 * mean[0]) & (mean[0] > 2.7 * (1 + 1e-6))
+            rec["max_rel_T_error"] = float(np.max(np.abs(T[gate] / mean[0][gate] - 1.0)))
+            rec["shells_compared"] = int(gate.sum())
+        out[label] = rec
     return out
 
 
@@ -352,7 +392,9 @@ def run_ours(args):
                    "inner_moves": args.inner_moves, "aggregate_atomics": args.aggregate_atomics} for _ in clouds]
     else:
         shapes = [autotune.best_launch(c, "mixed") for c in clouds]  # tuned here if not cached (untimed)
-    models = [D.Model(c, precision="mixed", fp64_radius=args.fp64_radius, **sh) for c, sh in zip(clouds, shapes)]
+    # FP64 crossings where the shell geometry needs them (the autotuner's rule; none on this workload)
+    r64 = [autotune.fp64_radius_for(c) if args.fp64_radius < 0 else args.fp64_radius for c in clouds]
+    models = [D.Model(c, precision="mixed", fp64_radius=r, **sh) for c, r, sh in zip(clouds, r64, shapes)]
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     seed_base = replica_seed_base(rank)
 
@@ -395,17 +437,26 @@ def run_ours(args):
     pk_step = len(models) * n
     value = job_value(world, pk_step, args.steps, total_ms)
 
-    # ---- end-to-end through the public API, host arrays in and out
+    # ---- end-to-end through the public API, host arrays in and out; the
+    # per-run split of Sect. 3.1 (total vs kernel time): input upload, table
+    # build, transport + temperatures (device events), host remainder
     e2e_dts, h2d, d2h = [], 0, 0
+    split = {"upload_ms": 0.0, "table_build_ms": 0.0, "kernel_and_finalize_ms": 0.0, "transport_ms": 0.0}
     barrier(dist)
-    for k in range(0 if args.no_e2e else max(1, min(args.steps, 3))):
+    n_e2e = 0 if args.no_e2e else max(1, min(args.steps, 3))
+    for k in range(n_e2e):
         torch.cuda.synchronize()
         t = time.perf_counter()
         h2d = d2h = 0
         for i, c in enumerate(clouds):
-            m = D.Model(c, precision="mixed", fp64_radius=args.fp64_radius, **shapes[i])
+            m = D.Model(c, precision="mixed", fp64_radius=r64[i], **shapes[i])
             m.run(n, seed=seed_base + 500 + 16 * k + i)
             T, sed = m.temperatures(), m.sed()
+            st = m.stats()
+            split["upload_ms"] += st["upload_ms"] / n_e2e
+            split["table_build_ms"] += (st["table_ms"] - st["upload_ms"]) / n_e2e
+            split["kernel_and_finalize_ms"] += st["kernel_ms"] / n_e2e
+            split["transport_ms"] += st["transport_ms"] / n_e2e
             h2d += (c.radii.nbytes + c.rho.nbytes + 6 * 64 * 8 + 64)
             d2h += T.nbytes + 2 * sed.nbytes + 16 * 8 + 8 * 8 + 4
             m.close()
@@ -415,6 +466,12 @@ def run_ours(args):
     if e2e_dts:
         e2e_dt = max_over_ranks(dist, statistics.median(e2e_dts), dev)
         e2e_value = world * pk_step / e2e_dt
+        split["total_ms"] = 1e3 * statistics.median(e2e_dts)
+        split["host_rest_ms"] = split["total_ms"] - split["upload_ms"] - split["table_build_ms"] - \
+            split["kernel_and_finalize_ms"]
+        split["note"] = ("per step of 9 runs through the public API from host arrays: upload, table build and "
+                         "transport + temperatures are device times (CUDA events); host_rest_ms is handle "
+                         "creation, workspace allocation, read-back and teardown")
 
     if rank != 0:
         if dist is not None:
@@ -423,8 +480,10 @@ def run_ours(args):
 
     # ---- roofline of the dominant kernel (transport): algorithmic ops / launch time
     ops = sum(OPS[k] * stats_acc[k] for k in OPS)
+    ops_rng = sum(OPS_RNG[k] * stats_acc[k] for k in OPS_RNG)
     t_transport = sum(transport_ms) * 1e-3
     achieved = ops / t_transport / 1e9
+    achieved_rng = ops_rng / t_transport / 1e9
     peaks = {}
     pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pp):
@@ -438,6 +497,7 @@ def run_ours(args):
     if not args.no_extras:
         extra["batched"] = measure_batch(D, autotune, args.batch_n)
         extra["precision_forms"] = measure_precision_forms(D, autotune)
+        extra["c5_full_size"] = measure_c5(D, autotune)
     # measured rates of the bounding units (after the timed region)
     unit_peaks = D.dies_measure_peaks() if not args.no_extras else None
     atomics_per_s = stats_acc["absorbed"] / t_transport
@@ -465,8 +525,12 @@ def run_ours(args):
             "kernel": "k_transport<MIXED,IRE> (persistent IRE transport)",
             "peak_source": f"derived issue peak: {SM_COUNT} SMs x {LANES_PER_SM} lanes x {sm_max:.0f} MHz",
             "ops_per_event": OPS,
+            "ops_note": "per-event operation counts of the method's arithmetic without the random-number "
+                        "generator; frac_incl_rng counts one Philox4x32-10 block per event as well",
+            "achieved_incl_rng": achieved_rng, "frac_incl_rng": achieved_rng / peak, "ops_per_event_incl_rng": OPS_RNG,
             "transport_share_of_step": t_transport / (sum(step_ms) * 1e-3),
         },
+        "time_split": split if e2e_dts else None,
         "cpu_baseline": None if cpu_rate is None else {
             "value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{cpu_n} packages of each of the 9 runs (serial FP64 oracle, one thread, {cpu_dt:.1f} s)"},
@@ -480,6 +544,7 @@ def run_ours(args):
         "events_per_package": {k: stats_acc[k] / max(1, stats_acc["injected"]) for k in ("crossed", "scattered", "absorbed")},
         "max_rel_T_error_vs_oracle": accuracy_vs_oracle(T_runs),
         "launch_shapes": shapes,
+        "fp64_radius": r64,
         **extra,
     }
     print(json.dumps(line))
@@ -501,7 +566,8 @@ def main():
     ap.add_argument("--rare-batch", type=int, default=16)
     ap.add_argument("--inner-moves", type=int, default=32)
     ap.add_argument("--aggregate-atomics", type=int, default=0)
-    ap.add_argument("--fp64-radius", type=float, default=0.0)
+    ap.add_argument("--fp64-radius", type=float, default=-1.0,
+                    help="FP64-crossing threshold (fraction of R); < 0: the autotuner's geometric rule")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batch and precision-form measurements")
