@@ -258,6 +258,24 @@ typedef struct dies_launch {
 } dies_launch;
 int dies_set_launch_ex(dies_model *m, const dies_launch *launch);
 
+/* Package range of the next run on this handle: checkpoint and resume at a
+ * package index (no counterpart in the paper; its N_B batches of Sect. 2.3
+ * split a run the same way).  The next dies_run, dies_run_async or
+ * dies_run_frozen call with n_packages = N runs only packages
+ * [first, first + count) of each active source of that N-package run: the
+ * same Philox streams and package energies L / N as the whole run.  With
+ * resume = 1 it adds to the absorbed energies, escaping SED, counters and
+ * energy sums the handle holds from its previous run instead of starting
+ * from zero (DIES_ESTATE if there was none); temperatures are those of all
+ * the packages so far.  Consecutive ranges covering [0, N) therefore compute
+ * the whole run: in the frozen pass the same per-package event counts and
+ * path hashes bit for bit (rows outside the range are left untouched); in IRE
+ * runs the same estimator, with the deposits of a later range ordered after
+ * those of earlier ones.  The setting applies to the next run only; a range
+ * outside [0, N) fails that run with DIES_EINVAL.  Graph mode is bypassed for
+ * a ranged run. */
+int dies_set_package_range(dies_model *m, uint64_t first, uint64_t count, int resume);
+
 /* Wall-clock budget of one transport launch in seconds (default 120).  A
  * launch that reaches it stops early and the run returns DIES_ETIMEOUT. */
 int dies_set_time_budget(dies_model *m, double seconds);

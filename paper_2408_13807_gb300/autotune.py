@@ -1,9 +1,9 @@
 """Launch autotuner for the IRE transport kernel.
 
 For a cloud model (or a batch of models) it times short runs and keeps the
-fastest configuration, in stages: a grid over (packages per thread: one in
-registers, or a second in the warp's shared-memory pool; block size, CTAs
-per SM, rare_batch, inner moves, aggregated absorption atomics), then the share of
+fastest configuration, in stages: a grid over (block size, CTAs per SM,
+rare_batch, inner moves, aggregated absorption atomics), then a second
+package per thread in the warp's shared-memory pool, then the share of
 the launch a warp claims per trip to the device work counter (1/16 to 1/256),
 then the layout of the re-emission table (alias rows or FP32 CDF rows).
 Every candidate computes the same distributions; only the speed differs.
@@ -132,10 +132,11 @@ def _cached(c: Dict[str, dict], key: str) -> Optional[dict]:
 
 
 def _stages(timer, fp64: bool, blocks, rare, bps, inner, agg, refill, tables, ppt=GRID_PPT, pool_ok=True):
-    """Coordinate search: packages per thread (one, or two with the shared-
-    memory pool) crossed with the shape grid, then the refill divisor, then
-    the table layout; returns (best, timings).  ``pool_ok`` is False where
-    the pool variant does not exist (FP64 form, forced first interaction)."""
+    """Coordinate search: the shape grid, then two packages per thread (the
+    shared-memory pool) with the best shape over block size and rare batch,
+    then the refill divisor, then the table layout; returns (best, timings).
+    ``pool_ok`` is False where the pool variant does not exist (FP64 form,
+    forced first interaction)."""
     times = {}
 
     def key(sh):
@@ -152,14 +153,21 @@ def _stages(timer, fp64: bool, blocks, rare, bps, inner, agg, refill, tables, pp
     if fp64 or not pool_ok:
         ppt = (1,)
     base = dict(DEFAULT)
+    for b in blocks:
+        for k in bps:
+            for r in rare:
+                for i in inner:
+                    for a in agg:
+                        try_shape(dict(base, block_size=b, blocks_per_sm=k, rare_batch=r, inner_moves=i,
+                                       aggregate_atomics=a))
+    best = dict(zip(KEYS, (int(x) for x in min(times, key=times.get).split("/"))))
+    # more packages per thread, with the best shape's inner moves and atomics, over block size and rare batch
     for q in ppt:
+        if q == 1:
+            continue
         for b in blocks:
-            for k in bps:
-                for r in rare:
-                    for i in inner:
-                        for a in agg:
-                            try_shape(dict(base, block_size=b, blocks_per_sm=k, rare_batch=r, inner_moves=i,
-                                           aggregate_atomics=a, packages_per_thread=q))
+            for r in rare:
+                try_shape(dict(best, block_size=b, rare_batch=r, packages_per_thread=q))
     best = dict(zip(KEYS, (int(x) for x in min(times, key=times.get).split("/"))))
     for p in refill:
         try_shape(dict(best, refill_divisor=p))

@@ -128,6 +128,11 @@ struct Problem {
   int n_tnodes = 1024;
   cudaStream_t stream = nullptr;
   int block = 256, blocks_per_sm = 0, rare_batch = 16, inner = 32, agg = 0;
+  // package range of the next run (dies_set_package_range): packages
+  // [range_first, range_first + range_count) of each source; resume keeps
+  // the accumulators of the previous run
+  bool range_set = false, range_resume = false;
+  uint64_t range_first = 0, range_count = 0;
   int pkgs_per_thread = 1;  // 2: a second package per lane in per-warp shared-memory pools (FP32 forms, no FFI)
   int refill_div = 0;  // a warp takes ~1/refill_div of its share of the launch per trip to the work counter (0 = 64)
   int remit_table = DIES_TABLE_ALIAS;
@@ -489,8 +494,34 @@ struct Problem {
     return DIES_OK;
   }
 
-  int reset_accumulators() { return reset_accumulators_on(stream); }
-  int reset_accumulators_on(cudaStream_t st) {
+  int reset_accumulators(bool resume = false) { return reset_accumulators_on(stream, resume); }
+
+  // the package range of this run ([first, first + count) of n), checked
+  int take_range(uint64_t n, uint64_t *first, uint64_t *count, bool *resume) {
+    *first = 0;
+    *count = n;
+    *resume = false;
+    if (!range_set) return DIES_OK;
+    range_set = false;  // applies to one run
+    if (range_count == 0 || range_first > n || range_count > n - range_first)
+      return fail(DIES_EINVAL, "package range [%llu, %llu) does not lie in [0, %llu)",
+                  (unsigned long long)range_first, (unsigned long long)(range_first + range_count),
+                  (unsigned long long)n);
+    if (range_resume && !has_result) return fail(DIES_ESTATE, "resume needs a previous run on this handle");
+    *first = range_first;
+    *count = range_count;
+    *resume = range_resume;
+    return DIES_OK;
+  }
+  // resume: keep absorbed energies, tallies, counters and energy sums of the
+  // previous run; only the work counter, status and diagnostics restart
+  int reset_accumulators_on(cudaStream_t st, bool resume = false) {
+    if (resume) {
+      DIES_CUDA(cudaMemsetAsync(ws + lay.queue, 0, 2 * 8, st));
+      DIES_CUDA(cudaMemsetAsync(ws + lay.status, 0, 4, st));
+      DIES_CUDA(cudaMemsetAsync(ws + lay.diag, 0, 16 * 4, st));
+      return DIES_OK;
+    }
     DIES_CUDA(cudaMemsetAsync(ws + lay.E, 0, (size_t)n_cells * 8, st));
     DIES_CUDA(cudaMemsetAsync(ws + lay.Eprev, 0, (size_t)n_cells * 4, st));
     DIES_CUDA(cudaMemsetAsync(ws + lay.Ecur, 0, (size_t)n_cells * 4, st));
@@ -518,6 +549,10 @@ struct Problem {
     int rc;
     if ((rc = check_ready())) return rc;
     if (n == 0) return fail(DIES_EINVAL, "n_packages must be >= 1");
+    const bool ranged = range_set;
+    uint64_t first, count;
+    bool resume;
+    if ((rc = take_range(n, &first, &count, &resume))) return rc;
     if ((rc = ensure_device())) return rc;
     launches_at_start = g_launches.load();
     DIES_CUDA(cudaEventRecord(ev[0], stream));
@@ -529,10 +564,10 @@ struct Problem {
     DIES_CUDA(cudaEventRecord(ev[1], stream));
     int grid;
     if ((rc = grid_for(prec, MODE_IRE, &grid))) return rc;
-    if (use_graph) {
+    if (use_graph && !ranged) {
       if ((rc = replay_graph(n, seed, grid))) return rc;
     } else {
-      if ((rc = enqueue_body(stream, n, seed, grid, nullptr))) return rc;
+      if ((rc = enqueue_body(stream, n, seed, grid, nullptr, first, count, resume))) return rc;
     }
     DIES_CUDA(cudaEventRecord(ev[4], stream));
     has_result = true;
@@ -546,20 +581,23 @@ struct Problem {
   // transport launch(es), tallies and temperatures, on stream st.  With
   // seed_dev set (graph capture) the kernels read the seed from there and
   // the timing events are recorded as graph nodes.
-  int enqueue_body(cudaStream_t st, uint64_t n, uint64_t seed, int grid, const unsigned long long *seed_dev) {
+  int enqueue_body(cudaStream_t st, uint64_t n, uint64_t seed, int grid, const unsigned long long *seed_dev,
+                   uint64_t first = 0, uint64_t count = 0, bool resume = false) {
     Range r("dies: enqueue transport + temperatures");
     int rc;
+    if (count == 0) count = n;
     const unsigned rec_flags = seed_dev ? cudaEventRecordExternal : cudaEventRecordDefault;
-    if ((rc = reset_accumulators_on(st))) return rc;
+    if ((rc = reset_accumulators_on(st, resume))) return rc;
     TransportParams P = params(MODE_IRE, n, seed);
     P.seed_dev = seed_dev;
     DIES_CUDA(cudaEventRecordWithFlags(ev[2], st, rec_flags));
+    // packages [first, first + count) of each source, in N_B sequential batches in the FP32 form
     const int nb = (prec == PREC_FP32) ? n_batches : 1;
-    const uint64_t per = (n + nb - 1) / nb;
+    const uint64_t per = (count + nb - 1) / nb;
     for (int b = 0; b < nb; ++b) {
-      const uint64_t begin = (uint64_t)b * per;
-      if (begin >= n) break;
-      const uint64_t len = (begin + per <= n) ? per : n - begin;
+      const uint64_t begin = first + (uint64_t)b * per;
+      if (begin >= first + count) break;
+      const uint64_t len = (begin + per <= first + count) ? per : first + count - begin;
       P.pkg_begin = begin;
       P.pkg_len = len;
       P.total = total_slots() * len;
@@ -569,6 +607,12 @@ struct Problem {
       if (prec == PREC_FP32) DIES_CUDA(launch_merge(st, n_cells, at<float>(lay.Eprev), at<float>(lay.Ecur)));
     }
     DIES_CUDA(cudaEventRecordWithFlags(ev[3], st, rec_flags));
+    // the FP32 forms' tally kernel adds the (cumulative) fixed-point injection
+    // and direct-escape tallies: their energy sums restart from zero
+    if (prec != PREC_FP64 && resume) {
+      DIES_CUDA(cudaMemsetAsync(ws + lay.energies + EN_INJECTED * 8, 0, 8, st));
+      DIES_CUDA(cudaMemsetAsync(ws + lay.energies + EN_DIRECT * 8, 0, 8, st));
+    }
     if (prec != PREC_FP64)
       DIES_CUDA(launch_tally(st, n_models, at<ModelDesc>(lay.desc), n, at<unsigned long long>(lay.sed_q),
                              at<unsigned long long>(lay.inj_q), at<unsigned long long>(lay.dir_q), at<double>(lay.sed),
@@ -646,7 +690,7 @@ struct Problem {
     DIES_CUDA(cudaStreamSynchronize(stream));
     if (!stats_pending) {
       if (stats.status_word & STATUS_TIMEOUT) return DIES_ETIMEOUT;
-      return (stats.status_word & STATUS_RANGE) ? DIES_ERANGE : DIES_OK;
+      return (stats.status_word & (STATUS_RANGE | STATUS_BOUNDS)) ? DIES_ERANGE : DIES_OK;
     }
     const bool st = static_pending;
     unsigned long long cnt[16];
@@ -698,6 +742,9 @@ struct Problem {
     if (status & STATUS_RANGE)
       return fail(DIES_ERANGE, "an absorbed-energy counter of the all-FP32 form left the FP32 range "
                                "(luminosity above ~1e38 erg/s): use DIES_PREC_MIXED");
+    if (status & STATUS_BOUNDS)
+      return fail(DIES_ERANGE, "device bounds check failed (check build; status 0x%x): an index left its table",
+                  status);
     return DIES_OK;
   }
 
@@ -720,6 +767,9 @@ struct Problem {
       return fail(DIES_EINVAL, "per-package records exist only in the FP64 form (n_events_out and path_hash_out must be NULL)");
     // the precision form of the pass: the handle's with DIES_FROZEN_FORM, else FP64
     const int fprec = in_form ? prec : PREC_FP64;
+    uint64_t first, count;
+    bool resume;
+    if ((rc = take_range(n, &first, &count, &resume))) return rc;
     if ((rc = ensure_device())) return rc;
     launches_at_start = g_launches.load();
     DIES_CUDA(cudaEventRecord(ev[0], stream));
@@ -753,12 +803,15 @@ struct Problem {
       if ((e = launch_frozen_cdf(stream, n_cells, F, at<double>(lay.freq), at<double>(lay.kabs), at<double>(lay.dnu),
                                  dT, dcdf)))
         break;
-      if ((rc = reset_accumulators())) break;
+      if ((rc = reset_accumulators(resume))) break;
       const int mode = (base == DIES_FROZEN_ABSORB_TERMINAL) ? MODE_FROZEN_TERMINAL : MODE_FROZEN;
       int grid;
       if ((rc = grid_for(fprec, mode, &grid))) break;
       if ((e = cudaEventRecord(ev[2], stream))) break;
       TransportParams P = params(mode, n, seed);
+      P.pkg_begin = first;
+      P.pkg_len = count;
+      P.total = total_slots() * count;
       P.cell_cdf = dcdf;
       P.rec_events = dev;
       P.rec_hash = dhash;
@@ -766,6 +819,10 @@ struct Problem {
       if ((e = launch_transport(fprec, mode, ev_out || hash_out, P, grid, block, stream))) break;
       if ((e = cudaEventRecord(ev[3], stream))) break;
       // the FP32 forms keep their escape and injection tallies in fixed point
+      if (fprec != PREC_FP64 && resume) {
+        if ((e = cudaMemsetAsync(ws + lay.energies + EN_INJECTED * 8, 0, 8, stream))) break;
+        if ((e = cudaMemsetAsync(ws + lay.energies + EN_DIRECT * 8, 0, 8, stream))) break;
+      }
       if (fprec != PREC_FP64 &&
           (e = launch_tally(stream, n_models, at<ModelDesc>(lay.desc), n, at<unsigned long long>(lay.sed_q),
                             at<unsigned long long>(lay.inj_q), at<unsigned long long>(lay.dir_q), at<double>(lay.sed),
@@ -1049,6 +1106,17 @@ static int set_launch_ex(Problem &p, const dies_launch *l) {
 int dies_set_launch_ex(dies_model *m, const dies_launch *launch) {
   if (!m) return fail(DIES_EINVAL, "model is NULL");
   return set_launch_ex(m->p, launch);
+}
+
+int dies_set_package_range(dies_model *m, uint64_t first, uint64_t count, int resume) {
+  if (!m) return fail(DIES_EINVAL, "model is NULL");
+  if (count == 0) return fail(DIES_EINVAL, "count must be >= 1");
+  if (resume != 0 && resume != 1) return fail(DIES_EINVAL, "resume must be 0 or 1");
+  m->p.range_set = true;
+  m->p.range_first = first;
+  m->p.range_count = count;
+  m->p.range_resume = resume != 0;
+  return DIES_OK;
 }
 
 int dies_set_time_budget(dies_model *m, double seconds) {
@@ -1355,6 +1423,10 @@ const char *dies_last_error(void) { return dies::t_error.c_str(); }
 
 uint64_t dies_launch_count(void) { return dies::g_launches.load(); }
 
-const char *dies_version(void) { return "dies-gb300 0.1 (sm_103a)"; }
+#ifdef DIES_CHECK
+const char *dies_version(void) { return "dies-gb300 0.2 (sm_103a, device bounds checks)"; }
+#else
+const char *dies_version(void) { return "dies-gb300 0.2 (sm_103a)"; }
+#endif
 
 }  // extern "C"

@@ -46,7 +46,27 @@ enum : uint32_t {
   STATUS_STUCK = 8u,   // a warp ran kFlightLimit moves without a rare event; its moving lanes were ended
   STATUS_ABANDONED = 16u,  // a package was still in flight when its lane left the work loop
   STATUS_RANGE = 32u,      // all-FP32 form: an absorbed-energy counter left the FP32 range
+  STATUS_BAD_ROW = 64u,    // check build: a table row, model or slot index out of range
 };
+constexpr uint32_t STATUS_BOUNDS = STATUS_BAD_CELL | STATUS_BAD_FREQ | STATUS_BAD_ROW;
+
+// Device bounds checks of the check build (compiled with -DDIES_CHECK): an
+// index outside its table sets a status flag (the run then reports
+// DIES_ERANGE) and is clamped into range, so the access that follows stays
+// in bounds.  No trap, no fault.  Compiled out otherwise.
+#ifdef DIES_CHECK
+#define DIES_BOUND(P, cond, flag, fix) \
+  do {                                 \
+    if (!(cond)) {                     \
+      atomicOr((P).status, (flag));    \
+      fix;                             \
+    }                                  \
+  } while (0)
+#else
+#define DIES_BOUND(P, cond, flag, fix) \
+  do {                                 \
+  } while (0)
+#endif
 
 // Consecutive loop iterations a warp may run without any lane finishing a
 // flight segment; a legitimate flight crosses at most ~2 x shells boundaries.
@@ -64,7 +84,7 @@ struct alignas(16) ModelDesc {
   double R;        // outer radius (length units)
   double L[2];     // source luminosities (erg/s), written by the table build
   unsigned long long pkg_off;  // first source slot of this model (slots x packages = work items)
-  float Lf[2];     // the luminosities as float (unused by the transport: package energies come from L)
+  float Lf[2];     // the luminosities as float (+inf above the float range; the transport forms L / N from L)
   float Rf;        // outer radius as float
   float pad1;
 };

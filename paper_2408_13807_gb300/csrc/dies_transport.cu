@@ -192,18 +192,15 @@ __device__ __forceinline__ int node_count_guided(const Shared &S, const float *L
   while (j < n && L[j] <= e) ++j;
   return j;
 }
-// The same count, also returning the first node above e (+inf past the table)
-// that the scan has loaded anyway.
+// The same count, also returning the first node above e (+inf past the
+// table).  The scan is bounded by n: e itself may be +inf (an energy beyond
+// the float range), which every node and the +inf padding would satisfy.
 __device__ __forceinline__ int node_count_guided_hi(const Shared &S, const float *L, int n, float e, float &hi) {
   const int d = __float_as_int(e) - S.g_b0;
   const int b = d < 0 ? 0 : min(d >> S.g_sh, kGuide - 1);
   int j = S.nguide[b];
-  float v = (j < n) ? L[j] : __int_as_float(0x7f800000);
-  while (v <= e) {
-    ++j;
-    v = (j < n) ? L[j] : __int_as_float(0x7f800000);
-  }
-  hi = v;
+  while (j < n && L[j] <= e) ++j;
+  hi = (j < n) ? L[j] : __int_as_float(0x7f800000);
   return j;
 }
 
@@ -315,6 +312,8 @@ __device__ __forceinline__ void add_model_q(unsigned long long *base, unsigned k
 template <int PREC>
 __device__ __forceinline__ void tally_sed(const TransportParams &P, Shared &S, Lane<typename RealOf<PREC>::T> &L,
                                           typename RealOf<PREC>::T w) {
+  DIES_BOUND(P, L.f >= 0 && L.f < kMaxFreq && L.model >= 0 && L.model < P.n_models, STATUS_BAD_FREQ,
+             { L.f = 0; L.model = 0; });
   if constexpr (PREC == PREC_FP64) {
     atomicAdd(P.sed + (size_t)L.model * kMaxFreq + L.f, w * L.eps);  // native FP64 reduction in L2
   } else {
@@ -364,7 +363,8 @@ template <int PREC, int OPT>
 __device__ __forceinline__ void boundary(const TransportParams &P, const Lane<typename RealOf<PREC>::T> &L,
                                          typename RealOf<PREC>::T &l, typename RealOf<PREC>::T &sb, int &next,
                                          typename RealOf<PREC>::T &rho) {
-  const int c = L.cell;
+  int c = L.cell;
+  DIES_BOUND(P, c >= -1 && c < L.n, STATUS_BAD_CELL, c = -1);
   if constexpr (PREC == PREC_FP64) {
     // cancellation-free forms of the two roots of |x + l d|^2 = R^2 (as the oracle)
     const int bi = L.cell_off + L.model + (c >= 0 ? c : 0);
@@ -600,6 +600,7 @@ __device__ __forceinline__ void assign(const TransportParams &P, Lane<typename R
     }
     m = lo;
   }
+  DIES_BOUND(P, m >= 0 && m < P.n_models, STATUS_BAD_ROW, m = 0);
   const ModelDesc *D = P.desc + m;
   const unsigned long long sl = slot - __ldg(&D->pkg_off);
   const int mask = __ldg(&D->src_mask);
@@ -652,7 +653,9 @@ __device__ __forceinline__ void inject(const TransportParams &P, Shared &S, Lane
   Real w_path = Real(1);  // free-path weight of the first flight (Eq. 8), applied after the injection tally
   if constexpr (PREC == PREC_FP64) {
     const double u_f = u01d(a.x, a.y), u_mu = u01d(a.z, a.w);
-    set_freq<PREC>(S, L, cdf_pick(S.src_cdf_d[L.src], u_f));
+    int f0 = cdf_pick(S.src_cdf_d[L.src], u_f);
+    DIES_BOUND(P, f0 >= 0 && f0 < P.F, STATUS_BAD_FREQ, f0 = 0);
+    set_freq<PREC>(S, L, f0);
     const U4 b = draw<PREC>(S, L);
     L.cell = (L.src == 0) ? L.n - 1 : __ldg(&D->point_cell);
     if (P.ffi) {  // the forced flight replaces these paths
@@ -684,7 +687,9 @@ __device__ __forceinline__ void inject(const TransportParams &P, Shared &S, Lane
       L.u_type = (P.ffi == 2) ? 0.0 : u01d(c.z, c.w);  // forcing on tau_A: the pre-walk sums tau_S0 here
     }
   } else {
-    set_freq<PREC>(S, L, alias_pick(S.src_alias[L.src], a.x >> 9));
+    int f0 = alias_pick(S.src_alias[L.src], a.x >> 9);
+    DIES_BOUND(P, f0 >= 0 && f0 < P.F, STATUS_BAD_FREQ, f0 = 0);
+    set_freq<PREC>(S, L, f0);
     const float v = u01f_fine(a.y);  // 1 - u of the direction draw
     L.cell = (L.src == 0) ? L.n - 1 : __ldg(&D->point_cell);
     w_path = set_paths(P, S, L, neg_ln_u(u01f_word(a.z)), neg_ln_u(u01f_word(a.w)));
@@ -866,10 +871,23 @@ __device__ __forceinline__ void scatter(const TransportParams &P, Shared &S, Lan
   record<RECORD>(L, EV_SCATTER, L.cell, L.f);
 }
 
+// Mixed form: the node count of e* = (E_old + u_e dE) / mass formed in FP64
+// and searched exactly against the FP64 nodes (E_old = old_d plus the
+// energies pre of the lane's aggregation-group predecessors).  Kept out of
+// line: inlined, this rarely taken FP64 code slowed the whole kernel by up
+// to 9 % (register allocation of the move loop, measured).
+__device__ __noinline__ int exact_row(const TransportParams &P, const Shared &S, const float *sLnode, double old_d,
+                                      float pre, float u_e, float dEf, int gc) {
+  const double od = old_d + f2d_nonneg(pre);
+  const double es_d = fma(f2d_nonneg(u_e), f2d_nonneg(dEf), od) * __ldg(P.inv_mass + gc);
+  return node_count_bits(P.Lnode_d, P.n_tnodes, node_count_guided(S, sLnode, P.n_tnodes, d2f_nonneg(es_d)), es_d);
+}
+
 // ---------------------------------------------- absorption + re-emission
 template <int PREC, int MODE, bool RECORD>
 __device__ __forceinline__ void absorb(const TransportParams &P, Shared &S, const float *sLnode,
                                        Lane<typename RealOf<PREC>::T> &L, Tally &T, const U4 &a) {
+  DIES_BOUND(P, L.cell >= 0 && L.cell < L.n, STATUS_BAD_CELL, L.cell = 0);
   const int gc = L.cell_off + L.cell;
   T.abs++;
   if constexpr (RECORD) L.nabs++;
@@ -897,9 +915,11 @@ __device__ __forceinline__ void absorb(const TransportParams &P, Shared &S, cons
       int j = node_count_f(sLnode, P.n_tnodes_pow2, (float)es);
       j = node_count_d(P.Lnode_d, P.n_tnodes, min(j, P.n_tnodes), es);
       if (en > __ldg(P.Lnode_d + P.n_tnodes - 1)) atomicAdd(&S.rare[CNT_CLAMP_HI], 1u);
-      const int row = min(j, P.n_tnodes - 1);
+      int row = min(j, P.n_tnodes - 1);
+      DIES_BOUND(P, row >= 0, STATUS_BAD_ROW, row = 0);
       f = cdf_pick_ldg(P.dcdf_d + ((size_t)row << kFreqShift), u_nu);
     }
+    DIES_BOUND(P, f >= 0 && f < P.F, STATUS_BAD_FREQ, f = 0);
     set_freq<PREC>(S, L, f);
     double rn = -1.0;  // re-emission radius; < 0: the absorption point
     if (P.remit_random) {
@@ -979,35 +999,42 @@ __device__ __forceinline__ void absorb(const TransportParams &P, Shared &S, cons
       // The row is the node interval holding e* = (E_old + u_e dE) / mass.
       // When e_new stays below the node above e_old by more than float
       // rounding (2^-20 relative), the interval of e_old holds e* for every
-      // u_e, and the float energies decide it.  Otherwise (an absorption whose
-      // [e_old, e_new] reaches a node: ~1e-4 of them in a well-filled cell)
-      // e* is formed in FP64 and searched exactly against the FP64 nodes: in
-      // a cell holding more than ~2^24 package energies dE is below one float
-      // ulp of E_old, where an FP32 e* would always take the interval of e_old.
+      // u_e, and the float energies decide it.  When [e_old, e_new] reaches
+      // a node and dE is resolved in float (dE > 2^-10 E_old: a cell holding
+      // few package energies), the float e* decides it.  Otherwise e* is
+      // formed in FP64 and searched exactly against the FP64 nodes: in a cell
+      // holding more than ~2^24 package energies dE is below one float ulp of
+      // E_old, where an FP32 e* would always take the interval of e_old.
+      // The float paths also need the float 1/mass to be a normal number (a
+      // very massive cell, e.g. a length unit of ~100 pc, underflows it).
       const float im = __ldg(P.inv_massf + gc);
-      const float eo = old_f * im;
-      en = fmaf(dEf, im, eo);
+      const float eo = old_f * im, de = dEf * im;
+      en = eo + de;
       float hi;
       j = node_count_guided_hi(S, sLnode, P.n_tnodes, eo, hi);
-      if (en >= hi * (1.0f - 0x1p-20f)) {
-        const double od = old_d + f2d_nonneg(pre_lane);
-        const double es_d = fma(f2d_nonneg(u_e), f2d_nonneg(dEf), od) * __ldg(P.inv_mass + gc);
-        j = node_count_bits(P.Lnode_d, P.n_tnodes, node_count_guided(S, sLnode, P.n_tnodes, d2f_nonneg(es_d)),
-                            es_d);
+      if (!(en < hi * (1.0f - 0x1p-20f)) || !(im >= 0x1p-126f)) {
+        if (de > eo * 0x1p-10f && im >= 0x1p-126f && en < __int_as_float(0x7f800000))
+          j = node_count_guided(S, sLnode, P.n_tnodes, fmaf(u_e, de, eo));
+        else
+          j = exact_row(P, S, sLnode, old_d, pre_lane, u_e, dEf, gc);
       }
     } else {
       const float im = __ldg(P.inv_massf + gc);
+      if (!(im >= 0x1p-126f)) atomicOr(P.status, STATUS_RANGE);  // 1/mass below the float range
       const float eo = old_f * im, de = dEf * im;
       j = node_count_guided(S, sLnode, P.n_tnodes, fmaf(u_e, de, eo));
       en = eo + de;
     }
     if (en > sLnode[P.n_tnodes - 1]) atomicAdd(&S.rare[CNT_CLAMP_HI], 1u);
-    const int row = min(j, P.n_tnodes - 1);
+    int row = min(j, P.n_tnodes - 1);
+    DIES_BOUND(P, row >= 0, STATUS_BAD_ROW, row = 0);
     // re-emission bin from the row of the interval holding e* (a launch option:
     // one probe of an alias row, or a binary search of an FP32 CDF row)
     const int f_new = P.remit_cdf ? cdf_pick_ldg(P.dcdf_f + ((size_t)row << kFreqShift), u01f_word(a.y))
                                   : alias_pick_ldg(P.dalias + ((size_t)row << kFreqShift), a.y >> 9);
-    set_freq<PREC>(S, L, f_new);
+    int f_chk = f_new;
+    DIES_BOUND(P, f_chk >= 0 && f_chk < P.F, STATUS_BAD_FREQ, f_chk = 0);
+    set_freq<PREC>(S, L, f_chk);
     float r2 = L.p2 + L.s * L.s;
     float r = sqrtf(r2);
     if (P.remit_random) {
@@ -1402,6 +1429,9 @@ __device__ __forceinline__ bool is_event(int st) {
 // g at pool[g * kPool + i], so a warp's accesses to distinct slots do not
 // share banks more than the 128-bit access pattern requires.
 __device__ __forceinline__ void pool_put(float4 *pool, int slot, const Lane<float> &L) {
+#ifdef DIES_CHECK
+  if ((unsigned)slot >= (unsigned)kPool) return;  // (the caller's ballot arithmetic keeps it in range)
+#endif
   const uint32_t meta =
       ((uint32_t)L.f & 63u) | ((uint32_t)L.src << 8) | ((uint32_t)L.st << 12) | ((uint32_t)L.next_ev << 16);
   pool[slot] = make_float4(L.p2, L.s, L.w, L.acc);
@@ -1413,6 +1443,9 @@ __device__ __forceinline__ void pool_put(float4 *pool, int slot, const Lane<floa
 }
 
 __device__ __forceinline__ void pool_get(const float4 *pool, int slot, const Shared &S, Lane<float> &L) {
+#ifdef DIES_CHECK
+  if ((unsigned)slot >= (unsigned)kPool) slot = 0;
+#endif
   const float4 a = pool[slot], b = pool[kPool + slot], c = pool[2 * kPool + slot], d = pool[3 * kPool + slot];
   L.p2 = a.x;
   L.s = a.y;

@@ -53,7 +53,7 @@ EXPORTS = (
     "dies_run_batch", "dies_run_batch_async", "dies_batch_get_temperatures", "dies_batch_get_escaping_sed",
     "dies_batch_get_stats", "dies_destroy_batch", "dies_last_error", "dies_launch_count", "dies_version",
     "dies_measure_peaks",
-    "dies_run_frozen_static", "dies_set_launch_ex", "dies_batch_set_launch_ex",
+    "dies_run_frozen_static", "dies_set_launch_ex", "dies_batch_set_launch_ex", "dies_set_package_range",
 )
 
 
@@ -158,6 +158,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "dies_batch_set_stream": (i, [_vp, _vp]),
         "dies_batch_set_launch": (i, [_vp, i, i, i, i, i]),
         "dies_set_launch_ex": (i, [_vp, _vp]),
+        "dies_set_package_range": (i, [_vp, u64, u64, i]),
         "dies_batch_set_launch_ex": (i, [_vp, _vp]),
         "dies_run_batch": (i, [_vp, u64, u64]),
         "dies_run_batch_async": (i, [_vp, u64, u64]),
@@ -245,6 +246,10 @@ def dies_set_launch_ex(h, **kw):
 
 def dies_batch_set_launch_ex(h, **kw):
     return _check(load().dies_batch_set_launch_ex(h, ctypes.byref(dies_launch(**kw))))
+
+
+def dies_set_package_range(h, first: int, count: int, resume: bool = False):
+    return _check(load().dies_set_package_range(h, int(first), int(count), int(bool(resume))))
 
 
 def dies_set_time_budget(h, seconds: float):

@@ -197,3 +197,21 @@ def test_frozen_flags_are_validated_on_the_host(lib):
             assert e.value.code == D.DIES_EINVAL, flags
     finally:
         D.dies_destroy_model(h)
+
+
+def test_package_range_is_validated(lib):
+    m = W.external_cloud(4, 1.0)
+    h = D.dies_create_model(m.radii, m.rho, m.length_unit_cm)
+    try:
+        D.dies_set_dust(h, m.freq, m.kabs, m.ksca, m.g)
+        D.dies_set_sources(h, m.J_ext, 0.0, None)
+        for args in ((0, 0, False), (0, 5, 2)):
+            with pytest.raises(D.DiesError) as e:
+                D._check(D.load().dies_set_package_range(h, args[0], args[1], int(args[2])))
+            assert e.value.code == D.DIES_EINVAL
+        D.dies_set_package_range(h, 3, 4, False)
+        with pytest.raises(D.DiesError) as e:  # [3, 7) does not lie in [0, 5): refused before any device work
+            D.dies_run(h, 5, 0)
+        assert e.value.code == D.DIES_EINVAL
+    finally:
+        D.dies_destroy_model(h)

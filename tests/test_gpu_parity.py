@@ -466,3 +466,62 @@ def test_two_packages_per_thread_in_a_batch_and_at_the_time_budget(D):
     st = m.run(200_000, seed=2).stats()
     assert st["status_word"] == 0 and st["injected"] == 200_000
     m.close()
+
+
+def test_package_range_resume_is_the_whole_run(D, oracle):
+    """Checkpoint and resume at a package index (dies_set_package_range).
+    A frozen pass split at package 7000, the second part resuming, gives
+    the whole pass's per-package event counts and path hashes bit for bit,
+    its counters exactly, and its absorbed energies and SED to FP64 rounding
+    of the summation order."""
+    cloud = W.external_cloud(16, 5.0).replace(L_point=W.L_SUN, point_spec=W.blackbody(W.freq_grid(), 6000.0))
+    T = np.linspace(12.0, 20.0, cloud.n_cells)
+    N, k = 20_000, 7_000
+    m = D.Model(cloud, precision="fp64")
+    ev_ref, hs_ref = m.run_frozen(T, N, seed=4)
+    E_ref, sed_ref, st_ref = m.absorbed(), m.sed(), m.stats()
+    D.dies_set_package_range(m.h, 0, k, False)
+    ev1, hs1 = m.run_frozen(T, N, seed=4)
+    D.dies_set_package_range(m.h, k, N - k, True)
+    ev2, hs2 = m.run_frozen(T, N, seed=4)
+    rows = np.arange(N * cloud.n_sources) % N < k  # row s*N + j of source s
+    assert not ev1[~rows].any() and not ev2[rows].any()  # rows outside a range are left untouched
+    ev = np.where(rows[:, None], ev1, ev2)
+    hs = np.where(rows, hs1, hs2)
+    assert np.array_equal(ev, ev_ref) and np.array_equal(hs, hs_ref)
+    st = m.stats()
+    for key in ("injected", "escaped", "absorbed", "scattered", "crossed", "killed_weight"):
+        assert st[key] == st_ref[key], key
+    np.testing.assert_allclose(m.absorbed(), E_ref, rtol=1e-12, atol=1e-15 * E_ref.max())
+    np.testing.assert_allclose(m.sed(), sed_ref, rtol=1e-12, atol=1e-15 * sed_ref.max())
+    assert st["E_injected"] == pytest.approx(st_ref["E_injected"], rel=1e-12)
+    with pytest.raises(D.DiesError) as ei:
+        D.dies_set_package_range(m.h, N - 10, 20, True)
+        m.run_frozen(T, N, seed=4)
+    assert ei.value.code == D.DIES_EINVAL
+    m.close()
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp32"])
+def test_package_range_resume_ire_matches_the_oracle(D, oracle, prec):
+    """An IRE run of 1e6 packages done as three resumed ranges starts every
+    package once, conserves energy, and its temperatures match the FP64
+    oracle over 16 seeds (the all-FP32 form with its N_B batches inside
+    each range)."""
+    cloud = W.config1()
+    N = 1_000_000
+    m = D.Model(cloud, precision=prec, n_batches=10 if prec == "fp32" else 1)
+    Tg = []
+    for s in range(16):
+        for first, count, resume in ((0, 300_000, False), (300_000, 450_000, True), (750_000, 250_000, True)):
+            D.dies_set_package_range(m.h, first, count, resume)
+            m.run(N, seed=s)
+        st = m.stats()
+        assert st["status_word"] == 0 and st["injected"] == N
+        assert st["escaped"] + st["killed_weight"] + st["killed_cap"] == N
+        assert st["E_escaped"] + st["E_lost"] == pytest.approx(st["E_injected"], rel=1e-9)
+        assert st["E_injected"] == pytest.approx(oracle.source_luminosity(cloud).sum(), rel=1e-9)
+        Tg.append(m.temperatures())
+    m.close()
+    To = np.array([r["T"] for r in oracle.run_seeds(cloud, N, range(100, 116))])
+    assert_ensembles_agree(np.array(Tg), To, 0.01, min_gated=cloud.n_cells // 2)

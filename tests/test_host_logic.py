@@ -116,7 +116,8 @@ def test_autotune_search_stages_cover_every_knob():
     assert best == {"block_size": 128, "blocks_per_sm": 0, "rare_batch": 24, "inner_moves": 64,
                     "aggregate_atomics": 1, "refill_divisor": 32, "reemit_table": 1, "packages_per_thread": 2}
     n_grid = len(autotune.GRID_BLOCK) * len(autotune.GRID_RARE) * len(autotune.GRID_INNER) * len(autotune.GRID_AGG)
-    assert len(times) == 2 * n_grid + len(autotune.GRID_REFILL) - 1 + len(autotune.GRID_TABLE) - 1
+    n_pool = len(autotune.GRID_BLOCK) * len(autotune.GRID_RARE)
+    assert len(times) == n_grid + n_pool + len(autotune.GRID_REFILL) - 1 + len(autotune.GRID_TABLE) - 1
     best1, _ = autotune._stages(timer2, False, (128,), (24,), (0,), (64,), (0, 1), (32,), (0, 1), pool_ok=False)
     assert best1["packages_per_thread"] == 1  # forced first interaction: no pool variant
     best64, _ = autotune._stages(timer2, True, (128,), (24,), (0,), (64,), (0, 1), (32,), (0, 1))
