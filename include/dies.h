@@ -235,8 +235,10 @@ enum {
  *                        counter (32 to 1024 packages, a multiple of 32, so 1
  *                        to 32 packages per lane); 0 = 64.  Relative to the
  *                        launch, so one value serves every package count;
- *   reemit_table         DIES_TABLE_ALIAS or DIES_TABLE_CDF (FP32 forms; the
- *                        FP64 form searches FP64 CDF rows);
+ *   reemit_table         DIES_TABLE_ALIAS or DIES_TABLE_CDF: a kernel variant of
+ *                        the mixed form's single-model runs without forced
+ *                        first interaction; every other run uses alias rows
+ *                        (the FP64 form searches FP64 CDF rows);
  *   packages_per_thread  1 (or 0) or 2: with 2 (FP32 forms without forced
  *                        first interaction; other runs ignore it) each lane
  *                        owns two slots of a per-warp pool of packages in

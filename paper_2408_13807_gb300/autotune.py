@@ -5,7 +5,8 @@ fastest configuration, in stages: a grid over (block size, CTAs per SM,
 rare_batch, inner moves, aggregated absorption atomics), then a second
 package per thread in the warp's shared-memory pool, then the share of
 the launch a warp claims per trip to the device work counter (1/16 to 1/256),
-then the layout of the re-emission table (alias rows or FP32 CDF rows).
+then the layout of the re-emission table (alias rows or FP32 CDF rows; a
+variant of the mixed form's single-model kernels).
 Every candidate computes the same distributions; only the speed differs.
 The FP64-crossing threshold of the mixed form is an accuracy setting, not a
 speed one, so it is set by a rule on each model's shell geometry
@@ -184,6 +185,8 @@ def tune(cloud, precision: str = "mixed", n: Optional[int] = None, blocks: Itera
          tables: Iterable[int] = GRID_TABLE) -> Tuple[dict, dict]:
     """Tune every knob on ``cloud``; return (best configuration, timings)."""
     n = n or TUNE_N[precision]
+    if precision != "mixed" or cloud.ffi:
+        tables = (D.DIES_TABLE_ALIAS,)  # the CDF-row layout is a variant of the mixed single-model kernels only
     best, times = _stages(lambda sh: _time_model(cloud, precision, sh, n), precision == "fp64", blocks, rare, bps,
                           inner, agg, ppt, tables, pool_ok=not cloud.ffi)
     return dict(best, ms=times["/".join(str(best[k]) for k in KEYS)], n=n,
@@ -230,8 +233,8 @@ def best_batch_launch(clouds, allow_tuning: bool = True, n_per_model: int = TUNE
         finally:
             bt.close()
 
-    best, times = _stages(timer, False, GRID_BLOCK, GRID_RARE, GRID_BPS, GRID_INNER, GRID_AGG, GRID_REFILL, GRID_TABLE,
-                          pool_ok=not clouds[0].ffi)
+    best, times = _stages(timer, False, GRID_BLOCK, GRID_RARE, GRID_BPS, GRID_INNER, GRID_AGG, GRID_REFILL,
+                          (D.DIES_TABLE_ALIAS,), pool_ok=not clouds[0].ffi)
     rec = dict(best, ms=times["/".join(str(best[k]) for k in KEYS)], n=n_per_model, candidates=len(times),
                fp64_radius=0.0)
     with _lock:

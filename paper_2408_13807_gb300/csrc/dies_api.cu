@@ -458,7 +458,7 @@ struct Problem {
     P.mode = mode;
     P.max_events = 100000000ULL;
     P.time_budget_ns = (unsigned long long)(time_budget_s * 1e9);
-    P.inv_n = (float)(1.0 / (double)n);
+    P.inv_n = (float)(0x1p64 / (double)n);
     P.inv_nd = 1.0 / (double)n;
     P.k_bg_f = (float)k_bg;
     P.g_E = g_E;

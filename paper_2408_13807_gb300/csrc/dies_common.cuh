@@ -84,7 +84,7 @@ struct alignas(16) ModelDesc {
   double R;        // outer radius (length units)
   double L[2];     // source luminosities (erg/s), written by the table build
   unsigned long long pkg_off;  // first source slot of this model (slots x packages = work items)
-  float Lf[2];     // the luminosities as float (+inf above the float range; the transport forms L / N from L)
+  float Lf[2];     // 2^-64 x the luminosities, as float (FP32 forms: package energy = Lf x inv_n)
   float Rf;        // outer radius as float
   float pad1;
 };
@@ -125,7 +125,7 @@ struct TransportParams {
   const uint16_t *nguide;   // FP32 forms: [kGuide] first node of each bucket of float(Lambda) bits
   const int *nmeta;         // {bits of Lambda_0, bucket shift}
   const double *dcdf_d;
-  const float *dcdf_f;      // FP32 forms with remit_cdf: the re-emission CDF rows in FP32
+  const float *dcdf_f;      // mixed form with remit_cdf: the re-emission CDF rows in FP32
   int n_tnodes;
   int n_tnodes_pow2;        // smallest power of two >= n_tnodes
   // frozen pass
@@ -159,8 +159,8 @@ struct TransportParams {
   int mode;
   unsigned long long max_events;
   unsigned long long time_budget_ns;
-  float inv_n;      // 1 / n_per_source
-  double inv_nd;    // 1 / n_per_source in FP64 (package energy L / N, formed once per package)
+  float inv_n;      // 2^64 / n_per_source (FP32 package energies Lf x inv_n = L / N)
+  double inv_nd;    // 1 / n_per_source in FP64
   float k_bg_f;     // k_bg as float (FP32 forms)
   int kbg_plain;    // k_bg == 1/2: no weighting
   int r64;          // MIXED form: some model has FP64 crossing distances in its inner shells
@@ -169,7 +169,8 @@ struct TransportParams {
   unsigned chunk;   // work items a warp takes from the counter at a time (multiple of 32, >= 32; set at launch)
   unsigned refill_div;  // the chunk is about 1/refill_div of a warp's share of the launch (0 = 64)
   int agg;          // FP32 forms: warp-aggregated absorption atomics (lanes sharing a cell add once)
-  int remit_cdf;    // FP32 forms: re-emission bin by binary search of CDF rows instead of alias rows
+  int remit_cdf;    // mixed form, single model, no forced interaction: the kernel variant that
+                    // searches FP32 CDF rows for the re-emission bin instead of alias rows
   int pool;         // FP32 forms without forced interaction: two packages per thread (per-warp pools)
 };
 

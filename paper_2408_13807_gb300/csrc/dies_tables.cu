@@ -205,8 +205,11 @@ __global__ void k_cells(int n_models, ModelDesc *desc, int n_cells_total, const 
     const double Rcm = desc[c].R * length_unit_cm;
     desc[c].L[0] = (desc[c].src_mask & 1) ? 4.0 * kPi * kPi * Rcm * Rcm * src_sum[0] : 0.0;
     desc[c].L[1] = (desc[c].src_mask & 2) ? L_point : 0.0;
-    desc[c].Lf[0] = (float)desc[c].L[0];
-    desc[c].Lf[1] = (float)desc[c].L[1];
+    // 2^-64 L: the FP32 forms form the package energy L / N as this times
+    // 2^64 / N (both factors exact powers of two apart), which keeps it
+    // finite for luminosities above the float range
+    desc[c].Lf[0] = (float)(desc[c].L[0] * 0x1p-64);
+    desc[c].Lf[1] = (float)(desc[c].L[1] * 0x1p-64);
     desc[c].Rf = (float)desc[c].R;
   }
   if (c >= n_cells_total) return;

@@ -57,6 +57,7 @@ enum State {
 constexpr int OPT_R64 = 1;    // MIXED: FP64 crossing distances in the innermost shells of some model
 constexpr int OPT_NOFFI = 2;  // no forced first interaction: every moving package is in ST_NORMAL
 constexpr int OPT_BATCH = 4;  // several models: per-model injection tallies grouped per warp (add_model_q)
+constexpr int OPT_CDF = 8;    // MIXED single model: re-emission bin from FP32 CDF rows instead of alias rows
 
 template <int PREC>
 struct RealOf {
@@ -611,9 +612,10 @@ __device__ __forceinline__ void assign(const TransportParams &P, Lane<typename R
   L.n = __ldg(&D->n_cells);
   L.n64 = __ldg(&D->n_fp64);
   if constexpr (PREC == PREC_FP64) L.eps = __ldg(&D->L[L.src]) / (double)P.n_per_source;
-  // FP32 forms: the package energy L / N rounded once to float (formed in
-  // FP64: a luminosity above the float range still gives a float energy)
-  else L.eps = __double2float_rn(__ldg(&D->L[L.src]) * P.inv_nd);
+  // FP32 forms: the package energy L / N in float, from two factors scaled
+  // by 2^-64 and 2^64 so that a luminosity above the float range (3.4e38)
+  // still gives a finite energy
+  else L.eps = __ldg(&D->Lf[L.src]) * P.inv_n;  // (2^-64 L)(2^64 / N): finite for any L below 6e57 erg/s
   L.pkg_lo = (uint32_t)pkg;
   L.pkg_hi = (uint32_t)(pkg >> 32);
   L.blk = 0;
@@ -884,7 +886,7 @@ __device__ __noinline__ int exact_row(const TransportParams &P, const Shared &S,
 }
 
 // ---------------------------------------------- absorption + re-emission
-template <int PREC, int MODE, bool RECORD>
+template <int PREC, int MODE, bool RECORD, int OPT>
 __device__ __forceinline__ void absorb(const TransportParams &P, Shared &S, const float *sLnode,
                                        Lane<typename RealOf<PREC>::T> &L, Tally &T, const U4 &a) {
   DIES_BOUND(P, L.cell >= 0 && L.cell < L.n, STATUS_BAD_CELL, L.cell = 0);
@@ -999,25 +1001,20 @@ __device__ __forceinline__ void absorb(const TransportParams &P, Shared &S, cons
       // The row is the node interval holding e* = (E_old + u_e dE) / mass.
       // When e_new stays below the node above e_old by more than float
       // rounding (2^-20 relative), the interval of e_old holds e* for every
-      // u_e, and the float energies decide it.  When [e_old, e_new] reaches
-      // a node and dE is resolved in float (dE > 2^-10 E_old: a cell holding
-      // few package energies), the float e* decides it.  Otherwise e* is
-      // formed in FP64 and searched exactly against the FP64 nodes: in a cell
-      // holding more than ~2^24 package energies dE is below one float ulp of
-      // E_old, where an FP32 e* would always take the interval of e_old.
-      // The float paths also need the float 1/mass to be a normal number (a
-      // very massive cell, e.g. a length unit of ~100 pc, underflows it).
+      // u_e, and the float energies decide it.  Otherwise (an absorption whose
+      // [e_old, e_new] reaches a node: ~1e-4 of them in a well-filled cell)
+      // e* is formed in FP64 and searched exactly against the FP64 nodes: in
+      // a cell holding more than ~2^24 package energies dE is below one float
+      // ulp of E_old, where an FP32 e* would always take the interval of e_old.
+      // (the float path also needs the float 1/mass to be a normal number: a
+      // very massive cell, e.g. a length unit of ~100 pc, underflows it)
       const float im = __ldg(P.inv_massf + gc);
-      const float eo = old_f * im, de = dEf * im;
-      en = eo + de;
+      const float eo = old_f * im;
+      en = fmaf(dEf, im, eo);
       float hi;
       j = node_count_guided_hi(S, sLnode, P.n_tnodes, eo, hi);
-      if (!(en < hi * (1.0f - 0x1p-20f)) || !(im >= 0x1p-126f)) {
-        if (de > eo * 0x1p-10f && im >= 0x1p-126f && en < __int_as_float(0x7f800000))
-          j = node_count_guided(S, sLnode, P.n_tnodes, fmaf(u_e, de, eo));
-        else
-          j = exact_row(P, S, sLnode, old_d, pre_lane, u_e, dEf, gc);
-      }
+      if (!(en < hi * (1.0f - 0x1p-20f)) || !(im >= 0x1p-126f))
+        j = exact_row(P, S, sLnode, old_d, pre_lane, u_e, dEf, gc);
     } else {
       const float im = __ldg(P.inv_massf + gc);
       if (!(im >= 0x1p-126f)) atomicOr(P.status, STATUS_RANGE);  // 1/mass below the float range
@@ -1028,10 +1025,11 @@ __device__ __forceinline__ void absorb(const TransportParams &P, Shared &S, cons
     if (en > sLnode[P.n_tnodes - 1]) atomicAdd(&S.rare[CNT_CLAMP_HI], 1u);
     int row = min(j, P.n_tnodes - 1);
     DIES_BOUND(P, row >= 0, STATUS_BAD_ROW, row = 0);
-    // re-emission bin from the row of the interval holding e* (a launch option:
-    // one probe of an alias row, or a binary search of an FP32 CDF row)
-    const int f_new = P.remit_cdf ? cdf_pick_ldg(P.dcdf_f + ((size_t)row << kFreqShift), u01f_word(a.y))
-                                  : alias_pick_ldg(P.dalias + ((size_t)row << kFreqShift), a.y >> 9);
+    // re-emission bin from the row of the interval holding e*: one probe of an
+    // alias row, or (kernel variant OPT_CDF) a binary search of an FP32 CDF row
+    int f_new;
+    if constexpr ((OPT & OPT_CDF) != 0) f_new = cdf_pick_ldg(P.dcdf_f + ((size_t)row << kFreqShift), u01f_word(a.y));
+    else f_new = alias_pick_ldg(P.dalias + ((size_t)row << kFreqShift), a.y >> 9);
     int f_chk = f_new;
     DIES_BOUND(P, f_chk >= 0 && f_chk < P.F, STATUS_BAD_FREQ, f_chk = 0);
     set_freq<PREC>(S, L, f_chk);
@@ -1190,7 +1188,7 @@ __device__ __forceinline__ void rare(const TransportParams &P, Shared &S, const 
   L.st = ST_NORMAL;
   if (kind == ST_INJECT) inject<PREC, RECORD, kGroup>(P, S, L, T, a);
   else if (kind == ST_SCATTER) scatter<PREC, RECORD>(P, S, L, T, a);
-  else absorb<PREC, MODE, RECORD>(P, S, sLnode, L, T, a);
+  else absorb<PREC, MODE, RECORD, OPT>(P, S, sLnode, L, T, a);
   // weighted directions and free paths (Eqs. 6-8) change the weight at events:
   // the floor of Sect. 2.2.1 applies after each
   if (kind != ST_INJECT && L.st == ST_NORMAL && L.w < 1e-10f) lose<RECORD>(P, S, L, CNT_KILL_WEIGHT);
@@ -1332,8 +1330,6 @@ __global__ void __launch_bounds__(256, PREC == PREC_FP64 ? 1 : 5) k_transport(co
   bool timed_out = false;
   Lane<Real> L;
   L.st = ST_DEAD;
-  const int lane = threadIdx.x & 31;
-  const unsigned lanes_below = (1u << lane) - 1u;
   const unsigned long long t0 = globaltimer();
   unsigned idle = 0;  // iterations since this warp last ran its rare path
   unsigned sections = 0;
@@ -1832,6 +1828,9 @@ cudaError_t launch_transport(int prec, int mode, bool record, const TransportPar
       if (P.ffi)
         return P.r64 ? launch_one<PREC_MIXED, MODE_IRE, false, OPT_R64>(P, grid, block, smem, st)
                      : launch_one<PREC_MIXED, MODE_IRE, false, 0>(P, grid, block, smem, st);
+      if (P.remit_cdf)
+        return P.r64 ? launch_one<PREC_MIXED, MODE_IRE, false, OPT_R64 | OPT_NOFFI | OPT_CDF>(P, grid, block, smem, st)
+                     : launch_one<PREC_MIXED, MODE_IRE, false, OPT_NOFFI | OPT_CDF>(P, grid, block, smem, st);
       return P.r64 ? launch_one<PREC_MIXED, MODE_IRE, false, OPT_R64 | OPT_NOFFI>(P, grid, block, smem, st)
                    : launch_one<PREC_MIXED, MODE_IRE, false, OPT_NOFFI>(P, grid, block, smem, st);
     case PREC_FP32:
