@@ -50,7 +50,8 @@ size_t transport_smem_bytes(int n_tnodes_pow2);
 cudaError_t launch_transport(int prec, int mode, bool record, const TransportParams &P, int grid, int block,
                              cudaStream_t st);
 cudaError_t transport_occupancy(int prec, int mode, int block, int n_tnodes_pow2, bool r64, bool ffi, bool batch,
-                                bool pool, int *blocks_per_sm);
+                                bool pool, bool plain, int *blocks_per_sm);
+bool plain_weighting(const TransportParams &P);
 cudaError_t launch_finalize(cudaStream_t st, int n_cells, const double *E, const float *Eprev, const float *Ecur,
                             int fp32, const double *inv_mass, const double *Lnode, const double *lnT, int n,
                             double *T_out);
@@ -486,8 +487,9 @@ struct Problem {
     int bps = blocks_per_sm;
     int occ = 0;
     const bool r64 = (prec_ == PREC_MIXED && fp64_radius > 0.0);
+    const bool plain = plain_weighting(params(mode, 1, 0));  // the kernel variant the launch will pick
     DIES_CUDA(transport_occupancy(prec_, mode, block, next_pow2(n_tnodes), r64, ffi != 0, n_models > 1,
-                                  pkgs_per_thread == 2, &occ));
+                                  pkgs_per_thread == 2, plain, &occ));
     if (occ < 1) return fail(DIES_ECUDA, "transport kernel cannot be resident with block size %d", block);
     if (bps <= 0 || bps > occ) bps = occ;
     *grid = sm_count * bps;
@@ -1284,7 +1286,7 @@ int dies_run_frozen_static(dies_model *m, const double *T_frozen_dev, uint64_t n
                               p.at<double>(p.lay.dnu), T_frozen_dev, cdf));
   int occ = 0;
   DIES_CUDA(transport_occupancy(PREC_FP64, MODE_FROZEN, p.block, next_pow2(p.n_tnodes), false, false, false, false,
-                                &occ));
+                                false, &occ));
   if (occ < 1) return fail(DIES_ECUDA, "transport kernel cannot be resident with block size %d", p.block);
   const int bps = (p.blocks_per_sm > 0 && p.blocks_per_sm < occ) ? p.blocks_per_sm : occ;
   const int mode = (flags == DIES_FROZEN_ABSORB_TERMINAL) ? MODE_FROZEN_TERMINAL : MODE_FROZEN;
