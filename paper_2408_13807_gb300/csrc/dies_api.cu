@@ -54,7 +54,7 @@ cudaError_t transport_occupancy(int prec, int mode, int block, int n_tnodes_pow2
 bool plain_weighting(const TransportParams &P);
 cudaError_t launch_finalize(cudaStream_t st, int n_cells, const double *E, const float *Eprev, const float *Ecur,
                             int fp32, const double *inv_mass, const double *Lnode, const double *lnT, int n,
-                            double *T_out);
+                            double *T_out, double *E_out);
 cudaError_t launch_merge(cudaStream_t st, int n_cells, float *Eprev, float *Ecur);
 cudaError_t launch_tally(cudaStream_t st, int n_models, const ModelDesc *desc, unsigned long long n_per_source,
                          const unsigned long long *sed_q, const unsigned long long *inj_q,
@@ -96,7 +96,7 @@ bool finite_nonneg(const double *a, int n) {
 
 // Offsets (bytes) of every segment of the device workspace.
 struct Layout {
-  size_t desc, radii, rho_in, r2d, r2f, rhod, rhof, inv_mass, inv_massf, kA_d, kA_f, geo, rhoe, E, Eprev, Ecur, T, sed;
+  size_t desc, radii, rho_in, r2d, r2f, rhod, rhof, inv_mass, inv_massf, kA_d, kA_f, geo, rhoe, E, Es, Eprev, Ecur, T, sed;
   size_t sed_q, inj_q, dir_q;
   size_t freq, kabs, ksca, g, J, spec, dnu, src_cdf_d, src_alias, src_sum;
   size_t Lnode_d, Lnode_f, lnT, dalias, dcdf_d, dcdf_f, nguide, nmeta;
@@ -218,8 +218,9 @@ struct Problem {
     L.geo = seg(nb * 16);
     L.rhoe = seg(nb * 4);
     L.E = seg(nc * 8);
+    L.Es = seg(nc * kAccSpreadBytes);  // IRE accumulator, one 256-byte segment per cell
     L.Eprev = seg(nc * 4);
-    L.Ecur = seg(nc * 4);
+    L.Ecur = seg(nc * kAccSpreadBytes);  // cell c at c * kCStride
     L.T = seg(nc * 8);
     L.sed = seg(nm * kMaxFreq * 8);
     const size_t rp = (size_t)tally_replicas();
@@ -423,9 +424,14 @@ struct Problem {
     P.inj_q = at<unsigned long long>(lay.inj_q);
     P.dir_q = at<unsigned long long>(lay.dir_q);
     P.rep = tally_replicas();
-    P.E = at<double>(lay.E);
+    // IRE runs add absorbed energies into the spread accumulator (E is
+    // filled from it by the finalize kernel); the frozen passes into E
+    const bool ire = (mode == MODE_IRE);
+    P.E = at<double>(ire ? lay.Es : lay.E);
+    P.e_stride = ire ? kEStride : 1;
     P.Eprev = at<float>(lay.Eprev);
     P.Ecur = at<float>(lay.Ecur);
+    P.c_stride = kCStride;
     P.sed = at<double>(lay.sed);
     P.kabs_d = at<double>(lay.kabs);
     P.ksca_d = at<double>(lay.ksca);
@@ -525,8 +531,9 @@ struct Problem {
       return DIES_OK;
     }
     DIES_CUDA(cudaMemsetAsync(ws + lay.E, 0, (size_t)n_cells * 8, st));
+    DIES_CUDA(cudaMemsetAsync(ws + lay.Es, 0, (size_t)n_cells * kAccSpreadBytes, st));
     DIES_CUDA(cudaMemsetAsync(ws + lay.Eprev, 0, (size_t)n_cells * 4, st));
-    DIES_CUDA(cudaMemsetAsync(ws + lay.Ecur, 0, (size_t)n_cells * 4, st));
+    DIES_CUDA(cudaMemsetAsync(ws + lay.Ecur, 0, (size_t)n_cells * kAccSpreadBytes, st));
     DIES_CUDA(cudaMemsetAsync(ws + lay.sed, 0, (size_t)n_models * kMaxFreq * 8, st));
     const size_t rp = (size_t)tally_replicas();
     DIES_CUDA(cudaMemsetAsync(ws + lay.sed_q, 0, rp * n_models * 2 * kMaxFreq * 8, st));
@@ -619,9 +626,9 @@ struct Problem {
       DIES_CUDA(launch_tally(st, n_models, at<ModelDesc>(lay.desc), n, at<unsigned long long>(lay.sed_q),
                              at<unsigned long long>(lay.inj_q), at<unsigned long long>(lay.dir_q), at<double>(lay.sed),
                              at<double>(lay.energies), tally_replicas()));
-    DIES_CUDA(launch_finalize(st, n_cells, at<double>(lay.E), at<float>(lay.Eprev), at<float>(lay.Ecur),
+    DIES_CUDA(launch_finalize(st, n_cells, at<double>(lay.Es), at<float>(lay.Eprev), at<float>(lay.Ecur),
                               prec == PREC_FP32, at<double>(lay.inv_mass), at<double>(lay.Lnode_d),
-                              at<double>(lay.lnT), n_tnodes, at<double>(lay.T)));
+                              at<double>(lay.lnT), n_tnodes, at<double>(lay.T), at<double>(lay.E)));
     return DIES_OK;
   }
 
@@ -1183,7 +1190,8 @@ int dies_get_absorbed(dies_model *m, double *E, int n) {
     if (rc && rc != DIES_ETIMEOUT && rc != DIES_ERANGE) return rc;
     std::vector<float> a(n), b(n);
     DIES_CUDA(cudaMemcpy(a.data(), p.ws + p.lay.Eprev, (size_t)n * 4, cudaMemcpyDeviceToHost));
-    DIES_CUDA(cudaMemcpy(b.data(), p.ws + p.lay.Ecur, (size_t)n * 4, cudaMemcpyDeviceToHost));
+    // the current-batch counter of cell i sits at i * kCStride
+    DIES_CUDA(cudaMemcpy2D(b.data(), 4, p.ws + p.lay.Ecur, dies::kAccSpreadBytes, 4, (size_t)n, cudaMemcpyDeviceToHost));
     for (int i = 0; i < n; ++i) E[i] = (double)a[i] + (double)b[i];
     return rc;
   }

@@ -172,7 +172,20 @@ struct TransportParams {
   int remit_cdf;    // mixed form, single model, no forced interaction: the kernel variant that
                     // searches FP32 CDF rows for the re-emission bin instead of alias rows
   int pool;         // FP32 forms without forced interaction: two packages per thread (per-warp pools)
+  int e_stride;     // doubles between two cells' accumulators in E (IRE runs: kEStride, else 1)
+  int c_stride;     // floats between two cells' counters in Ecur (IRE runs: kCStride, else 1)
 };
+
+// Absorbed-energy accumulators of IRE runs, one per cell, each on its own
+// 256-byte segment.  The absorptions of an optically thick model pile up in
+// a few inner cells; packed 8 bytes apart, those cells' returning atomic adds
+// all went to one L2 slice (measured: its atomic unit 65 % busy, the mean
+// slice 0.5 %).  Spread, they are served by different slices: +68 % packages/s
+// on the 1024-shell internal-source model, +28 % on C2 A_V = 100 (measured;
+// 128-byte spacing gave most of it, 4 KB no more than 256 bytes).
+constexpr int kAccSpreadBytes = 256;
+constexpr int kEStride = kAccSpreadBytes / 8;  // FP64 accumulator E
+constexpr int kCStride = kAccSpreadBytes / 4;  // FP32 current-batch counter Ecur
 
 // Alias-table entries (FP32 forms): bits 6..31 the 26-bit acceptance
 // threshold of the slot, bits 0..5 the alias bin; a slot that is full has

@@ -903,8 +903,8 @@ __device__ __forceinline__ void absorb(const TransportParams &P, Shared &S, cons
   if constexpr (MODE == MODE_FROZEN_TERMINAL) {
     // the package energy in FP64 in every form (a test mode: the tally must
     // match the FP64 injected energy, not the float package energy)
-    if constexpr (PREC == PREC_FP64) atomicAdd(P.E + gc, L.w * L.eps);
-    else atomicAdd(P.E + gc, (double)L.w * (__ldg(&P.desc[L.model].L[L.src]) * P.inv_nd));
+    if constexpr (PREC == PREC_FP64) atomicAdd(P.E + (size_t)gc * P.e_stride, L.w * L.eps);
+    else atomicAdd(P.E + (size_t)gc * P.e_stride, (double)L.w * (__ldg(&P.desc[L.model].L[L.src]) * P.inv_nd));
     record<RECORD>(L, EV_ABSORB, L.cell, L.f);
     finish<RECORD>(P, L);
     return;
@@ -914,10 +914,10 @@ __device__ __forceinline__ void absorb(const TransportParams &P, Shared &S, cons
     const double u_e = u01d(a.x, a.y), u_nu = u01d(a.z, a.w);
     int f;
     if constexpr (MODE == MODE_FROZEN) {
-      atomicAdd(P.E + gc, dE);
+      atomicAdd(P.E + (size_t)gc * P.e_stride, dE);
       f = cdf_pick_ldg(P.cell_cdf + (size_t)gc * kMaxFreq, u_nu);
     } else {
-      const double old = atomicAdd(P.E + gc, dE);
+      const double old = atomicAdd(P.E + (size_t)gc * P.e_stride, dE);
       const double im = __ldg(P.inv_mass + gc);
       const double eo = old * im, en = (old + dE) * im;
       const double es = eo + u_e * (en - eo);
@@ -983,21 +983,21 @@ __device__ __forceinline__ void absorb(const TransportParams &P, Shared &S, cons
       }
       if constexpr (PREC == PREC_MIXED) {
         double old = 0.0;
-        if (lane == lead) old = atomicAdd(P.E + gc, f2d_nonneg(tot));
+        if (lane == lead) old = atomicAdd(P.E + (size_t)gc * P.e_stride, f2d_nonneg(tot));
         old_d = __shfl_sync(grp, old, lead);
         old_f = d2f_nonneg(old_d) + pre;
         pre_lane = pre;
       } else {
         float old = 0.0f;
-        if (lane == lead) old = __ldg(P.Eprev + gc) + atomicAdd(P.Ecur + gc, tot);
+        if (lane == lead) old = __ldg(P.Eprev + gc) + atomicAdd(P.Ecur + (size_t)gc * P.c_stride, tot);
         old_f = __shfl_sync(grp, old, lead) + pre;
       }
     } else if constexpr (PREC == PREC_MIXED) {
-      old_d = atomicAdd(P.E + gc, f2d_nonneg(dEf));
+      old_d = atomicAdd(P.E + (size_t)gc * P.e_stride, f2d_nonneg(dEf));
       old_f = d2f_nonneg(old_d);
     } else {
       // FP32 form: two FP32 counters, E = E_prev (frozen in this batch) + E_cur
-      old_f = __ldg(P.Eprev + gc) + atomicAdd(P.Ecur + gc, dEf);
+      old_f = __ldg(P.Eprev + gc) + atomicAdd(P.Ecur + (size_t)gc * P.c_stride, dEf);
     }
     if constexpr (PREC == PREC_FP32) {
       if (!(old_f < 1.0e38f)) atomicOr(P.status, STATUS_RANGE);  // the run then reports DIES_ERANGE
@@ -1696,11 +1696,15 @@ __global__ void k_tally(const ModelDesc *desc, unsigned long long n_per_source, 
 // Temperature of every cell from its absorbed energy: log-log interpolation
 // of T(Lambda) between table nodes; below the first node T_min, above the
 // last T_max.
+// E and Ecur hold cell c at c * kEStride and c * kCStride (the spread IRE
+// accumulators); the FP64 forms' energies are also written to E_out packed.
 __global__ void k_finalize(int n_cells, const double *E, const float *Eprev, const float *Ecur, int fp32,
-                           const double *inv_mass, const double *Lnode, const double *lnT, int n, double *T_out) {
+                           const double *inv_mass, const double *Lnode, const double *lnT, int n, double *T_out,
+                           double *E_out) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n_cells) return;
-  const double Ec = fp32 ? (double)(Eprev[c] + Ecur[c]) : E[c];
+  const double Ec = fp32 ? (double)(Eprev[c] + Ecur[(size_t)c * kCStride]) : E[(size_t)c * kEStride];
+  if (!fp32) E_out[c] = Ec;
   const double e = Ec * inv_mass[c];
   double lT;
   if (!(e >= Lnode[0])) {
@@ -1724,8 +1728,9 @@ __global__ void k_finalize(int n_cells, const double *E, const float *Eprev, con
 __global__ void k_merge_batches(int n_cells, float *Eprev, float *Ecur) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c < n_cells) {
-    Eprev[c] += Ecur[c];
-    Ecur[c] = 0.0f;
+    float *cur = Ecur + (size_t)c * kCStride;  // spread counter (kCStride)
+    Eprev[c] += *cur;
+    *cur = 0.0f;
   }
 }
 
@@ -1930,9 +1935,10 @@ cudaError_t launch_tally(cudaStream_t st, int n_models, const ModelDesc *desc, u
 
 cudaError_t launch_finalize(cudaStream_t st, int n_cells, const double *E, const float *Eprev, const float *Ecur,
                             int fp32, const double *inv_mass, const double *Lnode, const double *lnT, int n,
-                            double *T_out) {
+                            double *T_out, double *E_out) {
   const int tb = 256;
-  k_finalize<<<(n_cells + tb - 1) / tb, tb, 0, st>>>(n_cells, E, Eprev, Ecur, fp32, inv_mass, Lnode, lnT, n, T_out);
+  k_finalize<<<(n_cells + tb - 1) / tb, tb, 0, st>>>(n_cells, E, Eprev, Ecur, fp32, inv_mass, Lnode, lnT, n, T_out,
+                                                     E_out);
   launch_counter_add(1);
   return cudaGetLastError();
 }
