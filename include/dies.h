@@ -115,7 +115,20 @@ typedef struct {
                              kernel_ms: the split of a run into upload, table build and
                              transport + temperatures that Sect. 3.1 reports as total vs
                              kernel time */
+  uint32_t grid;          /* transport launch of the run: CTAs (0 after dies_run_frozen_static) */
+  uint32_t block;         /* threads per CTA */
+  uint32_t variant;       /* DIES_VARIANT_* bits of the transport kernel that ran */
 } dies_stats;
+
+/* dies_stats.variant: compile-time variants of the transport kernel, chosen
+ * per run from the options and the launch (results do not depend on them
+ * beyond FP32 rounding order). */
+#define DIES_VARIANT_PLAIN_WEIGHTING 1u  /* FP32 forms: every weighting option but k_bg neutral,
+                                            the weighting code not compiled in */
+#define DIES_VARIANT_STAGED_GEOMETRY 2u  /* one model: geometry records copied to shared memory
+                                            per CTA (dies_launch.stage_geometry) */
+#define DIES_VARIANT_PACKAGE_POOL 4u     /* two packages per thread (launch knob) */
+#define DIES_VARIANT_FP64_CROSSINGS 8u   /* mixed form: FP64 crossing distances in inner shells */
 
 /* ------------------------------------------------------------ one model */
 
@@ -257,6 +270,11 @@ typedef struct dies_launch {
   int refill_divisor;
   int reemit_table;
   int packages_per_thread;
+  int stage_geometry;  /* 1: a single model (FP32 forms, no FP64 crossings, no package
+                          pools) has its geometry records (16 bytes + a density per
+                          shell and the void) copied to shared memory by every CTA
+                          and read there at each crossing, wherever that costs no
+                          resident CTA; 0: read through L1 (dies_set_launch: 1) */
 } dies_launch;
 int dies_set_launch_ex(dies_model *m, const dies_launch *launch);
 

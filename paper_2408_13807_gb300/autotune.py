@@ -6,7 +6,8 @@ rare_batch, inner moves, aggregated absorption atomics), then a second
 package per thread in the warp's shared-memory pool, then the share of
 the launch a warp claims per trip to the device work counter (1/16 to 1/256),
 then the layout of the re-emission table (alias rows or FP32 CDF rows; a
-variant of the mixed form's single-model kernels).
+variant of the mixed form's single-model kernels), then whether a single
+model's geometry records are staged in shared memory.
 Every candidate computes the same distributions; only the speed differs.
 The FP64-crossing threshold of the mixed form is an accuracy setting, not a
 speed one, so it is set by a rule on each model's shell geometry
@@ -35,10 +36,11 @@ GRID_BPS = (0,)
 GRID_REFILL = (16, 32, 64, 128, 256)   # refills per warp share of a launch (chunk = share / this)
 GRID_TABLE = (D.DIES_TABLE_ALIAS, D.DIES_TABLE_CDF)
 GRID_PPT = (1, 2)   # packages per thread: registers only, or a second one in the warp's shared-memory pool
+GRID_STAGE = (1, 0)  # single model: geometry staged in shared memory, or read through L1
 KEYS = ("block_size", "blocks_per_sm", "rare_batch", "inner_moves", "aggregate_atomics", "refill_divisor",
-        "reemit_table", "packages_per_thread")
+        "reemit_table", "packages_per_thread", "stage_geometry")
 DEFAULT = {"block_size": 256, "blocks_per_sm": 0, "rare_batch": 16, "inner_moves": 32, "aggregate_atomics": 0,
-           "refill_divisor": 64, "reemit_table": D.DIES_TABLE_ALIAS, "packages_per_thread": 1}
+           "refill_divisor": 64, "reemit_table": D.DIES_TABLE_ALIAS, "packages_per_thread": 1, "stage_geometry": 1}
 
 # FP64 crossing distances where FP32 would lose more than this relative
 # accuracy on a crossing (see fp64_radius_for): a path-length error of 1e-4
@@ -132,12 +134,14 @@ def _cached(c: Dict[str, dict], key: str) -> Optional[dict]:
     return {k: int(e[k]) for k in KEYS} if e is not None and all(k in e for k in KEYS) else None
 
 
-def _stages(timer, fp64: bool, blocks, rare, bps, inner, agg, refill, tables, ppt=GRID_PPT, pool_ok=True):
+def _stages(timer, fp64: bool, blocks, rare, bps, inner, agg, refill, tables, ppt=GRID_PPT, pool_ok=True,
+            stage=GRID_STAGE):
     """Coordinate search: the shape grid, then two packages per thread (the
     shared-memory pool) with the best shape over block size and rare batch,
-    then the refill divisor, then the table layout; returns (best, timings).
-    ``pool_ok`` is False where the pool variant does not exist (FP64 form,
-    forced first interaction)."""
+    then the refill divisor, then the table layout, then geometry staging;
+    returns (best, timings).  ``pool_ok`` is False where the pool variant
+    does not exist (FP64 form, forced first interaction); ``stage`` is (1,)
+    where staging does not apply (FP64 form, batches)."""
     times = {}
 
     def key(sh):
@@ -150,7 +154,7 @@ def _stages(timer, fp64: bool, blocks, rare, bps, inner, agg, refill, tables, pp
         return times[k]
 
     if fp64:
-        agg, tables = (0,), (D.DIES_TABLE_ALIAS,)  # no aggregated path, FP64 CDF rows only
+        agg, tables, stage = (0,), (D.DIES_TABLE_ALIAS,), (1,)  # no aggregated path, FP64 CDF rows only
     if fp64 or not pool_ok:
         ppt = (1,)
     base = dict(DEFAULT)
@@ -175,20 +179,23 @@ def _stages(timer, fp64: bool, blocks, rare, bps, inner, agg, refill, tables, pp
     best = dict(zip(KEYS, (int(x) for x in min(times, key=times.get).split("/"))))
     for t in tables:
         try_shape(dict(best, reemit_table=t))
+    best = dict(zip(KEYS, (int(x) for x in min(times, key=times.get).split("/"))))
+    for g in stage:
+        try_shape(dict(best, stage_geometry=g))
     k = min(times, key=times.get)
     return dict(zip(KEYS, (int(x) for x in k.split("/")))), times
 
 
 def tune(cloud, precision: str = "mixed", n: Optional[int] = None, blocks: Iterable[int] = GRID_BLOCK,
          rare: Iterable[int] = GRID_RARE, bps: Iterable[int] = GRID_BPS,
-         inner: Iterable[int] = GRID_INNER, agg: Iterable[int] = GRID_AGG, ppt: Iterable[int] = GRID_REFILL,
+         inner: Iterable[int] = GRID_INNER, agg: Iterable[int] = GRID_AGG, refill: Iterable[int] = GRID_REFILL,
          tables: Iterable[int] = GRID_TABLE) -> Tuple[dict, dict]:
     """Tune every knob on ``cloud``; return (best configuration, timings)."""
     n = n or TUNE_N[precision]
     if precision != "mixed" or cloud.ffi:
         tables = (D.DIES_TABLE_ALIAS,)  # the CDF-row layout is a variant of the mixed single-model kernels only
     best, times = _stages(lambda sh: _time_model(cloud, precision, sh, n), precision == "fp64", blocks, rare, bps,
-                          inner, agg, ppt, tables, pool_ok=not cloud.ffi)
+                          inner, agg, refill, tables, pool_ok=not cloud.ffi)
     return dict(best, ms=times["/".join(str(best[k]) for k in KEYS)], n=n,
                 fp64_radius=fp64_radius_for(cloud) if precision == "mixed" else 0.0,
                 candidates=len(times)), times
@@ -234,7 +241,7 @@ def best_batch_launch(clouds, allow_tuning: bool = True, n_per_model: int = TUNE
             bt.close()
 
     best, times = _stages(timer, False, GRID_BLOCK, GRID_RARE, GRID_BPS, GRID_INNER, GRID_AGG, GRID_REFILL,
-                          (D.DIES_TABLE_ALIAS,), pool_ok=not clouds[0].ffi)
+                          (D.DIES_TABLE_ALIAS,), pool_ok=not clouds[0].ffi, stage=(1,) if len(clouds) > 1 else GRID_STAGE)
     rec = dict(best, ms=times["/".join(str(best[k]) for k in KEYS)], n=n_per_model, candidates=len(times),
                fp64_radius=0.0)
     with _lock:

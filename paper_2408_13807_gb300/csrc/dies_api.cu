@@ -50,7 +50,7 @@ size_t transport_smem_bytes(int n_tnodes_pow2);
 cudaError_t launch_transport(int prec, int mode, bool record, const TransportParams &P, int grid, int block,
                              cudaStream_t st);
 cudaError_t transport_occupancy(int prec, int mode, int block, int n_tnodes_pow2, bool r64, bool ffi, bool batch,
-                                bool pool, bool plain, int *blocks_per_sm);
+                                bool pool, bool plain, int sgeo_n, int *blocks_per_sm);
 bool plain_weighting(const TransportParams &P);
 cudaError_t launch_finalize(cudaStream_t st, int n_cells, const double *E, const float *Eprev, const float *Ecur,
                             int fp32, const double *inv_mass, const double *Lnode, const double *lnT, int n,
@@ -135,6 +135,9 @@ struct Problem {
   bool range_set = false, range_resume = false;
   uint64_t range_first = 0, range_count = 0;
   int pkgs_per_thread = 1;  // 2: a second package per lane in per-warp shared-memory pools (FP32 forms, no FFI)
+  int stage_geo = 1;  // launch knob: stage a single model's geometry in shared memory where it costs no CTA
+  int sgeo_n = 0;  // geometry records the next IRE launch stages in shared memory (set by grid_for; 0: none)
+  uint32_t last_grid = 0, last_block = 0, last_variant = 0;  // the launch grid_for chose (reported in dies_stats)
   int refill_div = 0;  // a warp takes ~1/refill_div of its share of the launch per trip to the work counter (0 = 64)
   int remit_table = DIES_TABLE_ALIAS;
   double time_budget_s = 120.0;
@@ -432,6 +435,7 @@ struct Problem {
     P.Eprev = at<float>(lay.Eprev);
     P.Ecur = at<float>(lay.Ecur);
     P.c_stride = kCStride;
+    P.sgeo_n = (mode == MODE_IRE) ? sgeo_n : 0;
     P.sed = at<double>(lay.sed);
     P.kabs_d = at<double>(lay.kabs);
     P.ksca_d = at<double>(lay.ksca);
@@ -489,16 +493,40 @@ struct Problem {
     return P;
   }
 
+  // Grid of the next launch, and whether it stages the geometry in shared
+  // memory: only for one model without FP64 crossings or package pools, and
+  // only where the staged records cost no resident CTA.
   int grid_for(int prec_, int mode, int *grid) {
     int bps = blocks_per_sm;
     int occ = 0;
     const bool r64 = (prec_ == PREC_MIXED && fp64_radius > 0.0);
+    const bool pool = pkgs_per_thread == 2;
+    sgeo_n = 0;
     const bool plain = plain_weighting(params(mode, 1, 0));  // the kernel variant the launch will pick
-    DIES_CUDA(transport_occupancy(prec_, mode, block, next_pow2(n_tnodes), r64, ffi != 0, n_models > 1,
-                                  pkgs_per_thread == 2, plain, &occ));
+    DIES_CUDA(transport_occupancy(prec_, mode, block, next_pow2(n_tnodes), r64, ffi != 0, n_models > 1, pool, plain,
+                                  0, &occ));
     if (occ < 1) return fail(DIES_ECUDA, "transport kernel cannot be resident with block size %d", block);
     if (bps <= 0 || bps > occ) bps = occ;
+    if (stage_geo && mode == MODE_IRE && n_models == 1 && prec_ != PREC_FP64 && !r64 && !(pool && ffi == 0)) {
+      int occ_s = 0;
+      // a refusal here (staged records beyond the shared-memory limit) only means: no staging
+      if (transport_occupancy(prec_, mode, block, next_pow2(n_tnodes), false, ffi != 0, false, pool, plain,
+                              n_cells + 1, &occ_s) != cudaSuccess) {
+        cudaGetLastError();
+        occ_s = 0;
+      }
+      if (occ_s >= bps) sgeo_n = n_cells + 1;
+    }
     *grid = sm_count * bps;
+    last_grid = (uint32_t)*grid;
+    last_block = (uint32_t)block;
+    last_variant = 0;
+    if (mode == MODE_IRE && prec_ != PREC_FP64) {
+      if (plain) last_variant |= DIES_VARIANT_PLAIN_WEIGHTING;
+      if (sgeo_n > 0) last_variant |= DIES_VARIANT_STAGED_GEOMETRY;
+      if (pool && ffi == 0) last_variant |= DIES_VARIANT_PACKAGE_POOL;
+      if (r64) last_variant |= DIES_VARIANT_FP64_CROSSINGS;
+    }
     return DIES_OK;
   }
 
@@ -744,6 +772,11 @@ struct Problem {
     s.status_word = status;
     for (int i = 0; i < 16; ++i) s.diag[i] = diag[i];
     s.launches = (uint32_t)(g_launches.load() - launches_at_start);
+    if (!st) {
+      s.grid = last_grid;
+      s.block = last_block;
+      s.variant = last_variant;
+    }
     stats = s;
     stats_pending = false;
     static_pending = false;
@@ -1104,11 +1137,13 @@ static int set_launch_ex(Problem &p, const dies_launch *l) {
     return fail(DIES_EINVAL, "packages_per_thread must be 0, 1 or 2");
   if (l->reemit_table != DIES_TABLE_ALIAS && l->reemit_table != DIES_TABLE_CDF)
     return fail(DIES_EINVAL, "reemit_table must be DIES_TABLE_ALIAS or DIES_TABLE_CDF");
+  if (l->stage_geometry != 0 && l->stage_geometry != 1) return fail(DIES_EINVAL, "stage_geometry must be 0 or 1");
   int rc = set_launch(p, l->block_size, l->blocks_per_sm, l->rare_batch, l->inner_moves, l->aggregate_atomics);
   if (rc) return rc;
   p.refill_div = l->refill_divisor;
   p.pkgs_per_thread = l->packages_per_thread == 2 ? 2 : 1;
   p.remit_table = l->reemit_table;
+  p.stage_geo = l->stage_geometry;
   return DIES_OK;
 }
 
@@ -1294,7 +1329,7 @@ int dies_run_frozen_static(dies_model *m, const double *T_frozen_dev, uint64_t n
                               p.at<double>(p.lay.dnu), T_frozen_dev, cdf));
   int occ = 0;
   DIES_CUDA(transport_occupancy(PREC_FP64, MODE_FROZEN, p.block, next_pow2(p.n_tnodes), false, false, false, false,
-                                false, &occ));
+                                false, 0, &occ));
   if (occ < 1) return fail(DIES_ECUDA, "transport kernel cannot be resident with block size %d", p.block);
   const int bps = (p.blocks_per_sm > 0 && p.blocks_per_sm < occ) ? p.blocks_per_sm : occ;
   const int mode = (flags == DIES_FROZEN_ABSORB_TERMINAL) ? MODE_FROZEN_TERMINAL : MODE_FROZEN;

@@ -174,6 +174,7 @@ struct TransportParams {
   int pool;         // FP32 forms without forced interaction: two packages per thread (per-warp pools)
   int e_stride;     // doubles between two cells' accumulators in E (IRE runs: kEStride, else 1)
   int c_stride;     // floats between two cells' counters in Ecur (IRE runs: kCStride, else 1)
+  int sgeo_n;       // single-model IRE runs: geometry records staged in shared memory (0: read from L1/L2)
 };
 
 // Absorbed-energy accumulators of IRE runs, one per cell, each on its own

@@ -37,6 +37,10 @@ DIES_FROZEN_FORM = 2
 DIES_MAX_FREQ = 64
 DIES_TABLE_ALIAS = 0
 DIES_TABLE_CDF = 1
+DIES_VARIANT_PLAIN_WEIGHTING = 1
+DIES_VARIANT_STAGED_GEOMETRY = 2
+DIES_VARIANT_PACKAGE_POOL = 4
+DIES_VARIANT_FP64_CROSSINGS = 8
 
 PREC = {"mixed": DIES_PREC_MIXED, "fp32": DIES_PREC_FP32, "fp64": DIES_PREC_FP64}
 
@@ -73,6 +77,7 @@ class dies_stats(ctypes.Structure):
         ("transport_ms", ctypes.c_double),
         ("status_word", ctypes.c_uint32), ("launches", ctypes.c_uint32), ("diag", ctypes.c_uint32 * 16),
         ("upload_ms", ctypes.c_double),
+        ("grid", ctypes.c_uint32), ("block", ctypes.c_uint32), ("variant", ctypes.c_uint32),
     ]
 
     def as_dict(self):
@@ -237,7 +242,7 @@ def dies_set_launch(h, block_size: int, blocks_per_sm: int = 0, rare_batch: int 
 class dies_launch(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int) for k in ("block_size", "blocks_per_sm", "rare_batch", "inner_moves",
                                              "aggregate_atomics", "refill_divisor", "reemit_table",
-                                             "packages_per_thread")]
+                                             "packages_per_thread", "stage_geometry")]
 
 
 def dies_set_launch_ex(h, **kw):
@@ -439,7 +444,7 @@ class Model:
                  tgrid=(2.7, 1500.0, 1024), torch_memory: bool = True, device: int = 0, block_size: int = 256,
                  blocks_per_sm: int = 0, rare_batch: int = 16, inner_moves: int = 32, aggregate_atomics: int = 0,
                  graph: bool = False, refill_divisor: int = 0, reemit_table: int = DIES_TABLE_ALIAS,
-                 packages_per_thread: int = 1):
+                 packages_per_thread: int = 1, stage_geometry: int = 1):
         self.cloud = cloud
         self.h = dies_create_model(cloud.radii, cloud.rho, cloud.length_unit_cm)
         self.n_cells = cloud.n_cells
@@ -453,7 +458,7 @@ class Model:
         dies_set_launch_ex(self.h, block_size=block_size, blocks_per_sm=blocks_per_sm, rare_batch=rare_batch,
                            inner_moves=inner_moves, aggregate_atomics=aggregate_atomics,
                            refill_divisor=refill_divisor, reemit_table=reemit_table,
-                                 packages_per_thread=packages_per_thread)
+                           packages_per_thread=packages_per_thread, stage_geometry=stage_geometry)
         dies_set_graph(self.h, graph)
         if torch_memory:
             stream, self._ws = _torch_stream_and_workspace(dies_workspace_bytes(self.h), device)
@@ -512,7 +517,7 @@ class Batch:
     def __init__(self, clouds, block_size: int = 256, blocks_per_sm: int = 0, rare_batch: int = 16,
                  inner_moves: int = 32, aggregate_atomics: int = 0, graph: bool = False,
                  precision: str = "mixed", n_batches: int = 1, refill_divisor: int = 0,
-                 reemit_table: int = DIES_TABLE_ALIAS, packages_per_thread: int = 1):
+                 reemit_table: int = DIES_TABLE_ALIAS, packages_per_thread: int = 1, stage_geometry: int = 1):
         c0 = clouds[0]
         n = np.array([c.n_cells for c in clouds], dtype=np.int32)
         self.offsets = np.concatenate([[0], np.cumsum(n)]).astype(np.int32)
@@ -530,7 +535,7 @@ class Batch:
         dies_batch_set_launch_ex(self.h, block_size=block_size, blocks_per_sm=blocks_per_sm, rare_batch=rare_batch,
                                  inner_moves=inner_moves, aggregate_atomics=aggregate_atomics,
                                  refill_divisor=refill_divisor, reemit_table=reemit_table,
-                                 packages_per_thread=packages_per_thread)
+                                 packages_per_thread=packages_per_thread, stage_geometry=stage_geometry)
         dies_batch_set_graph(self.h, graph)
         dies_batch_set_weighting(self.h, weighting_of(c0))
         dies_batch_set_precision(self.h, PREC[precision], n_batches)

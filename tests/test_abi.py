@@ -20,6 +20,10 @@ def lib():
     return D.load()
 
 
+OK_LAUNCH = dict(block_size=128, blocks_per_sm=0, rare_batch=12, inner_moves=32, aggregate_atomics=0,
+                 refill_divisor=64, reemit_table=0, packages_per_thread=1, stage_geometry=1)
+
+
 def declared_functions():
     src = open(os.path.join(ROOT, "include", "dies.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
@@ -75,6 +79,10 @@ def test_create_and_set_validate_inputs(lib):
             lambda: D.dies_set_launch(h, 128, 0, 8, 0),
             lambda: D.dies_set_launch(h, 128, 0, 8, 65),
             lambda: D.dies_set_launch(h, 128, 0, 8, 8, 2),
+            lambda: D.dies_set_launch_ex(h, **dict(OK_LAUNCH, refill_divisor=5000)),
+            lambda: D.dies_set_launch_ex(h, **dict(OK_LAUNCH, reemit_table=2)),
+            lambda: D.dies_set_launch_ex(h, **dict(OK_LAUNCH, packages_per_thread=3)),
+            lambda: D.dies_set_launch_ex(h, **dict(OK_LAUNCH, stage_geometry=2)),
             lambda: D._check(D.load().dies_set_graph(h, 2)),
             lambda: D.dies_set_time_budget(h, 0.0),
             lambda: D.dies_set_weighting_ex(h, D.weighting_of(m.replace(g_E=1.0))),
@@ -215,3 +223,51 @@ def test_package_range_is_validated(lib):
         assert e.value.code == D.DIES_EINVAL
     finally:
         D.dies_destroy_model(h)
+
+
+def _header_constants():
+    """Numeric #define DIES_* and enum constants DIES_* = value of include/dies.h."""
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "dies.h")).read(), flags=re.S)
+    c = {k: int(v) for k, v in re.findall(r"#define\s+(DIES_[A-Z0-9_]+)\s+(-?\d+)u?\s*$", src, flags=re.M)}
+    c.update({k: int(v) for k, v in re.findall(r"\b(DIES_[A-Z0-9_]+)\s*=\s*(-?\d+)", src)})
+    return c
+
+
+# limits of the library that the binding does not need
+HOST_ONLY = {"DIES_MAX_SHELLS", "DIES_MAX_TNODES", "DIES_STATIC_MAX_SHELLS"}
+
+
+def test_header_constants_match_the_binding():
+    """Every numeric constant of include/dies.h has the same value in the binding."""
+    consts = _header_constants()
+    assert len(consts) >= 25
+    for k, v in consts.items():
+        if k not in HOST_ONLY:
+            assert getattr(D, k) == v, k
+
+
+def test_binding_structs_match_the_c_layout(tmp_path):
+    """The ctypes mirrors of the ABI structs have the size and field offsets
+    that a C compiler gives the header's structs."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    structs = {"dies_stats": D.dies_stats, "dies_weighting": D.dies_weighting, "dies_peaks": D.dies_peaks,
+               "dies_launch": D.dies_launch}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "dies.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["  return 0;", "}"]
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)])
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l}
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert got[(name, f)] == getattr(cls, f).offset, (name, f)

@@ -343,6 +343,33 @@ def test_plain_kernel_variant_matches_the_general_kernel(D, prec, ffi):
         assert st["status_word"] == 0
         assert st["E_escaped"] + st["E_lost"] == pytest.approx(st["E_injected"], rel=1e-6)
     assert sp["E_injected"] == pytest.approx(sg["E_injected"], rel=1e-6)
+    assert sp["variant"] & D.DIES_VARIANT_PLAIN_WEIGHTING
+    assert not sg["variant"] & D.DIES_VARIANT_PLAIN_WEIGHTING
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp32"])
+def test_staged_geometry_matches_reading_it_through_l1(D, prec):
+    """A single model's geometry records copied to shared memory by every CTA
+    (launch knob stage_geometry = 1) against the same model with the records
+    read through L1 (0): the variant bits report which kernel ran, the
+    16-seed temperature ensembles of the two pass the acceptance rule
+    against each other, and both conserve energy."""
+    cloud = W.config3()
+    N = 10_000_000
+    nb = 10 if prec == "fp32" else 1
+    runs = {}
+    for g in (1, 0):
+        m = D.Model(cloud, precision=prec, n_batches=nb, stage_geometry=g)
+        T = np.array([m.run(N, seed=100 * g + s).temperatures() for s in range(16)])
+        runs[g] = (T, m.stats())
+        m.close()
+    assert runs[1][1]["variant"] & D.DIES_VARIANT_STAGED_GEOMETRY
+    assert not runs[0][1]["variant"] & D.DIES_VARIANT_STAGED_GEOMETRY
+    for _, st in runs.values():
+        assert st["status_word"] == 0 and st["injected"] == N
+        assert st["E_escaped"] + st["E_lost"] == pytest.approx(st["E_injected"], rel=1e-6)
+    r = assert_ensembles_agree(runs[1][0], runs[0][0], 0.01, min_gated=cloud.n_cells // 4)
+    print(f"{prec} staged vs L1: gated {r['n_gated']}, max rel {r['max_rel_gated']:.4f}, max |t| {r['max_z']:.2f}")
 
 
 def test_density_dependent_kA_matches_oracle(D, oracle):

@@ -70,7 +70,7 @@ def test_autotune_uses_cache_without_gpu(tmp_path, monkeypatch):
     key = autotune.config_class(m, "mixed")
     old = autotune.config_class(W.config3(), "mixed")
     full = {"block_size": 128, "blocks_per_sm": 0, "rare_batch": 12, "inner_moves": 16, "aggregate_atomics": 1,
-            "refill_divisor": 128, "reemit_table": 1, "packages_per_thread": 2}
+            "refill_divisor": 128, "reemit_table": 1, "packages_per_thread": 2, "stage_geometry": 0}
     cache.write_text(json.dumps({key: dict(full, ms=1.0),
                                  old: {"block_size": 128, "blocks_per_sm": 0, "rare_batch": 12, "inner_moves": 16,
                                        "aggregate_atomics": 1, "ms": 1.0}}))
@@ -104,25 +104,29 @@ def test_noise_profile_statistics():
 def test_autotune_search_stages_cover_every_knob():
     """The tuner's coordinate search (with a synthetic timer: fastest at
     block 128, rare 24, inner 64, aggregation on, refill divisor 32, CDF
-    rows) visits the shape grid, then packages per thread, then the table
-    layout, and returns the optimum of each stage."""
+    rows, geometry read through L1) visits the shape grid, then packages per
+    thread, then the refill divisor, the table layout and geometry staging,
+    and returns the optimum of each stage."""
     def timer(sh):
         return (abs(sh["block_size"] - 128) + abs(sh["rare_batch"] - 24) + abs(sh["inner_moves"] - 64) +
-                (1 - sh["aggregate_atomics"]) + abs(sh["refill_divisor"] - 32) + (1 - sh["reemit_table"]))
+                (1 - sh["aggregate_atomics"]) + abs(sh["refill_divisor"] - 32) + (1 - sh["reemit_table"]) +
+                sh["stage_geometry"])
     def timer2(sh):  # the pool variant wins by a margin
         return timer(sh) - (0.5 if sh["packages_per_thread"] == 2 else 0.0)
     best, times = autotune._stages(timer2, False, autotune.GRID_BLOCK, autotune.GRID_RARE, autotune.GRID_BPS,
                                    autotune.GRID_INNER, autotune.GRID_AGG, autotune.GRID_REFILL, autotune.GRID_TABLE)
     assert best == {"block_size": 128, "blocks_per_sm": 0, "rare_batch": 24, "inner_moves": 64,
-                    "aggregate_atomics": 1, "refill_divisor": 32, "reemit_table": 1, "packages_per_thread": 2}
+                    "aggregate_atomics": 1, "refill_divisor": 32, "reemit_table": 1, "packages_per_thread": 2,
+                    "stage_geometry": 0}
     n_grid = len(autotune.GRID_BLOCK) * len(autotune.GRID_RARE) * len(autotune.GRID_INNER) * len(autotune.GRID_AGG)
     n_pool = len(autotune.GRID_BLOCK) * len(autotune.GRID_RARE)
-    assert len(times) == n_grid + n_pool + len(autotune.GRID_REFILL) - 1 + len(autotune.GRID_TABLE) - 1
+    assert len(times) == (n_grid + n_pool + len(autotune.GRID_REFILL) - 1 + len(autotune.GRID_TABLE) - 1 +
+                          len(autotune.GRID_STAGE) - 1)
     best1, _ = autotune._stages(timer2, False, (128,), (24,), (0,), (64,), (0, 1), (32,), (0, 1), pool_ok=False)
     assert best1["packages_per_thread"] == 1  # forced first interaction: no pool variant
     best64, _ = autotune._stages(timer2, True, (128,), (24,), (0,), (64,), (0, 1), (32,), (0, 1))
     assert best64["aggregate_atomics"] == 0 and best64["reemit_table"] == 0  # no such paths in the FP64 form
-    assert best64["packages_per_thread"] == 1
+    assert best64["packages_per_thread"] == 1 and best64["stage_geometry"] == 1  # nor staging
 
 
 def test_fp64_threshold_rule_covers_thin_cells_only():
