@@ -274,7 +274,8 @@ typedef struct dies_launch {
                           pools) has its geometry records (16 bytes + a density per
                           shell and the void) copied to shared memory by every CTA
                           and read there at each crossing, wherever that costs no
-                          resident CTA; 0: read through L1 (dies_set_launch: 1) */
+                          resident CTA; 0: read through L1.  Default 1;
+                          dies_set_launch leaves it as it is */
 } dies_launch;
 int dies_set_launch_ex(dies_model *m, const dies_launch *launch);
 

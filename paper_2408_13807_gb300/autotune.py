@@ -6,8 +6,9 @@ rare_batch, inner moves, aggregated absorption atomics), then a second
 package per thread in the warp's shared-memory pool, then the share of
 the launch a warp claims per trip to the device work counter (1/16 to 1/256),
 then the layout of the re-emission table (alias rows or FP32 CDF rows; a
-variant of the mixed form's single-model kernels), then whether a single
-model's geometry records are staged in shared memory.
+variant of the mixed form's single-model kernels); the shape grid is
+searched once with a single model's geometry records staged in shared
+memory and once without.
 Every candidate computes the same distributions; only the speed differs.
 The FP64-crossing threshold of the mixed form is an accuracy setting, not a
 speed one, so it is set by a rule on each model's shell geometry
@@ -110,13 +111,16 @@ def config_class(cloud, precision: str) -> str:
 # Tuning sizes: the package counts the benchmark runs use (the best shape
 # depends on them: work refills, the launch's tail), three timed runs each.
 TUNE_N = {"mixed": 100_000_000, "fp32": 100_000_000, "fp64": 20_000_000}
+# the all-FP32 form is tuned with the N_B = 50 sequential batches its
+# accuracy needs (Sect. 2.3): 50 launches of 2e6 packages, not one of 1e8
+TUNE_NB = {"fp32": 50}
 TUNE_N_BATCH = 200_000
 TUNE_REPS = 3
 
 
 def _time_model(cloud, precision: str, shape: dict, n: int, reps: int = TUNE_REPS) -> float:
     m = D.Model(cloud, precision=precision, fp64_radius=fp64_radius_for(cloud) if precision == "mixed" else 0.0,
-                **shape)
+                n_batches=TUNE_NB.get(precision, 1), **shape)
     try:
         m.run(min(n, 200_000), seed=7)  # tables + warm-up
         best = float("inf")
@@ -136,12 +140,13 @@ def _cached(c: Dict[str, dict], key: str) -> Optional[dict]:
 
 def _stages(timer, fp64: bool, blocks, rare, bps, inner, agg, refill, tables, ppt=GRID_PPT, pool_ok=True,
             stage=GRID_STAGE):
-    """Coordinate search: the shape grid, then two packages per thread (the
-    shared-memory pool) with the best shape over block size and rare batch,
-    then the refill divisor, then the table layout, then geometry staging;
-    returns (best, timings).  ``pool_ok`` is False where the pool variant
-    does not exist (FP64 form, forced first interaction); ``stage`` is (1,)
-    where staging does not apply (FP64 form, batches)."""
+    """Coordinate search: the shape grid under each geometry staging (the
+    best shape differs between the two kernels), then two packages per
+    thread (the shared-memory pool) with the best shape over block size and
+    rare batch, then the refill divisor, then the table layout; returns
+    (best, timings).  ``pool_ok`` is False where the pool variant does not
+    exist (FP64 form, forced first interaction); ``stage`` is (1,) where
+    staging does not apply (FP64 form, batches)."""
     times = {}
 
     def key(sh):
@@ -158,13 +163,14 @@ def _stages(timer, fp64: bool, blocks, rare, bps, inner, agg, refill, tables, pp
     if fp64 or not pool_ok:
         ppt = (1,)
     base = dict(DEFAULT)
-    for b in blocks:
-        for k in bps:
-            for r in rare:
-                for i in inner:
-                    for a in agg:
-                        try_shape(dict(base, block_size=b, blocks_per_sm=k, rare_batch=r, inner_moves=i,
-                                       aggregate_atomics=a))
+    for g in stage:
+        for b in blocks:
+            for k in bps:
+                for r in rare:
+                    for i in inner:
+                        for a in agg:
+                            try_shape(dict(base, block_size=b, blocks_per_sm=k, rare_batch=r, inner_moves=i,
+                                           aggregate_atomics=a, stage_geometry=g))
     best = dict(zip(KEYS, (int(x) for x in min(times, key=times.get).split("/"))))
     # more packages per thread, with the best shape's inner moves and atomics, over block size and rare batch
     for q in ppt:
@@ -179,9 +185,6 @@ def _stages(timer, fp64: bool, blocks, rare, bps, inner, agg, refill, tables, pp
     best = dict(zip(KEYS, (int(x) for x in min(times, key=times.get).split("/"))))
     for t in tables:
         try_shape(dict(best, reemit_table=t))
-    best = dict(zip(KEYS, (int(x) for x in min(times, key=times.get).split("/"))))
-    for g in stage:
-        try_shape(dict(best, stage_geometry=g))
     k = min(times, key=times.get)
     return dict(zip(KEYS, (int(x) for x in k.split("/")))), times
 

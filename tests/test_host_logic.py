@@ -105,8 +105,8 @@ def test_autotune_search_stages_cover_every_knob():
     """The tuner's coordinate search (with a synthetic timer: fastest at
     block 128, rare 24, inner 64, aggregation on, refill divisor 32, CDF
     rows, geometry read through L1) visits the shape grid, then packages per
-    thread, then the refill divisor, the table layout and geometry staging,
-    and returns the optimum of each stage."""
+    thread, then the refill divisor and the table layout, the shape grid
+    under both geometry stagings, and returns the optimum of each stage."""
     def timer(sh):
         return (abs(sh["block_size"] - 128) + abs(sh["rare_batch"] - 24) + abs(sh["inner_moves"] - 64) +
                 (1 - sh["aggregate_atomics"]) + abs(sh["refill_divisor"] - 32) + (1 - sh["reemit_table"]) +
@@ -120,8 +120,8 @@ def test_autotune_search_stages_cover_every_knob():
                     "stage_geometry": 0}
     n_grid = len(autotune.GRID_BLOCK) * len(autotune.GRID_RARE) * len(autotune.GRID_INNER) * len(autotune.GRID_AGG)
     n_pool = len(autotune.GRID_BLOCK) * len(autotune.GRID_RARE)
-    assert len(times) == (n_grid + n_pool + len(autotune.GRID_REFILL) - 1 + len(autotune.GRID_TABLE) - 1 +
-                          len(autotune.GRID_STAGE) - 1)
+    assert len(times) == (n_grid * len(autotune.GRID_STAGE) + n_pool + len(autotune.GRID_REFILL) - 1 +
+                          len(autotune.GRID_TABLE) - 1)
     best1, _ = autotune._stages(timer2, False, (128,), (24,), (0,), (64,), (0, 1), (32,), (0, 1), pool_ok=False)
     assert best1["packages_per_thread"] == 1  # forced first interaction: no pool variant
     best64, _ = autotune._stages(timer2, True, (128,), (24,), (0,), (64,), (0, 1), (32,), (0, 1))
