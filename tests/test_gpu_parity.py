@@ -158,6 +158,39 @@ def test_empty_cloud_mixed_sed_samples_the_source(D, oracle, point):
     assert np.all(sed[~ok] <= L * 1e-5)
 
 
+@pytest.mark.parametrize("prec", ["mixed", "fp32"])
+@pytest.mark.parametrize("stage", [1, 0])
+def test_crossing_count_in_an_empty_cloud(D, prec, stage):
+    """With zero density the crossings are geometry alone.  A package of a
+    central point source crosses each of the n boundaries once (n per
+    package, exactly).  An external package entering at impact parameter p
+    (p^2 uniform for k_bg = 1/2) crosses every inner boundary R_k > p twice
+    and the surface once: K = #{k : R_k > p} has mean sum (R_k/R)^2 and
+    E[K^2] = sum_k sum_l min((R_k/R)^2, (R_l/R)^2), and the mean count
+    1 + 2 E[K] is met within 5 standard errors.  This pins the kernels'
+    crossing counter (counted per block of moves), with the geometry staged
+    in shared memory and read through L1."""
+    base = W.config1().replace(rho=np.zeros(32))
+    n = base.n_cells
+    N = 10_000_000
+    pt = base.replace(J_ext=None, L_point=W.L_SUN, point_spec=W.blackbody(base.freq, 6000.0))
+    m = D.Model(pt, precision=prec, stage_geometry=stage).run(N, seed=1)
+    st = m.stats()
+    assert st["escaped"] == N and st["crossed"] == n * N
+    assert bool(st["variant"] & D.DIES_VARIANT_STAGED_GEOMETRY) == bool(stage)
+    m.close()
+    m = D.Model(base, precision=prec, stage_geometry=stage).run(N, seed=2)
+    st = m.stats()
+    m.close()
+    q = (base.radii[1:-1] / base.radii[-1]) ** 2
+    mean_k = q.sum()
+    var_k = np.minimum.outer(q, q).sum() - mean_k ** 2
+    expect = 1.0 + 2.0 * mean_k
+    se = 2.0 * np.sqrt(var_k / N)
+    assert st["escaped"] == N
+    assert abs(st["crossed"] / N - expect) < 5.0 * se, (st["crossed"] / N, expect, se)
+
+
 def test_single_shell_and_single_package(D, oracle):
     cloud = W.grey_model(1, 1.0, albedo=0.3, g=0.5)
     T = np.array([20.0])
