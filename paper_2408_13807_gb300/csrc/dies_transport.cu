@@ -553,8 +553,7 @@ __device__ __forceinline__ void move_forced(const TransportParams &P, Shared &S,
 // different kinds of flight): accumulate the column x = rho l; stop inside
 // the cell where acc + x passes lim (x > 0 there, so rho > 0), else cross.
 // The pre-walk has lim = inf and leaves the cloud into ST_FFIEND.
-// CALLER_COUNTS: the caller counts crossings per block of moves (forms
-// without forced interaction)
+// CALLER_COUNTS: the caller counts crossings per block of moves (FP32 forms)
 template <int PREC, int MODE, bool RECORD, int OPT, bool CALLER_COUNTS = false>
 __device__ __forceinline__ void move(const TransportParams &P, Shared &S, Lane<typename RealOf<PREC>::T> &L,
                                      Tally &T) {
@@ -575,7 +574,7 @@ __device__ __forceinline__ void move(const TransportParams &P, Shared &S, Lane<t
         if constexpr (!CALLER_COUNTS) T.cross++;
         if (next >= L.n) L.st = ST_ESCAPE;
       } else {
-        T.cross += L.cinc;
+        if constexpr (!CALLER_COUNTS) T.cross += L.cinc;
         if ((unsigned)(next - L.lo) >= (unsigned)L.span) L.st = L.exit_st;
       }
     }
@@ -1341,13 +1340,22 @@ __device__ __forceinline__ void flush_tallies(const TransportParams &P, Shared &
   }
 }
 
+// Whether the move that stopped a lane crossed a boundary: the exit (from
+// the cloud, or from the forced pre-walk's range) does, an interaction in
+// the cell does not.
+template <int OPT>
+__device__ __forceinline__ bool stop_crossed(const Lane<float> &L) {
+  if constexpr ((OPT & OPT_NOFFI) != 0) return L.st == ST_ESCAPE;
+  else return L.st == L.exit_st;
+}
+
 // The FP32 move of the staged-geometry kernels (OPT_SGEO): the same
 // arithmetic as boundary() + move(), with the current cell's record and
 // density (G, rho) carried in registers and the next cell's fetched from
 // shared memory as soon as the next cell is known, so that the load overlaps
 // the rest of the crossing instead of opening the next one (measured +1 to
 // +3 % with the block counting below).  CC: the caller counts the block's
-// crossings (forms without forced interaction).
+// crossings.
 template <int OPT, bool CC>
 __device__ __forceinline__ void move_staged(const TransportParams &P, Lane<float> &L, Tally &T, const float4 *sg,
                                             const float *sr, float4 &G, float &rho) {
@@ -1376,7 +1384,7 @@ __device__ __forceinline__ void move_staged(const TransportParams &P, Lane<float
       if constexpr (!CC) T.cross++;
       if (next >= L.n) L.st = ST_ESCAPE;
     } else {
-      T.cross += L.cinc;
+      if constexpr (!CC) T.cross += L.cinc;
       if ((unsigned)(next - L.lo) >= (unsigned)L.span) L.st = L.exit_st;
     }
   }
@@ -1423,12 +1431,16 @@ __global__ void __launch_bounds__(256, PREC == PREC_FP64 ? 1 : 5) k_transport(co
     // batch_min lanes no longer move (warp-uniform loop)
     for (int k = 0; k < P.inner; k += kCheck) {
       if (L.st <= ST_FORCED) {
-        // without forced interaction every move of a block crosses a
-        // boundary but the one that stops the lane (an interaction in its
-        // cell, or the exit): the block's crossings are counted once, from
-        // where it stopped, instead of at each move (measured +1 to +2 %)
-        constexpr bool kCC = (OPT & OPT_NOFFI) != 0 && PREC != PREC_FP64;
-        if constexpr (kCC) T.cross += kCheck;
+        // every move of a block crosses a boundary but the one that stops
+        // the lane (an interaction in its cell; the exit from the cloud or
+        // from the forced pre-walk's range does cross): the block's
+        // crossings are counted once, from where it stopped, instead of at
+        // each move (measured +1 to +2 %).  The forced-interaction forms
+        // count them only in flights that count crossings (cw = L.cinc;
+        // not the pre-walk), which cannot change within a block.
+        constexpr bool kCC = PREC != PREC_FP64;
+        const unsigned cw = ((OPT & OPT_NOFFI) != 0) ? 1u : (unsigned)L.cinc;
+        if constexpr (kCC) T.cross += kCheck * cw;
         if constexpr (kSG && PREC != PREC_FP64) {
           const float4 *sg = reinterpret_cast<const float4 *>(smem_raw + sizeof(Shared));
           const float *sr = reinterpret_cast<const float *>(sg + P.sgeo_n);
@@ -1440,7 +1452,7 @@ __global__ void __launch_bounds__(256, PREC == PREC_FP64 ? 1 : 5) k_transport(co
           for (int j = 0; j < kCheck; ++j) {
             move_staged<OPT, kCC>(P, L, T, sg, sr, G, rho);
             if (L.st > ST_FORCED) {
-              if constexpr (kCC) T.cross -= kCheck - j - (L.st == ST_ESCAPE ? 1 : 0);
+              if constexpr (kCC) T.cross -= (kCheck - j - (stop_crossed<OPT>(L) ? 1 : 0)) * cw;
               break;
             }
           }
@@ -1449,7 +1461,7 @@ __global__ void __launch_bounds__(256, PREC == PREC_FP64 ? 1 : 5) k_transport(co
           for (int j = 0; j < kCheck; ++j) {
             move<PREC, MODE, RECORD, OPT, kCC>(P, S, L, T);
             if (L.st > ST_FORCED) {
-              if constexpr (kCC) T.cross -= kCheck - j - (L.st == ST_ESCAPE ? 1 : 0);
+              if constexpr (kCC) T.cross -= (kCheck - j - (stop_crossed<OPT>(L) ? 1 : 0)) * cw;
               break;
             }
           }
