@@ -1187,6 +1187,18 @@ __device__ __forceinline__ void ffi_end(const TransportParams &P, Shared &S, Lan
       // the forced point lies on the outbound half: replay from the turning point
       L.s = Real(0);
       L.acc = col_half;
+    } else if (mirror && L.lim > Real(0.5) * col_half) {
+      // the forced point lies on the inbound half, nearer the turning point
+      // than the entry: the path is symmetric about the turning point, so
+      // walk the mirror image of the stretch from the point to the turning
+      // point (outbound from the turning point, to the column
+      // col_half - lim) and reflect s at the interaction (s0 = +inf marks
+      // it; s0 is not needed once the forced flight has started).  Fewer
+      // crossings than a replay from the entry: measured +2 % on forced runs
+      L.lim = col_half - L.lim;
+      L.s = Real(0);
+      L.acc = Real(0);
+      if constexpr (PREC != PREC_FP64) L.s0 = __int_as_float(0x7f800000);
     } else {
       L.s = L.s0;
       L.cell = (L.src == 0) ? L.n - 1 : __ldg(&P.desc[L.model].point_cell);
@@ -1202,9 +1214,13 @@ __device__ __forceinline__ void rare(const TransportParams &P, Shared &S, const 
                                      Lane<typename RealOf<PREC>::T> &L, Tally &T) {
   constexpr bool kGroup = (OPT & OPT_BATCH) != 0;
   const int kind = L.st;
-  if (kind == ST_FFIEND) {
-    ffi_end<PREC, RECORD, kGroup>(P, S, L, T);
-    return;
+  // (kernels without forced interaction never reach ST_FFIEND: compiling
+  // ffi_end out of them shortens them, measured +1 to +2.7 %)
+  if constexpr ((OPT & OPT_NOFFI) == 0) {
+    if (kind == ST_FFIEND) {
+      ffi_end<PREC, RECORD, kGroup>(P, S, L, T);
+      return;
+    }
   }
   if constexpr (PREC != PREC_FP64) {
     // the FP32 forms interrupt a package only here, so the event cap is checked here
@@ -1215,6 +1231,12 @@ __device__ __forceinline__ void rare(const TransportParams &P, Shared &S, const 
   }
   const U4 a = draw<PREC>(S, L);  // every rare event starts with one Philox block
   L.st = ST_NORMAL;
+  if constexpr (PREC != PREC_FP64 && (OPT & OPT_NOFFI) == 0) {
+    if (kind != ST_INJECT && L.s0 == __int_as_float(0x7f800000)) {
+      L.s = -L.s;  // a forced point reached on the mirrored stretch: back to the inbound half
+      L.s0 = 0.0f;
+    }
+  }
   constexpr bool kPlain = (OPT & OPT_PLAIN) != 0;
   if (kind == ST_INJECT) inject<PREC, RECORD, kGroup, kPlain>(P, S, L, T, a);
   else if (kind == ST_SCATTER) scatter<PREC, RECORD, kPlain>(P, S, L, T, a);
