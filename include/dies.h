@@ -229,7 +229,8 @@ int dies_set_stream(dies_model *m, void *cuda_stream);
  * same shell in the same pass add their energies with one atomic, each lane
  * taking as its E_old the returned value plus the energies of the lower
  * lanes (the order of a serial run; for absorption-heavy models with hot
- * inner shells).  Defaults 256, 0, 16, 32, 0.  Results do not depend on
+ * inner shells; a kernel variant, not used by the two-packages-per-thread
+ * kernels).  Defaults 256, 0, 16, 32, 0.  Results do not depend on
  * these values beyond FP32 rounding. */
 int dies_set_launch(dies_model *m, int block_size, int blocks_per_sm, int rare_batch, int inner_moves,
                     int aggregate_atomics);

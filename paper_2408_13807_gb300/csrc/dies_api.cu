@@ -50,7 +50,7 @@ size_t transport_smem_bytes(int n_tnodes_pow2);
 cudaError_t launch_transport(int prec, int mode, bool record, const TransportParams &P, int grid, int block,
                              cudaStream_t st);
 cudaError_t transport_occupancy(int prec, int mode, int block, int n_tnodes_pow2, bool r64, bool ffi, bool batch,
-                                bool pool, bool plain, int sgeo_n, int *blocks_per_sm);
+                                bool pool, bool plain, bool agg, int sgeo_n, int *blocks_per_sm);
 bool plain_weighting(const TransportParams &P);
 cudaError_t launch_finalize(cudaStream_t st, int n_cells, const double *E, const float *Eprev, const float *Ecur,
                             int fp32, const double *inv_mass, const double *Lnode, const double *lnT, int n,
@@ -504,14 +504,14 @@ struct Problem {
     sgeo_n = 0;
     const bool plain = plain_weighting(params(mode, 1, 0));  // the kernel variant the launch will pick
     DIES_CUDA(transport_occupancy(prec_, mode, block, next_pow2(n_tnodes), r64, ffi != 0, n_models > 1, pool, plain,
-                                  0, &occ));
+                                  agg != 0, 0, &occ));
     if (occ < 1) return fail(DIES_ECUDA, "transport kernel cannot be resident with block size %d", block);
     if (bps <= 0 || bps > occ) bps = occ;
     if (stage_geo && mode == MODE_IRE && n_models == 1 && prec_ != PREC_FP64 && !r64 && !(pool && ffi == 0)) {
       int occ_s = 0;
       // a refusal here (staged records beyond the shared-memory limit) only means: no staging
       if (transport_occupancy(prec_, mode, block, next_pow2(n_tnodes), false, ffi != 0, false, pool, plain,
-                              n_cells + 1, &occ_s) != cudaSuccess) {
+                              agg != 0, n_cells + 1, &occ_s) != cudaSuccess) {
         cudaGetLastError();
         occ_s = 0;
       }
@@ -1329,7 +1329,7 @@ int dies_run_frozen_static(dies_model *m, const double *T_frozen_dev, uint64_t n
                               p.at<double>(p.lay.dnu), T_frozen_dev, cdf));
   int occ = 0;
   DIES_CUDA(transport_occupancy(PREC_FP64, MODE_FROZEN, p.block, next_pow2(p.n_tnodes), false, false, false, false,
-                                false, 0, &occ));
+                                false, false, 0, &occ));
   if (occ < 1) return fail(DIES_ECUDA, "transport kernel cannot be resident with block size %d", p.block);
   const int bps = (p.blocks_per_sm > 0 && p.blocks_per_sm < occ) ? p.blocks_per_sm : occ;
   const int mode = (flags == DIES_FROZEN_ABSORB_TERMINAL) ? MODE_FROZEN_TERMINAL : MODE_FROZEN;

@@ -71,6 +71,10 @@ constexpr int OPT_PLAIN = 16;
 // addressing and latency); the host picks it only where the staged records
 // do not reduce the CTAs resident per SM
 constexpr int OPT_SGEO = 32;
+// FP32 forms, launch knob aggregate_atomics: the warp-aggregated absorption
+// atomics compiled in (without it the kernel carries no aggregation code:
+// measured +0.6 to +1 % on the classes that do not aggregate)
+constexpr int OPT_AGG = 64;
 
 template <int PREC>
 struct RealOf {
@@ -987,7 +991,7 @@ __device__ __forceinline__ void absorb(const TransportParams &P, Shared &S, cons
     // group predecessors), as a float in old_f; FP32 form from its two counters
     double old_d = 0.0;
     float old_f = 0.0f, pre_lane = 0.0f;
-    if (P.agg) {
+    if constexpr ((OPT & OPT_AGG) != 0) {
       // Lanes of this warp absorbing in the same cell add their energies
       // with one atomic; each lane's E_old is the group's old value plus the
       // energies of the group's lower lanes (the order of a serial run).
@@ -1922,7 +1926,7 @@ cudaError_t occupancy_one(int block, size_t smem, int *blocks_per_sm) {
 // option, and with sgeo_n > 0 (single model, no FP64 crossings) the
 // variant with the geometry staged in shared memory
 template <int PREC, int OPT>
-cudaError_t launch_ire(const TransportParams &P, bool plain, int grid, int block, size_t smem, cudaStream_t st) {
+cudaError_t launch_ire_a(const TransportParams &P, bool plain, int grid, int block, size_t smem, cudaStream_t st) {
   if constexpr ((OPT & (OPT_BATCH | OPT_R64)) == 0) {
     if (P.sgeo_n > 0) {
       const size_t sm = smem + sgeo_bytes(P.sgeo_n);
@@ -1935,7 +1939,13 @@ cudaError_t launch_ire(const TransportParams &P, bool plain, int grid, int block
 }
 
 template <int PREC, int OPT>
-cudaError_t occupancy_ire(bool plain, int sgeo_n, int block, size_t smem, int *blocks_per_sm) {
+cudaError_t launch_ire(const TransportParams &P, bool plain, int grid, int block, size_t smem, cudaStream_t st) {
+  return P.agg ? launch_ire_a<PREC, OPT | OPT_AGG>(P, plain, grid, block, smem, st)
+               : launch_ire_a<PREC, OPT>(P, plain, grid, block, smem, st);
+}
+
+template <int PREC, int OPT>
+cudaError_t occupancy_ire_a(bool plain, int sgeo_n, int block, size_t smem, int *blocks_per_sm) {
   if constexpr ((OPT & (OPT_BATCH | OPT_R64)) == 0) {
     if (sgeo_n > 0) {
       const size_t sm = smem + sgeo_bytes(sgeo_n);
@@ -1945,6 +1955,12 @@ cudaError_t occupancy_ire(bool plain, int sgeo_n, int block, size_t smem, int *b
   }
   return plain ? occupancy_one<PREC, MODE_IRE, false, OPT | OPT_PLAIN>(block, smem, blocks_per_sm)
                : occupancy_one<PREC, MODE_IRE, false, OPT>(block, smem, blocks_per_sm);
+}
+
+template <int PREC, int OPT>
+cudaError_t occupancy_ire(bool plain, bool agg, int sgeo_n, int block, size_t smem, int *blocks_per_sm) {
+  return agg ? occupancy_ire_a<PREC, OPT | OPT_AGG>(plain, sgeo_n, block, smem, blocks_per_sm)
+             : occupancy_ire_a<PREC, OPT>(plain, sgeo_n, block, smem, blocks_per_sm);
 }
 
 }  // namespace
@@ -2026,7 +2042,7 @@ cudaError_t launch_transport(int prec, int mode, bool record, const TransportPar
 }
 
 cudaError_t transport_occupancy(int prec, int mode, int block, int n_tnodes_pow2, bool r64, bool ffi, bool batch,
-                                bool pool, bool plain, int sgeo_n, int *blocks_per_sm) {
+                                bool pool, bool plain, bool agg, int sgeo_n, int *blocks_per_sm) {
   const size_t smem = transport_smem_bytes(n_tnodes_pow2);
   if (pool && mode == MODE_IRE && !ffi && prec != PREC_FP64) {
     const size_t sp = transport_smem_bytes_pool(n_tnodes_pow2, block);
@@ -2054,21 +2070,21 @@ cudaError_t transport_occupancy(int prec, int mode, int block, int n_tnodes_pow2
   }
   if (mode != MODE_IRE) return occupancy_one<PREC_FP64, MODE_FROZEN, true>(block, smem, blocks_per_sm);
   if (batch && !r64 && prec == PREC_MIXED)
-    return ffi ? occupancy_ire<PREC_MIXED, OPT_BATCH>(plain, sgeo_n, block, smem, blocks_per_sm)
-               : occupancy_ire<PREC_MIXED, OPT_BATCH | OPT_NOFFI>(plain, sgeo_n, block, smem, blocks_per_sm);
+    return ffi ? occupancy_ire<PREC_MIXED, OPT_BATCH>(plain, agg, sgeo_n, block, smem, blocks_per_sm)
+               : occupancy_ire<PREC_MIXED, OPT_BATCH | OPT_NOFFI>(plain, agg, sgeo_n, block, smem, blocks_per_sm);
   if (batch && prec == PREC_FP32)
-    return ffi ? occupancy_ire<PREC_FP32, OPT_BATCH>(plain, sgeo_n, block, smem, blocks_per_sm)
-               : occupancy_ire<PREC_FP32, OPT_BATCH | OPT_NOFFI>(plain, sgeo_n, block, smem, blocks_per_sm);
+    return ffi ? occupancy_ire<PREC_FP32, OPT_BATCH>(plain, agg, sgeo_n, block, smem, blocks_per_sm)
+               : occupancy_ire<PREC_FP32, OPT_BATCH | OPT_NOFFI>(plain, agg, sgeo_n, block, smem, blocks_per_sm);
   switch (prec) {
     case PREC_MIXED:
       if (ffi)
-        return r64 ? occupancy_ire<PREC_MIXED, OPT_R64>(plain, sgeo_n, block, smem, blocks_per_sm)
-                   : occupancy_ire<PREC_MIXED, 0>(plain, sgeo_n, block, smem, blocks_per_sm);
-      return r64 ? occupancy_ire<PREC_MIXED, OPT_R64 | OPT_NOFFI>(plain, sgeo_n, block, smem, blocks_per_sm)
-                 : occupancy_ire<PREC_MIXED, OPT_NOFFI>(plain, sgeo_n, block, smem, blocks_per_sm);
+        return r64 ? occupancy_ire<PREC_MIXED, OPT_R64>(plain, agg, sgeo_n, block, smem, blocks_per_sm)
+                   : occupancy_ire<PREC_MIXED, 0>(plain, agg, sgeo_n, block, smem, blocks_per_sm);
+      return r64 ? occupancy_ire<PREC_MIXED, OPT_R64 | OPT_NOFFI>(plain, agg, sgeo_n, block, smem, blocks_per_sm)
+                 : occupancy_ire<PREC_MIXED, OPT_NOFFI>(plain, agg, sgeo_n, block, smem, blocks_per_sm);
     case PREC_FP32:
-      return ffi ? occupancy_ire<PREC_FP32, 0>(plain, sgeo_n, block, smem, blocks_per_sm)
-                 : occupancy_ire<PREC_FP32, OPT_NOFFI>(plain, sgeo_n, block, smem, blocks_per_sm);
+      return ffi ? occupancy_ire<PREC_FP32, 0>(plain, agg, sgeo_n, block, smem, blocks_per_sm)
+                 : occupancy_ire<PREC_FP32, OPT_NOFFI>(plain, agg, sgeo_n, block, smem, blocks_per_sm);
     default: return occupancy_one<PREC_FP64, MODE_IRE, false>(block, smem, blocks_per_sm);
   }
 }
