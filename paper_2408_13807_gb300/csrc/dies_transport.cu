@@ -1922,9 +1922,9 @@ cudaError_t occupancy_one(int block, size_t smem, int *blocks_per_sm) {
 }
 
 // IRE kernels of the FP32 forms: the OPT_PLAIN variant when every weighting
-// option it drops is neutral
-// option, and with sgeo_n > 0 (single model, no FP64 crossings) the
-// variant with the geometry staged in shared memory
+// option it drops is neutral, with sgeo_n > 0 (single model, no FP64
+// crossings) the variant with the geometry staged in shared memory, and
+// (launch_ire) the OPT_AGG variant when the launch aggregates its atomics
 template <int PREC, int OPT>
 cudaError_t launch_ire_a(const TransportParams &P, bool plain, int grid, int block, size_t smem, cudaStream_t st) {
   if constexpr ((OPT & (OPT_BATCH | OPT_R64)) == 0) {
