@@ -367,8 +367,8 @@ void dies_destroy_model(dies_model *m);
 
 /* Frozen-temperature pass that allocates no device memory.  The paper has no
  * counterpart: this entry point serves callers that cannot call cudaMalloc
- * (code running while a stream is being captured, plug-ins whose host
- * application owns all device memory, allocators that forbid side
+ * (plug-ins whose host application owns all device memory, code whose
+ * memory budget is fixed up front, allocators that forbid side
  * allocations).  It computes the absorbed energies, the escaping SED, the
  * per-package event counts and the path hashes that dies_run_frozen
  * computes, but every input and output is a caller-owned DEVICE pointer and

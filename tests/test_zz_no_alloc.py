@@ -1,6 +1,6 @@
 """dies_run_frozen_static: the frozen-temperature pass for callers that cannot
-allocate device memory (for instance code running under stream capture, or a
-plug-in whose host application owns every device allocation).  Its scratch
+allocate device memory (for instance a plug-in whose host application owns
+every device allocation, or code whose memory budget is fixed up front).  Its scratch
 is a fixed array inside the library, so it must reproduce the allocating
 entry point dies_run_frozen exactly, call after call, with nothing left over
 from the previous call.  Collected last (file name) so that a failure here
